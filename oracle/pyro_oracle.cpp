@@ -1,0 +1,762 @@
+// CPU oracle for pointwise combustion thermochemistry — TEST INFRASTRUCTURE.
+//
+// This file is the plain, slow, obviously correct reference for the GPU library.
+// Only the test suite, the smoke check and the CPU-baseline leg of the benchmark
+// may load it; the library never does, and nothing here is shared with it
+// (its own mechanism parser, its own formulas, no common headers).
+//
+// Every quantity is the direct definition from the paper's formulation
+// appendix (Sec. A), evaluated literally: powers by std::pow, exponentials by
+// std::exp, products and sums by loops over species and reactions.  The code is
+// templated on the scalar type so that the same definitions run in
+//   double                -- the oracle proper,
+//   long double           -- a rounding-error envelope for the oracle itself,
+//   std::complex<double>  -- complex-step derivatives (Jacobian, JVP, VJP).
+//
+// Readings of passages that the paper leaves silent, ambiguous or garbled are
+// marked "reading (cN)" and listed in the design doc.
+//
+// Units: SI with kmol.  R = 8314.462618 J/(kmol K), p0 = 1 atm = 101325 Pa.
+
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+const double R_GAS = 8314.462618;   // J/(kmol K)
+const double P_ATM = 101325.0;      // Pa
+
+// ---------------------------------------------------------------------------
+// Mechanism (own parser of the text interchange format)
+// ---------------------------------------------------------------------------
+
+struct OSpecies {
+  std::string name;
+  std::vector<std::pair<int, int>> comp;   // (element index, count)
+  double W = 0;                            // kg/kmol
+  double t_low = 0, t_mid = 0, t_high = 0;
+  double lo[7] = {0}, hi[7] = {0};
+};
+
+enum { K_ARRHENIUS = 0, K_THREEBODY = 1, K_FALLOFF = 2 };
+
+struct OReaction {
+  int kind = K_ARRHENIUS;
+  bool reversible = true, duplicate = false;
+  std::vector<std::pair<int, int>> reac, prod;   // (species, coefficient)
+  double A = 0, b = 0, theta = 0;
+  std::vector<std::pair<int, double>> eff;       // efficiencies (default 1)
+  bool has_low = false;
+  double A0 = 0, b0 = 0, theta0 = 0;
+  int n_troe = 0;
+  double troe[4] = {0, 0, 0, 0};
+};
+
+struct OMech {
+  std::vector<std::string> el_name;
+  std::vector<double> el_weight;
+  std::vector<OSpecies> sp;
+  std::vector<OReaction> rx;
+  int N() const { return (int)sp.size(); }
+  int M() const { return (int)rx.size(); }
+};
+
+thread_local std::string g_err;
+
+bool parse_mech(const char* path, OMech& m) {
+  std::ifstream f(path);
+  if (!f) { g_err = std::string("cannot open ") + path; return false; }
+  std::string line, key;
+  std::vector<std::string> lines;
+  while (std::getline(f, line)) {
+    if (line.empty() || line[0] == '#') continue;
+    lines.push_back(line);
+  }
+  size_t li = 0;
+  auto next = [&](std::istringstream& is) -> bool {
+    if (li >= lines.size()) return false;
+    is.clear(); is.str(lines[li++]); return true;
+  };
+  std::istringstream is;
+  if (!next(is)) { g_err = "empty file"; return false; }
+  int ver = 0; is >> key >> ver;
+  if (key != "pyro-mech" || ver != 1) { g_err = "bad header"; return false; }
+  next(is);                                        // name
+  int ne = 0; next(is); is >> key >> ne;
+  for (int i = 0; i < ne; ++i) {
+    next(is); std::string s; double w; is >> key >> s >> w;
+    m.el_name.push_back(s); m.el_weight.push_back(w);
+  }
+  int ns = 0; next(is); is >> key >> ns;
+  m.sp.resize(ns);
+  for (int k = 0; k < ns; ++k) {
+    next(is); int nc; is >> key >> m.sp[k].name >> nc;
+    for (int c = 0; c < nc; ++c) {
+      std::string e; int cnt; is >> e >> cnt;
+      int ei = -1;
+      for (int q = 0; q < ne; ++q) if (m.el_name[q] == e) ei = q;
+      if (ei < 0) { g_err = "unknown element " + e; return false; }
+      m.sp[k].comp.push_back({ei, cnt});
+    }
+  }
+  for (int k = 0; k < ns; ++k) {
+    next(is); int idx; is >> key >> idx;
+    if (key != "thermo" || idx < 0 || idx >= ns) { g_err = "bad thermo line"; return false; }
+    OSpecies& s = m.sp[idx];
+    is >> s.t_low >> s.t_mid >> s.t_high;
+    for (int i = 0; i < 7; ++i) is >> s.lo[i];
+    for (int i = 0; i < 7; ++i) is >> s.hi[i];
+    if (!is) { g_err = "short thermo line"; return false; }
+  }
+  // molecular weights from atomic weights (Sec. A.1: W_k of species k)
+  for (auto& s : m.sp) {
+    double W = 0;
+    for (auto& c : s.comp) W += c.second * m.el_weight[c.first];
+    s.W = W;
+  }
+  int nr = 0; next(is); is >> key >> nr;
+  m.rx.resize(nr);
+  for (int j = 0; j < nr; ++j) {
+    next(is); OReaction& r = m.rx[j];
+    std::string kind; is >> key >> kind;
+    if (kind == "arrhenius") r.kind = K_ARRHENIUS;
+    else if (kind == "threebody") r.kind = K_THREEBODY;
+    else if (kind == "falloff") r.kind = K_FALLOFF;
+    else { g_err = "unknown reaction kind " + kind; return false; }
+    std::string tok;
+    while (is >> tok && tok != "end") {
+      if (tok == "rev") { int v; is >> v; r.reversible = v != 0; }
+      else if (tok == "dup") { int v; is >> v; r.duplicate = v != 0; }
+      else if (tok == "reac" || tok == "prod") {
+        int n; is >> n;
+        for (int q = 0; q < n; ++q) {
+          int k, nu; is >> k >> nu;
+          (tok == "reac" ? r.reac : r.prod).push_back({k, nu});
+        }
+      } else if (tok == "arr") { is >> r.A >> r.b >> r.theta; }
+      else if (tok == "eff") {
+        int n; is >> n;
+        for (int q = 0; q < n; ++q) { int k; double e; is >> k >> e; r.eff.push_back({k, e}); }
+      } else if (tok == "low") { r.has_low = true; is >> r.A0 >> r.b0 >> r.theta0; }
+      else if (tok == "troe") {
+        // 3 or 4 numbers follow; peek until a keyword
+        r.n_troe = 0;
+        std::streampos pos;
+        while (true) {
+          pos = is.tellg();
+          std::string t2; if (!(is >> t2)) break;
+          char* endp = nullptr;
+          double v = std::strtod(t2.c_str(), &endp);
+          if (endp == t2.c_str() || *endp != '\0') { is.seekg(pos); break; }
+          if (r.n_troe < 4) r.troe[r.n_troe++] = v;
+        }
+      } else { g_err = "unknown reaction token " + tok; return false; }
+    }
+    if (tok != "end") { g_err = "unterminated reaction"; return false; }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Scalar helpers (real part for comparisons, so complex steps pass through)
+// ---------------------------------------------------------------------------
+
+inline double re(double x) { return x; }
+inline long double re(long double x) { return x; }
+inline double re(const std::complex<double>& x) { return x.real(); }
+
+// ---------------------------------------------------------------------------
+// Thermodynamics: NASA-7 polynomials (Sec. A.1, Eq. nasa_poly, Eq. nasa_poly_c)
+// ---------------------------------------------------------------------------
+
+inline const double* nasa_coeffs(const OSpecies& s, double T) {
+  // reading (c6): low range if T < T_mid, else high range; no clamping
+  return T < s.t_mid ? s.lo : s.hi;
+}
+
+// cp/R = sum_{m=1}^{5} a_m T^{m-1}      (Eq. nasa_poly_c, reading (c3))
+template <class S> S cp_R(const OSpecies& s, S T) {
+  const double* a = nasa_coeffs(s, re(T));
+  S v = 0;
+  for (int m = 1; m <= 5; ++m) v += a[m - 1] * std::pow(T, (double)(m - 1));
+  return v;
+}
+
+// h/(R T) = a6/T + sum_{m=1}^{5} a_m T^{m-1}/m     (Eq. nasa_poly, first line; reading (c4))
+template <class S> S h_RT(const OSpecies& s, S T) {
+  const double* a = nasa_coeffs(s, re(T));
+  S v = a[5] / T;
+  for (int m = 1; m <= 5; ++m) v += a[m - 1] * std::pow(T, (double)(m - 1)) / (double)m;
+  return v;
+}
+
+// s/R = a1 ln T + sum_{m=2}^{5} a_m T^{m-1}/(m-1) + a7    (Eq. nasa_poly, second line; reading (c2))
+template <class S> S s_R(const OSpecies& s, S T) {
+  const double* a = nasa_coeffs(s, re(T));
+  S v = a[0] * std::log(T) + a[6];
+  for (int m = 2; m <= 5; ++m) v += a[m - 1] * std::pow(T, (double)(m - 1)) / (double)(m - 1);
+  return v;
+}
+
+// g/(R T) = h/(R T) - s/R     (Eq. gibbs)
+template <class S> S g_RT(const OSpecies& s, S T) { return h_RT(s, T) - s_R(s, T); }
+
+// ---------------------------------------------------------------------------
+// Mixture relations (Sec. A.1 Eq. eos; Sec. A.3.1 Eq. int_energy, Eq. cv)
+// ---------------------------------------------------------------------------
+
+// W = (sum Y_i/W_i)^{-1};  rho = p W / (R T)      (Eq. eos)
+template <class S> S density(const OMech& m, S p, S T, const S* Y) {
+  S inv = 0;
+  for (int k = 0; k < m.N(); ++k) inv += Y[k] / m.sp[k].W;
+  return p / (R_GAS * T * inv);
+}
+
+// e = sum_k Y_k (h_k - R T)/W_k          (Eq. int_energy)
+template <class S> S internal_energy(const OMech& m, S T, const S* Y) {
+  S e = 0;
+  for (int k = 0; k < m.N(); ++k) {
+    S hk = R_GAS * T * h_RT(m.sp[k], T);
+    e += Y[k] * (hk - R_GAS * T) / m.sp[k].W;
+  }
+  return e;
+}
+
+// c_v = sum_k Y_k (cp_k - R)/W_k = de/dT      (Eq. cv, reading (c5): per-mass form)
+template <class S> S cv_mass(const OMech& m, S T, const S* Y) {
+  S c = 0;
+  for (int k = 0; k < m.N(); ++k) c += Y[k] * (R_GAS * cp_R(m.sp[k], T) - R_GAS) / m.sp[k].W;
+  return c;
+}
+
+// Newton iteration for T(e, Y)       (Sec. A.3.1, Eq. delta_temp)
+//   T_{m+1} = T_m - (Y.e(T_m) - e) / c_v(T_m)
+// reading (c7): stop once |dT| <= tol*T_{m+1}, then take one more step;
+// reading (c6): iterates clamped to [100, 5000] K.  Returns iterations used,
+// or -1 if max_iter was reached without meeting the stop rule.
+int temperature_newton(const OMech& m, double e, const double* Y, double T0, double tol,
+                       int max_iter, double* T_out) {
+  double T = T0;
+  for (int it = 1; it <= max_iter; ++it) {
+    double dT = -(internal_energy(m, T, Y) - e) / cv_mass(m, T, Y);
+    double Tn = T + dT;
+    if (Tn < 100.0) Tn = 100.0;
+    if (Tn > 5000.0) Tn = 5000.0;
+    bool done = std::fabs(Tn - T) <= tol * Tn;
+    T = Tn;
+    if (done) {
+      double dT2 = -(internal_energy(m, T, Y) - e) / cv_mass(m, T, Y);
+      T = T + dT2;
+      *T_out = T;
+      return it + 1;
+    }
+  }
+  *T_out = T;
+  return -1;
+}
+
+// Bisection on [lo, hi] for e(T) = e (independent check of the Newton result).
+double temperature_bisect(const OMech& m, double e, const double* Y, double lo, double hi) {
+  double flo = internal_energy(m, lo, Y) - e;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    double fm = internal_energy(m, mid, Y) - e;
+    if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else { hi = mid; }
+  }
+  return 0.5 * (lo + hi);
+}
+
+// ---------------------------------------------------------------------------
+// Kinetics (Sec. A.1 Eqs. reactions, production_rates, reaction_rates,
+// concentrations, rate_coeff, equil_constants)
+// ---------------------------------------------------------------------------
+
+// k = A T^b exp(-theta/T)      (Eq. rate_coeff)
+template <class S> S arrhenius(double A, double b, double theta, S T) {
+  return A * std::pow(T, b) * std::exp(-theta / T);
+}
+
+// [M]_j = sum_k eps_kj C_k, eps default 1      (reading (c9))
+template <class S> S third_body(const OReaction& r, const S* C, int N) {
+  S M = 0;
+  for (int k = 0; k < N; ++k) {
+    double e = 1.0;
+    for (auto& p : r.eff) if (p.first == k) e = p.second;
+    M += e * C[k];
+  }
+  return M;
+}
+
+// Troe falloff blending (cited in Sec. A.1 for concentration-dependent rate
+// coefficients; standard form, reading (c8)).  Lindemann when no Troe data.
+template <class S> S falloff_factor(const OReaction& r, S T, S Pr) {
+  if (r.n_troe < 3) return S(1.0);
+  double a = r.troe[0], T3 = r.troe[1], T1 = r.troe[2];
+  S Fcent = (1.0 - a) * std::exp(-T / T3) + a * std::exp(-T / T1);
+  if (r.n_troe >= 4) Fcent += std::exp(-r.troe[3] / T);
+  S lFc = std::log10(Fcent);
+  S c = -0.4 - 0.67 * lFc;
+  S n = 0.75 - 1.27 * lFc;
+  const double d = 0.14;
+  S lPr = std::log10(Pr);
+  S f = (lPr + c) / (n - d * (lPr + c));
+  S lF = lFc / (1.0 + f * f);
+  return std::pow(S(10.0), lF);
+}
+
+// forward rate coefficient k_f,j (includes [M] for third-body reactions, reading (c14))
+template <class S> S forward_rate_coefficient(const OMech& m, const OReaction& r, S T, const S* C) {
+  int N = m.N();
+  if (r.kind == K_ARRHENIUS) return arrhenius(r.A, r.b, r.theta, T);
+  if (r.kind == K_THREEBODY) return arrhenius(r.A, r.b, r.theta, T) * third_body(r, C, N);
+  // falloff: k = k_inf * Pr/(1+Pr) * F,  Pr = k0 [M] / k_inf
+  S kinf = arrhenius(r.A, r.b, r.theta, T);
+  S k0 = arrhenius(r.A0, r.b0, r.theta0, T);
+  S Pr = k0 * third_body(r, C, N) / kinf;
+  if (re(Pr) < 1e-300) Pr = Pr - re(Pr) + 1e-300;   // guard log10(0) (reading (c8))
+  return kinf * (Pr / (1.0 + Pr)) * falloff_factor(r, T, Pr);
+}
+
+// K_j = (p0/(R T))^{sum_i nu_ij} exp(-sum_i nu_ij g_i/(R T))      (Eq. equil_constants, reading (c1))
+template <class S> S equilibrium_constant(const OMech& m, const OReaction& r, S T) {
+  double dnu = 0;
+  S dg = 0;
+  for (auto& p : r.prod) { dnu += p.second; dg += (double)p.second * g_RT(m.sp[p.first], T); }
+  for (auto& p : r.reac) { dnu -= p.second; dg -= (double)p.second * g_RT(m.sp[p.first], T); }
+  return std::pow(P_ATM / (R_GAS * T), dnu) * std::exp(-dg);
+}
+
+template <class S> S conc_product(const std::vector<std::pair<int, int>>& side, const S* C) {
+  S p = 1.0;
+  for (auto& q : side)
+    for (int i = 0; i < q.second; ++i) p *= C[q.first];
+  return p;
+}
+
+// C_k = rho Y_k / W_k      (Eq. concentrations)
+template <class S> void concentrations(const OMech& m, S rho, const S* Y, S* C) {
+  for (int k = 0; k < m.N(); ++k) C[k] = rho * Y[k] / m.sp[k].W;
+}
+
+// Rates of progress, law of mass action (Eq. reaction_rates):
+//   R_j = k_j [prod C^nu' - (1/K_j) prod C^nu'']  = Rf_j - Rr_j
+template <class S> void rates_of_progress(const OMech& m, S rho, S T, const S* Y, S* Rf, S* Rr,
+                                          S* kf_out = nullptr, S* Kc_out = nullptr) {
+  int N = m.N();
+  std::vector<S> C(N);
+  concentrations(m, rho, Y, C.data());
+  for (int j = 0; j < m.M(); ++j) {
+    const OReaction& r = m.rx[j];
+    S kf = forward_rate_coefficient(m, r, T, C.data());
+    S Kc = equilibrium_constant(m, r, T);
+    Rf[j] = kf * conc_product(r.reac, C.data());
+    Rr[j] = r.reversible ? kf / Kc * conc_product(r.prod, C.data()) : S(0.0);
+    if (kf_out) kf_out[j] = kf;
+    if (Kc_out) Kc_out[j] = Kc;
+  }
+}
+
+// Net production rates (Eq. production_rates): omega_i = sum_j nu_ij R_j,
+// nu = nu'' - nu' (Eq. reactions).  Optionally the gross scale
+// G_i = sum_j |nu_ij| (|Rf_j| + |Rr_j|) used for the parity tolerance (reading (c15)).
+template <class S> void net_production_rates(const OMech& m, S rho, S T, const S* Y, S* omega,
+                                             double* gross = nullptr) {
+  int N = m.N(), M = m.M();
+  std::vector<S> Rf(M), Rr(M);
+  rates_of_progress(m, rho, T, Y, Rf.data(), Rr.data());
+  for (int k = 0; k < N; ++k) omega[k] = 0.0;
+  if (gross) for (int k = 0; k < N; ++k) gross[k] = 0.0;
+  for (int j = 0; j < M; ++j) {
+    const OReaction& r = m.rx[j];
+    S Rj = Rf[j] - Rr[j];
+    // nu_ij for every species of the reaction (a species may appear on both sides)
+    std::map<int, int> nu;
+    for (auto& p : r.prod) nu[p.first] += p.second;
+    for (auto& p : r.reac) nu[p.first] -= p.second;
+    for (auto& q : nu) {
+      omega[q.first] += (double)q.second * Rj;
+      if (gross) gross[q.first] += std::abs(q.second) * (std::fabs((double)re(Rf[j])) + std::fabs((double)re(Rr[j])));
+    }
+  }
+}
+
+// Temperature rate of the adiabatic isochoric reactor (Sec. A.1 Eq. massfrac_ode with
+// e fixed, reading (c13)):  dT/dt = -sum_k (h_k - R T) omega_k / (rho c_v)
+template <class S> S temperature_rate(const OMech& m, S rho, S T, const S* Y, const S* omega) {
+  S num = 0;
+  for (int k = 0; k < m.N(); ++k) num += (R_GAS * T * h_RT(m.sp[k], T) - R_GAS * T) * omega[k];
+  return -num / (rho * cv_mass(m, T, Y));
+}
+
+typedef std::complex<double> cplx;
+const double CS_H = 1e-30;   // complex-step size (no subtractive cancellation)
+
+// ---------------------------------------------------------------------------
+// BF16 MLP for the Newton initial guess (model definition; FP64 arithmetic
+// with bf16 rounding at the same points as the GPU network).
+// ---------------------------------------------------------------------------
+
+double round_bf16(double x) {
+  // round-to-nearest-even to 8 significant bits (bf16), via float
+  float f = (float)x;
+  uint32_t u; std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return f;
+  uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  u &= 0xffff0000u;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+template <class S> S silu(S x) { return x / (1.0 + std::exp(-x)); }
+template <class S> S rbf(S x) { return x - re(x) + round_bf16(re(x)); }   // straight-through rounding
+
+
+template <class S>
+S mlp_forward_one(int D, int H, const double* P, const S* x, std::vector<S>& a1, std::vector<S>& a2,
+                  std::vector<S>& z1, std::vector<S>& z2) {
+  const double* W1 = P; const double* b1 = W1 + H * D;
+  const double* W2 = b1 + H; const double* b2 = W2 + H * H;
+  const double* w3 = b2 + H; const double* b3 = w3 + H;
+  for (int o = 0; o < H; ++o) {
+    S z = b1[o];
+    for (int i = 0; i < D; ++i) z += W1[o * D + i] * rbf(x[i]);
+    z1[o] = z; a1[o] = rbf(silu(z));
+  }
+  for (int o = 0; o < H; ++o) {
+    S z = b2[o];
+    for (int i = 0; i < H; ++i) z += W2[o * H + i] * a1[i];
+    z2[o] = z; a2[o] = rbf(silu(z));
+  }
+  S y = b3[0];
+  for (int i = 0; i < H; ++i) y += w3[i] * a2[i];
+  return y;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C interface (ctypes).  All arrays SoA: X[k*n + p].
+// ===========================================================================
+
+extern "C" {
+
+const char* orc_last_error() { return g_err.c_str(); }
+
+void* orc_load(const char* path) {
+  OMech* m = new OMech();
+  if (!parse_mech(path, *m)) { delete m; return nullptr; }
+  return m;
+}
+
+void orc_free(void* h) { delete (OMech*)h; }
+
+int orc_info(void* h, int* N, int* M) {
+  OMech* m = (OMech*)h; *N = m->N(); *M = m->M(); return 0;
+}
+
+int orc_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_set_threads(int t) {
+#ifdef _OPENMP
+  if (t > 0) omp_set_num_threads(t);
+#else
+  (void)t;
+#endif
+}
+
+void orc_mol_weights(void* h, double* W) {
+  OMech* m = (OMech*)h;
+  for (int k = 0; k < m->N(); ++k) W[k] = m->sp[k].W;
+}
+
+// out[4] = cp/R, h/RT, s/R, g/RT of species k at T
+void orc_species_thermo(void* h, int k, double T, double* out) {
+  OMech* m = (OMech*)h;
+  out[0] = cp_R(m->sp[k], T); out[1] = h_RT(m->sp[k], T);
+  out[2] = s_R(m->sp[k], T);  out[3] = g_RT(m->sp[k], T);
+}
+
+// complex-step temperature derivatives: out[0] = d(h/R)/dT, out[1] = d(s/R)/dT, out[2] = d(cp/R)/dT
+void orc_species_thermo_dT(void* h, int k, double T, double* out) {
+  OMech* m = (OMech*)h;
+  cplx Tc(T, CS_H);
+  out[0] = (Tc * h_RT(m->sp[k], Tc)).imag() / CS_H;
+  out[1] = s_R(m->sp[k], Tc).imag() / CS_H;
+  out[2] = cp_R(m->sp[k], Tc).imag() / CS_H;
+}
+
+void orc_density(void* h, int64_t n, const double* p, const double* T, const double* Y, double* rho) {
+  OMech* m = (OMech*)h; int N = m->N();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    rho[i] = density(*m, p[i], T[i], y.data());
+  }
+}
+
+void orc_internal_energy(void* h, int64_t n, const double* T, const double* Y, double* e, double* cv) {
+  OMech* m = (OMech*)h; int N = m->N();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    e[i] = internal_energy(*m, T[i], y.data());
+    if (cv) cv[i] = cv_mass(*m, T[i], y.data());
+  }
+}
+
+// Returns the number of points that did not converge.
+int64_t orc_temperature(void* h, int64_t n, const double* e, const double* Y, const double* guess,
+                        double T_guess, double tol, int max_iter, double* T, int32_t* iters) {
+  OMech* m = (OMech*)h; int N = m->N();
+  int64_t bad = 0;
+#pragma omp parallel for schedule(static) reduction(+:bad)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    double T0 = guess ? guess[i] : T_guess;
+    int it = temperature_newton(*m, e[i], y.data(), T0, tol, max_iter, &T[i]);
+    if (iters) iters[i] = it;
+    if (it < 0) ++bad;
+  }
+  return bad;
+}
+
+void orc_temperature_bisect(void* h, int64_t n, const double* e, const double* Y, double lo, double hi,
+                            double* T) {
+  OMech* m = (OMech*)h; int N = m->N();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    T[i] = temperature_bisect(*m, e[i], y.data(), lo, hi);
+  }
+}
+
+// Per-reaction quantities at each point: kf, Kc, Rf, Rr (each [M][n]); any may be null.
+void orc_reaction_data(void* h, int64_t n, const double* rho, const double* T, const double* Y,
+                       double* kf, double* Kc, double* Rf, double* Rr) {
+  OMech* m = (OMech*)h; int N = m->N(), M = m->M();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N), a(M), b(M), c(M), d(M);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    rates_of_progress(*m, rho[i], T[i], y.data(), a.data(), b.data(), c.data(), d.data());
+    for (int j = 0; j < M; ++j) {
+      if (Rf) Rf[j * n + i] = a[j];
+      if (Rr) Rr[j * n + i] = b[j];
+      if (kf) kf[j * n + i] = c[j];
+      if (Kc) Kc[j * n + i] = d[j];
+    }
+  }
+}
+
+// omega [N][n] and (optional) gross scale [N][n]; if T_in is null, T is solved
+// from e (Newton from T_guess) and written to T_out.
+void orc_net_production_rates(void* h, int64_t n, const double* rho, const double* T_in, const double* Y,
+                              double* omega, double* gross) {
+  OMech* m = (OMech*)h; int N = m->N();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N), w(N), g(N);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    net_production_rates(*m, rho[i], T_in[i], y.data(), w.data(), gross ? g.data() : nullptr);
+    for (int k = 0; k < N; ++k) {
+      omega[k * n + i] = w[k];
+      if (gross) gross[k * n + i] = g[k];
+    }
+  }
+}
+
+// the same in long double (rounding envelope of the double oracle)
+void orc_net_production_rates_ld(void* h, int64_t n, const double* rho, const double* T_in,
+                                 const double* Y, double* omega) {
+  OMech* m = (OMech*)h; int N = m->N();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<long double> y(N), w(N);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    net_production_rates<long double>(*m, rho[i], T_in[i], y.data(), w.data(), nullptr);
+    for (int k = 0; k < N; ++k) omega[k * n + i] = (double)w[k];
+  }
+}
+
+// dT/dt of the adiabatic isochoric reactor, [n]
+void orc_temperature_rate(void* h, int64_t n, const double* rho, const double* T, const double* Y,
+                          double* Tdot) {
+  OMech* m = (OMech*)h; int N = m->N();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N), w(N);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    net_production_rates(*m, rho[i], T[i], y.data(), w.data());
+    Tdot[i] = temperature_rate(*m, rho[i], T[i], y.data(), w.data());
+  }
+}
+
+// Dense Jacobian d(Tdot, omega)/d(T, Y) at fixed rho by complex step, reading (c13).
+// J[(r*(N+1) + c)*n + p]; row 0 = Tdot, rows 1..N = omega; column 0 = T, columns 1..N = Y.
+void orc_jacobian(void* h, int64_t n, const double* rho, const double* T, const double* Y, double* J) {
+  OMech* m = (OMech*)h; int N = m->N(); int NP = N + 1;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<cplx> y(N), w(N);
+    for (int c = 0; c < NP; ++c) {
+      cplx Tc(T[i], c == 0 ? CS_H : 0.0);
+      for (int k = 0; k < N; ++k) y[k] = cplx(Y[k * n + i], (c == k + 1) ? CS_H : 0.0);
+      cplx rc(rho[i], 0.0);
+      net_production_rates<cplx>(*m, rc, Tc, y.data(), w.data());
+      cplx td = temperature_rate<cplx>(*m, rc, Tc, y.data(), w.data());
+      J[(0 * NP + c) * n + i] = td.imag() / CS_H;
+      for (int k = 0; k < N; ++k) J[((k + 1) * NP + c) * n + i] = w[k].imag() / CS_H;
+    }
+  }
+}
+
+// JVP of omega(rho, T, Y) along (drho, dT, dY) by complex step: domega [N][n]
+void orc_jvp(void* h, int64_t n, const double* rho, const double* T, const double* Y,
+             const double* drho, const double* dT, const double* dY, double* domega) {
+  OMech* m = (OMech*)h; int N = m->N();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<cplx> y(N), w(N);
+    for (int k = 0; k < N; ++k) y[k] = cplx(Y[k * n + i], CS_H * dY[k * n + i]);
+    net_production_rates<cplx>(*m, cplx(rho[i], CS_H * drho[i]), cplx(T[i], CS_H * dT[i]), y.data(), w.data());
+    for (int k = 0; k < N; ++k) domega[k * n + i] = w[k].imag() / CS_H;
+  }
+}
+
+// VJP of omega(rho, T, Y): (rho_bar, T_bar, Y_bar) = J^T omega_bar with J = d omega/d(rho, T, Y)
+// formed column by column (complex step).
+void orc_vjp(void* h, int64_t n, const double* rho, const double* T, const double* Y,
+             const double* wbar, double* rho_bar, double* T_bar, double* Y_bar) {
+  OMech* m = (OMech*)h; int N = m->N();
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<cplx> y(N), w(N);
+    for (int c = 0; c < N + 2; ++c) {
+      cplx rc(rho[i], c == 0 ? CS_H : 0.0), Tc(T[i], c == 1 ? CS_H : 0.0);
+      for (int k = 0; k < N; ++k) y[k] = cplx(Y[k * n + i], (c == k + 2) ? CS_H : 0.0);
+      net_production_rates<cplx>(*m, rc, Tc, y.data(), w.data());
+      double acc = 0;
+      for (int k = 0; k < N; ++k) acc += wbar[k * n + i] * (w[k].imag() / CS_H);
+      if (c == 0) rho_bar[i] = acc;
+      else if (c == 1) T_bar[i] = acc;
+      else Y_bar[(c - 2) * n + i] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// MLP (D_in -> H -> H -> 1, SiLU).  Parameters packed as
+//   W1[H][D], b1[H], W2[H][H], b2[H], w3[H], b3[1]     (row-major, doubles)
+// Input features x[n][D] (already normalised; rounded to bf16 here), output
+// y[n] = network output in normalised units.  Weights are used as given
+// (the caller passes bf16-exact values); hidden activations are rounded to
+// bf16 after SiLU, the output is not.
+// ---------------------------------------------------------------------------
+
+void orc_mlp_forward(int D, int H, const double* P, int64_t n, const double* x, double* y) {
+#pragma omp parallel for schedule(static)
+  for (int64_t p = 0; p < n; ++p) {
+    std::vector<double> a1(H), a2(H), z1(H), z2(H);
+    y[p] = mlp_forward_one<double>(D, H, P, x + p * D, a1, a2, z1, z2);
+  }
+}
+
+// Gradient of L = (1/n) sum_p (y_p - t_p)^2 w.r.t. all parameters (same packing),
+// by the chain rule (backpropagation), rounding treated as identity.
+double orc_mlp_loss_grad(int D, int H, const double* P, int64_t n, const double* x, const double* t,
+                         double* grad) {
+  int NPAR = H * D + H + H * H + H + H + 1;
+  for (int q = 0; q < NPAR; ++q) grad[q] = 0;
+  const double* W2 = P + H * D + H;
+  const double* w3 = W2 + H * H + H;
+  double loss = 0;
+  for (int64_t p = 0; p < n; ++p) {
+    std::vector<double> a1(H), a2(H), z1(H), z2(H), d2(H), d1(H);
+    const double* xp = x + p * D;
+    double y = mlp_forward_one<double>(D, H, P, xp, a1, a2, z1, z2);
+    double r = y - t[p];
+    loss += r * r;
+    double dy = 2.0 * r / (double)n;
+    double* gW1 = grad; double* gb1 = gW1 + H * D; double* gW2 = gb1 + H;
+    double* gb2 = gW2 + H * H; double* gw3 = gb2 + H; double* gb3 = gw3 + H;
+    gb3[0] += dy;
+    for (int i = 0; i < H; ++i) {
+      gw3[i] += dy * a2[i];
+      double s = 1.0 / (1.0 + std::exp(-z2[i]));
+      d2[i] = dy * w3[i] * (s * (1.0 + z2[i] * (1.0 - s)));   // d silu/dz
+    }
+    for (int o = 0; o < H; ++o) {
+      gb2[o] += d2[o];
+      for (int i = 0; i < H; ++i) gW2[o * H + i] += d2[o] * a1[i];
+    }
+    for (int i = 0; i < H; ++i) {
+      double acc = 0;
+      for (int o = 0; o < H; ++o) acc += d2[o] * W2[o * H + i];
+      double s = 1.0 / (1.0 + std::exp(-z1[i]));
+      d1[i] = acc * (s * (1.0 + z1[i] * (1.0 - s)));
+    }
+    for (int o = 0; o < H; ++o) {
+      gb1[o] += d1[o];
+      for (int i = 0; i < D; ++i) gW1[o * D + i] += d1[o] * round_bf16(xp[i]);
+    }
+  }
+  return loss / (double)n;
+}
+
+// complex-step derivative of the same loss along a parameter direction v (pin for the backprop)
+double orc_mlp_loss_dir(int D, int H, const double* P, const double* v, int64_t n, const double* x,
+                        const double* t) {
+  int NPAR = H * D + H + H * H + H + H + 1;
+  std::vector<double> Pr(NPAR);
+  // complex parameters: evaluate with a complex copy
+  std::vector<cplx> Pc(NPAR);
+  for (int q = 0; q < NPAR; ++q) Pc[q] = cplx(P[q], CS_H * v[q]);
+  cplx L = 0;
+  for (int64_t p = 0; p < n; ++p) {
+    const cplx* W1 = Pc.data(); const cplx* b1 = W1 + H * D;
+    const cplx* W2 = b1 + H; const cplx* b2 = W2 + H * H;
+    const cplx* w3 = b2 + H; const cplx* b3 = w3 + H;
+    std::vector<cplx> a1(H), a2(H);
+    for (int o = 0; o < H; ++o) {
+      cplx z = b1[o];
+      for (int i = 0; i < D; ++i) z += W1[o * D + i] * round_bf16(x[p * D + i]);
+      a1[o] = rbf(silu(z));
+    }
+    for (int o = 0; o < H; ++o) {
+      cplx z = b2[o];
+      for (int i = 0; i < H; ++i) z += W2[o * H + i] * a1[i];
+      a2[o] = rbf(silu(z));
+    }
+    cplx y = b3[0];
+    for (int i = 0; i < H; ++i) y += w3[i] * a2[i];
+    cplx r = y - t[p];
+    L += r * r;
+  }
+  (void)Pr;
+  return (L / (double)n).imag() / CS_H;
+}
+
+}  // extern "C"

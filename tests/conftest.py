@@ -1,0 +1,30 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+
+
+@pytest.fixture(scope="session")
+def mech_dir(tmp_path_factory):
+    return str(tmp_path_factory.mktemp("mechs"))
+
+
+@pytest.fixture(scope="session")
+def mech_files(mech_dir):
+    """Synthetic workload mechanisms written once per session: {0: path, 1: path, 4: path}."""
+    from paper_2503_24286_gb300 import synth
+    out, objs = {}, {}
+    for i in (0, 1, 4):
+        m = synth.config_mechanism(i)
+        p = os.path.join(mech_dir, "mech%d.txt" % i)
+        synth.write_mechanism(m, p)
+        out[i], objs[i] = p, m
+    return out, objs
