@@ -1,0 +1,131 @@
+/* libpyro: GB300-native pointwise combustion thermochemistry (C ABI).
+ *
+ * The library evaluates, for millions of independent states, the
+ * thermochemistry of a detailed kinetic mechanism as formulated in the
+ * Pyrometheus paper (arXiv 2503.24286, Appendix A):
+ *   - temperature from mixture internal energy by Newton iteration on two-range
+ *     NASA-7 polynomials (Sec. A.3.1, Eq. int_energy, Eq. delta_temp, Eq. cv);
+ *   - species thermodynamics (Sec. A.1, Eq. nasa_poly, Eq. nasa_poly_c, Eq. gibbs);
+ *   - Arrhenius rate coefficients (Eq. rate_coeff) with third-body efficiencies
+ *     and Troe falloff, equilibrium constants from Gibbs energies
+ *     (Eq. equil_constants), mass-action rates of progress (Eq. reaction_rates)
+ *     and net production rates (Eq. production_rates);
+ *   - derivatives of the production rates (Eq. jacobian, Eq. chem_jacobian).
+ *
+ * Conventions for every entry point below:
+ *   - Units: SI with kmol (rho kg/m^3, T K, e J/kg, omega kmol/(m^3 s), p Pa).
+ *   - Arrays are FP64, structure-of-arrays with the point index fastest:
+ *     Y[k*n + p] for species k, point p (the species-major layout of the
+ *     paper's array inputs).  Per-point scalars are [n].
+ *   - Pointers may be device pointers (CUDA global memory of the device the
+ *     mechanism was loaded on) or host pointers.  With device pointers the call
+ *     is asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  With host pointers (all array arguments of the call on the host)
+ *     the library stages the data through its own device buffers, and the call
+ *     returns after the results have been copied back.  Mixed host/device
+ *     argument lists are rejected with PYRO_EINVAL.
+ *   - The caller owns all arrays; the library owns the mechanism handle, the
+ *     compiled module and its staging buffers.
+ *   - Return value: PYRO_OK (0) or a negative status; argument checks are made
+ *     before anything is launched.  pyro_last_error() gives the message of the
+ *     calling thread's last failure.
+ *   - n == 0 is a no-op that returns PYRO_OK.
+ */
+#ifndef PYRO_H
+#define PYRO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PYRO_OK 0
+#define PYRO_EINVAL (-1)   /* bad argument (null pointer, n < 0, mixed host/device) */
+#define PYRO_ECUDA (-2)    /* CUDA runtime/driver error */
+#define PYRO_ECOMPILE (-3) /* NVRTC compilation of the emitted kernels failed */
+#define PYRO_EMECH (-4)    /* mechanism file unreadable or fails validation */
+#define PYRO_ENOCONV (-5)  /* Newton iteration did not converge for some points */
+#define PYRO_ENOMLP (-6)   /* learned guess requested but no network is loaded */
+
+typedef struct pyro_mech pyro_mech;
+
+/* Load a mechanism file (text format "pyro-mech 1"), validate it (element
+ * balance of every reaction, positive Arrhenius factors, NASA ranges, cp/R > 1,
+ * Troe data), emit the mechanism-specialised CUDA C, compile it for sm_103a
+ * with NVRTC (cached on disk by source hash) and load it on the current device.
+ * options: NULL or "key=value;..." with keys
+ *   block=<threads per block, default 128>
+ *   newton=mixed|fp64   (mixed: FP32 Newton to |dT|<=1e-5 T, then FP64; fp64:
+ *                        FP64 Newton from the initial guess as in Sec. A.3.1)
+ *   cache=0|1           (on-disk cubin cache, default 1; dir $PYRO_CACHE_DIR)
+ *   checked=0|1         (1: calls that run Newton synchronise and return
+ *                        PYRO_ENOCONV if any point failed to converge)
+ * On success *out receives a handle to free with pyro_mech_free. */
+int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out);
+void pyro_mech_free(pyro_mech* mech);
+
+/* Sizes and molecular weights (host array of n_species doubles owned by the handle). */
+int pyro_mech_info(const pyro_mech* mech, int* n_species, int* n_reactions,
+                   const double** mol_weights);
+
+/* Static per-point FP64-pipe operation counts of the emitted kernels and other
+ * build facts, by name (e.g. "omega_fp64_flops_per_point").  PYRO_EINVAL if
+ * the key is unknown. */
+int pyro_mech_stat(const pyro_mech* mech, const char* key, double* value);
+
+/* The emitted CUDA C source (owned by the handle). */
+const char* pyro_mech_source(const pyro_mech* mech);
+
+/* Density from the equation of state p = rho R T / W, W = (sum Y_k/W_k)^-1
+ * (Sec. A.1 Eq. eos).  p, T: [n]; Y: [N][n]; rho: [n] out. */
+int pyro_density(const pyro_mech* mech, int64_t n, const double* p, const double* T,
+                 const double* Y, double* rho, void* stream);
+
+/* Mixture internal energy e = sum_k Y_k (h_k - R T)/W_k (Sec. A.3.1 Eq. int_energy)
+ * and, if cv != NULL, c_v = de/dT (Eq. cv).  T: [n]; Y: [N][n]; e, cv: [n] out. */
+int pyro_internal_energy(const pyro_mech* mech, int64_t n, const double* T, const double* Y,
+                         double* e, double* cv, void* stream);
+
+/* Temperature from internal energy by Newton iteration (Sec. A.3.1 Eq. delta_temp).
+ * e: [n]; Y: [N][n]; T_out: [n].
+ * guess_mode 0: start from T_guess[p] if T_guess != NULL, else 1200 K.
+ * guess_mode 1: start from the learned initial guess (BF16 MLP, see
+ *   pyro_mlp_load); PYRO_ENOMLP if none is loaded.
+ * Stops when |dT| <= 1e-10 T, then takes one more step; at most 50 FP64 steps.
+ * iters_out (nullable, int32 [n]): Newton steps taken, -1 where the stop rule
+ * was not met (T_out then holds the last iterate).  Non-convergence is also
+ * counted on the device; read it with pyro_nonconverged. */
+int pyro_temperature(const pyro_mech* mech, int64_t n, const double* e, const double* Y,
+                     const double* T_guess, int guess_mode, double* T_out, int32_t* iters_out,
+                     void* stream);
+
+/* Net production rates omega_k = sum_j nu_kj R_j (Sec. A.1 Eq. production_rates)
+ * with R_j by the law of mass action (Eq. reaction_rates).
+ * rho: [n]; T_or_e: [n] temperature, or internal energy if input_is_energy != 0
+ * (then T is solved first as in pyro_temperature from 1200 K and written to
+ * T_out, which must be non-NULL); Y: [N][n]; omega_out: [N][n]. */
+int pyro_net_production_rates(const pyro_mech* mech, int64_t n, const double* rho,
+                              const double* T_or_e, int input_is_energy, const double* Y,
+                              double* T_out, double* omega_out, void* stream);
+
+/* Points whose Newton solve failed since the last call (synchronises `stream`,
+ * then resets the device counter). */
+int pyro_nonconverged(const pyro_mech* mech, void* stream, int64_t* count);
+
+/* Diagnostic: the library's device exp (fn 0), log (fn 1) or reciprocal (fn 2)
+ * over x[n] -> y[n], for accuracy checks against a reference libm. */
+int pyro_math_eval(const pyro_mech* mech, int fn, int64_t n, const double* x, double* y,
+                   void* stream);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* pyro_last_error(void);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int pyro_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PYRO_H */

@@ -1,0 +1,200 @@
+"""Thin ctypes binding of the libpyro C ABI (``include/pyro.h``).
+
+Argument marshalling only: every step of the computation runs in the library's
+CUDA kernels.  Arrays may be torch CUDA tensors (device pointers, launched on
+torch's current stream) or numpy arrays (host pointers, staged by the library).
+All arrays are float64, contiguous, species-major: ``Y[k, p]``.
+
+There is no CPU fallback: if ``libpyro.so`` cannot be loaded the import of
+:func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "libpyro.so")
+
+PYRO_OK = 0
+PYRO_EINVAL = -1
+PYRO_ECUDA = -2
+PYRO_ECOMPILE = -3
+PYRO_EMECH = -4
+PYRO_ENOCONV = -5
+PYRO_ENOMLP = -6
+
+# every entry point declared in include/pyro.h
+EXPORTS = [
+    "pyro_mech_load", "pyro_mech_free", "pyro_mech_info", "pyro_mech_stat", "pyro_mech_source",
+    "pyro_density", "pyro_internal_energy", "pyro_temperature", "pyro_net_production_rates",
+    "pyro_nonconverged", "pyro_math_eval", "pyro_last_error", "pyro_version",
+]
+
+_lib = None
+
+
+class PyroError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("libpyro error %d: %s" % (code, msg))
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpyro.so is not built (run __graft_entry__.build() or "
+                               "python -m paper_2503_24286_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I64, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p
+        L.pyro_mech_load.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
+        L.pyro_mech_free.argtypes = [P]
+        L.pyro_mech_free.restype = None
+        L.pyro_mech_info.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]
+        L.pyro_mech_stat.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
+        L.pyro_mech_source.argtypes = [P]
+        L.pyro_mech_source.restype = ctypes.c_char_p
+        L.pyro_density.argtypes = [P, I64, D, D, D, D, P]
+        L.pyro_internal_energy.argtypes = [P, I64, D, D, D, D, P]
+        L.pyro_temperature.argtypes = [P, I64, D, D, D, ctypes.c_int, D, D, P]
+        L.pyro_net_production_rates.argtypes = [P, I64, D, D, ctypes.c_int, D, D, D, P]
+        L.pyro_nonconverged.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64)]
+        L.pyro_math_eval.argtypes = [P, ctypes.c_int, I64, D, D, P]
+        L.pyro_last_error.restype = ctypes.c_char_p
+        L.pyro_last_error.argtypes = []
+        L.pyro_version.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != PYRO_OK:
+        raise PyroError(rc, lib().pyro_last_error().decode())
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    """(pointer, is_device) of a float64/int32 contiguous array or None."""
+    if a is None:
+        return None, None
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), a.is_cuda
+    if not a.flags.c_contiguous:
+        raise ValueError("array must be C-contiguous")
+    return ctypes.c_void_p(a.ctypes.data), False
+
+
+def _stream(arrays):
+    dev = [a for a in arrays if a is not None and _is_torch(a) and a.is_cuda]
+    if dev:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream(dev[0].device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _empty_like(ref, shape, dtype="float64"):
+    if _is_torch(ref):
+        import torch
+        return torch.empty(shape, dtype=getattr(torch, dtype), device=ref.device)
+    return np.empty(shape, dtype=dtype)
+
+
+def _n(a) -> int:
+    return int(a.shape[-1])
+
+
+class Mechanism:
+    """A loaded, compiled mechanism (``pyro_mech_load``)."""
+
+    def __init__(self, path: str, options: Optional[str] = None):
+        L = lib()
+        h = ctypes.c_void_p()
+        _check(L.pyro_mech_load(path.encode(), options.encode() if options else None, ctypes.byref(h)))
+        self._h = h
+        ns, nr = ctypes.c_int(), ctypes.c_int()
+        W = ctypes.POINTER(ctypes.c_double)()
+        _check(L.pyro_mech_info(h, ctypes.byref(ns), ctypes.byref(nr), ctypes.byref(W)))
+        self.n_species, self.n_reactions = ns.value, nr.value
+        self.W = np.array([W[i] for i in range(ns.value)])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pyro_mech_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stat(self, key: str) -> float:
+        v = ctypes.c_double()
+        _check(lib().pyro_mech_stat(self._h, key.encode(), ctypes.byref(v)))
+        return v.value
+
+    def source(self) -> str:
+        return lib().pyro_mech_source(self._h).decode()
+
+    # --- entry points ---------------------------------------------------------
+    def density(self, p, T, Y, out=None):
+        out = _empty_like(T, (_n(T),)) if out is None else out
+        args = [p, T, Y, out]
+        _check(lib().pyro_density(self._h, _n(T), *[_ptr(a)[0] for a in args], _stream(args)))
+        return out
+
+    def internal_energy(self, T, Y, with_cv=False):
+        e = _empty_like(T, (_n(T),))
+        cv = _empty_like(T, (_n(T),)) if with_cv else None
+        args = [T, Y, e, cv]
+        _check(lib().pyro_internal_energy(self._h, _n(T), *[_ptr(a)[0] for a in args], _stream(args)))
+        return (e, cv) if with_cv else e
+
+    def temperature(self, e, Y, guess=None, learned=False, with_iters=False, out=None):
+        T = _empty_like(e, (_n(e),)) if out is None else out
+        it = _empty_like(e, (_n(e),), "int32") if with_iters else None
+        args = [e, Y, guess, T, it]
+        ptrs = [_ptr(a)[0] for a in args]
+        _check(lib().pyro_temperature(self._h, _n(e), ptrs[0], ptrs[1], ptrs[2], 1 if learned else 0,
+                                      ptrs[3], ptrs[4], _stream(args)))
+        return (T, it) if with_iters else T
+
+    def net_production_rates(self, rho, Y, T=None, e=None, T_out=None, out=None):
+        """omega [N, n] from (rho, T, Y), or from (rho, e, Y) with T solved (returns (omega, T))."""
+        if (T is None) == (e is None):
+            raise ValueError("give exactly one of T or e")
+        n = _n(rho)
+        w = _empty_like(rho, (self.n_species, n)) if out is None else out
+        energy = e is not None
+        if energy and T_out is None:
+            T_out = _empty_like(rho, (n,))
+        args = [rho, e if energy else T, Y, T_out if energy else None, w]
+        ptrs = [_ptr(a)[0] for a in args]
+        _check(lib().pyro_net_production_rates(self._h, n, ptrs[0], ptrs[1], 1 if energy else 0, ptrs[2],
+                                               ptrs[3], ptrs[4], _stream(args)))
+        return (w, T_out) if energy else w
+
+    def nonconverged(self, stream=None) -> int:
+        c = ctypes.c_int64()
+        _check(lib().pyro_nonconverged(self._h, stream or ctypes.c_void_p(0), ctypes.byref(c)))
+        return c.value
+
+    def math_eval(self, fn: int, x):
+        y = _empty_like(x, (_n(x),))
+        args = [x, y]
+        _check(lib().pyro_math_eval(self._h, int(fn), _n(x), *[_ptr(a)[0] for a in args], _stream(args)))
+        return y

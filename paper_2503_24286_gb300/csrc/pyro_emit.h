@@ -1,0 +1,28 @@
+// Emitter: mechanism -> mechanism-specialised CUDA C for sm_103a.
+#pragma once
+
+#include <map>
+#include <string>
+
+#include "pyro_mech.h"
+
+namespace pyro {
+
+struct EmitOptions {
+  int block = 128;            // threads per block (one point per thread)
+  int min_blocks = 2;         // __launch_bounds__ minimum resident blocks
+  bool mixed_newton = true;   // FP32 Newton to ~1e-5, then FP64 Newton (else FP64 only)
+};
+
+struct EmitResult {
+  std::string source;                     // CUDA C translation unit
+  std::map<std::string, double> stats;    // static FP64-pipe op counts per point etc.
+  int smem_dyn_bytes_omega = 0;           // dynamic shared memory of the omega kernel
+};
+
+EmitResult emit_module(const Mechanism& m, const EmitOptions& opt);
+
+// The device-math header text (embedded at build time).
+extern const char* kDeviceMathSource;
+
+}  // namespace pyro

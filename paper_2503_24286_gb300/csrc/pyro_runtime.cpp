@@ -1,0 +1,506 @@
+// libpyro C ABI: mechanism loading, NVRTC compilation with an on-disk cache,
+// module management through driver entry points, argument checks, host-pointer
+// staging and kernel launches.
+#include "pyro.h"
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "pyro_emit.h"
+#include "pyro_mech.h"
+
+using namespace pyro;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+// ---- driver entry points (resolved through the runtime; no link to libcuda) ----
+struct Driver {
+  decltype(&cuModuleLoadData) ModuleLoadData = nullptr;
+  decltype(&cuModuleUnload) ModuleUnload = nullptr;
+  decltype(&cuModuleGetFunction) ModuleGetFunction = nullptr;
+  decltype(&cuLaunchKernel) LaunchKernel = nullptr;
+  decltype(&cuFuncSetAttribute) FuncSetAttribute = nullptr;
+  decltype(&cuOccupancyMaxActiveBlocksPerMultiprocessor) Occupancy = nullptr;
+  decltype(&cuGetErrorString) GetErrorString = nullptr;
+  bool ok = false;
+  std::string err;
+};
+
+Driver& driver() {
+  static Driver d;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    auto get = [&](const char* name, void** fn) {
+      cudaDriverEntryPointQueryResult q;
+      cudaError_t e = cudaGetDriverEntryPointByVersion(name, fn, 12000, cudaEnableDefault, &q);
+      if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !*fn) {
+        d.err = std::string("driver entry point ") + name + " unavailable: " + cudaGetErrorString(e);
+        return false;
+      }
+      return true;
+    };
+    d.ok = get("cuModuleLoadData", (void**)&d.ModuleLoadData) &&
+           get("cuModuleUnload", (void**)&d.ModuleUnload) &&
+           get("cuModuleGetFunction", (void**)&d.ModuleGetFunction) &&
+           get("cuLaunchKernel", (void**)&d.LaunchKernel) &&
+           get("cuFuncSetAttribute", (void**)&d.FuncSetAttribute) &&
+           get("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void**)&d.Occupancy) &&
+           get("cuGetErrorString", (void**)&d.GetErrorString);
+  });
+  return d;
+}
+
+std::string cu_err(CUresult r) {
+  const char* s = nullptr;
+  if (driver().GetErrorString) driver().GetErrorString(r, &s);
+  return s ? s : ("CUresult " + std::to_string((int)r));
+}
+
+uint64_t fnv1a(const std::string& s, uint64_t h = 1469598103934665603ull) {
+  for (unsigned char c : s) { h ^= c; h *= 1099511628211ull; }
+  return h;
+}
+
+std::string cache_dir() {
+  const char* d = std::getenv("PYRO_CACHE_DIR");
+  if (d && *d) return d;
+  const char* x = std::getenv("XDG_CACHE_HOME");
+  std::string base = (x && *x) ? std::string(x) : std::string(std::getenv("HOME") ? std::getenv("HOME") : "/tmp") + "/.cache";
+  return base + "/pyro_gb300";
+}
+
+void mkdirs(const std::string& path) {
+  std::string cur;
+  std::stringstream ss(path);
+  std::string part;
+  if (!path.empty() && path[0] == '/') cur = "/";
+  while (std::getline(ss, part, '/')) {
+    if (part.empty()) continue;
+    cur += part + "/";
+    mkdir(cur.c_str(), 0755);
+  }
+}
+
+const char* kArch = "sm_103a";
+
+// Compile CUDA C to a cubin for sm_103a with NVRTC.
+bool nvrtc_compile(const std::string& src, std::vector<char>& cubin, std::string& log) {
+  nvrtcProgram prog;
+  const char* hdrs[] = {kDeviceMathSource};
+  const char* names[] = {"pyro_device_math.cuh"};
+  if (nvrtcCreateProgram(&prog, src.c_str(), "pyro_mech.cu", 1, hdrs, names) != NVRTC_SUCCESS) {
+    log = "nvrtcCreateProgram failed";
+    return false;
+  }
+  std::string arch = std::string("--gpu-architecture=") + kArch;
+  const char* opts[] = {arch.c_str(), "-std=c++17", "-lineinfo", "-default-device"};
+  nvrtcResult r = nvrtcCompileProgram(prog, 4, opts);
+  size_t ls = 0;
+  nvrtcGetProgramLogSize(prog, &ls);
+  log.assign(ls, '\0');
+  if (ls) nvrtcGetProgramLog(prog, &log[0]);
+  if (r != NVRTC_SUCCESS) { nvrtcDestroyProgram(&prog); return false; }
+  size_t cs = 0;
+  nvrtcGetCUBINSize(prog, &cs);
+  cubin.resize(cs);
+  nvrtcGetCUBIN(prog, cubin.data());
+  nvrtcDestroyProgram(&prog);
+  return true;
+}
+
+struct Options {
+  int block = 128;
+  bool mixed = true;
+  bool cache = true;
+  bool checked = false;
+  bool device = true;     // false: parse, validate, emit and compile only (no CUDA device needed)
+};
+
+bool parse_options(const char* s, Options& o, std::string& err) {
+  if (!s) return true;
+  std::string str(s);
+  for (char& c : str) if (c == ',') c = ';';
+  std::stringstream ss(str);
+  std::string kv;
+  while (std::getline(ss, kv, ';')) {
+    if (kv.empty()) continue;
+    size_t eq = kv.find('=');
+    if (eq == std::string::npos) { err = "option without '=': " + kv; return false; }
+    std::string k = kv.substr(0, eq), v = kv.substr(eq + 1);
+    if (k == "block") { o.block = std::atoi(v.c_str()); if (o.block < 32 || o.block > 512 || o.block % 32) { err = "block must be a multiple of 32 in [32, 512]"; return false; } }
+    else if (k == "newton") { if (v == "mixed") o.mixed = true; else if (v == "fp64") o.mixed = false; else { err = "newton=mixed|fp64"; return false; } }
+    else if (k == "cache") o.cache = v != "0";
+    else if (k == "checked") o.checked = v != "0";
+    else if (k == "device") o.device = v != "0";
+    else { err = "unknown option '" + k + "'"; return false; }
+  }
+  return true;
+}
+
+}  // namespace
+
+struct pyro_mech {
+  Mechanism m;
+  Options opt;
+  EmitResult emitted;
+  std::vector<double> W;
+  int device = -1;
+  int num_sms = 0;
+  CUmodule module = nullptr;
+  CUfunction f_omega = nullptr, f_temperature = nullptr, f_energy = nullptr, f_density = nullptr,
+             f_math = nullptr;
+  int omega_blocks_per_sm = 1;
+  unsigned long long* d_fail = nullptr;
+  // staging buffers for host-pointer calls
+  std::vector<void*> stage;
+  std::vector<size_t> stage_bytes;
+  std::mutex mu;
+};
+
+namespace {
+
+CUstream as_stream(void* s) { return (CUstream)s; }
+
+// where a pointer lives: 1 device-accessible, 0 host, -1 invalid
+int pointer_kind(const void* p) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) { cudaGetLastError(); return 0; }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 1;
+  return 0;
+}
+
+struct ArgSpec {
+  const void* host;     // caller pointer
+  size_t bytes;
+  bool in, out;
+};
+
+// Classify the non-null pointers of a call: returns 1 (all device), 0 (all host) or -1 (mixed).
+int classify(const std::vector<const void*>& ptrs) {
+  int kind = -2;
+  for (const void* p : ptrs) {
+    if (!p) continue;
+    int k = pointer_kind(p);
+    if (kind == -2) kind = k;
+    else if (kind != k) return -1;
+  }
+  return kind == -2 ? 1 : kind;
+}
+
+int ensure_stage(pyro_mech* h, size_t i, size_t bytes) {
+  if (h->stage.size() <= i) { h->stage.resize(i + 1, nullptr); h->stage_bytes.resize(i + 1, 0); }
+  if (h->stage_bytes[i] < bytes) {
+    if (h->stage[i]) cudaFree(h->stage[i]);
+    h->stage[i] = nullptr;
+    cudaError_t e = cudaMalloc(&h->stage[i], bytes);
+    if (e != cudaSuccess) { h->stage_bytes[i] = 0; return fail(PYRO_ECUDA, std::string("staging allocation: ") + cudaGetErrorString(e)); }
+    h->stage_bytes[i] = bytes;
+  }
+  return PYRO_OK;
+}
+
+// Run `launch(device pointers)` either directly (device pointers) or through
+// staging buffers (host pointers: copy in, launch, copy out, synchronise).
+template <class F>
+int with_args(pyro_mech* h, std::vector<ArgSpec> args, void* stream, F launch) {
+  std::vector<const void*> ptrs;
+  for (auto& a : args) ptrs.push_back(a.host);
+  int kind = classify(ptrs);
+  if (kind < 0) return fail(PYRO_EINVAL, "arrays must be all device pointers or all host pointers");
+  std::vector<void*> dev(args.size(), nullptr);
+  if (kind == 1) {
+    for (size_t i = 0; i < args.size(); ++i) dev[i] = const_cast<void*>(args[i].host);
+    return launch(dev);
+  }
+  std::lock_guard<std::mutex> lock(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  for (size_t i = 0; i < args.size(); ++i) {
+    if (!args[i].host) continue;
+    int rc = ensure_stage(h, i, args[i].bytes);
+    if (rc) return rc;
+    dev[i] = h->stage[i];
+    if (args[i].in) {
+      cudaError_t e = cudaMemcpyAsync(dev[i], args[i].host, args[i].bytes, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("H2D copy: ") + cudaGetErrorString(e));
+    }
+  }
+  int rc = launch(dev);
+  if (rc) return rc;
+  for (size_t i = 0; i < args.size(); ++i) {
+    if (!args[i].host || !args[i].out) continue;
+    cudaError_t e = cudaMemcpyAsync(const_cast<void*>(args[i].host), dev[i], args[i].bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("D2H copy: ") + cudaGetErrorString(e));
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("stream synchronize: ") + cudaGetErrorString(e));
+  return PYRO_OK;
+}
+
+int check_device(const pyro_mech* h) {
+  if (!h->module) return fail(PYRO_EINVAL, "mechanism handle was loaded with device=0 (compile only)");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(PYRO_ECUDA, "cudaGetDevice failed");
+  if (dev != h->device) return fail(PYRO_EINVAL, "mechanism was loaded on device " + std::to_string(h->device) +
+                                                   " but the current device is " + std::to_string(dev));
+  return PYRO_OK;
+}
+
+int launch(const pyro_mech* h, CUfunction f, int64_t n, int blocks_per_sm, unsigned smem, void* stream,
+           void** params) {
+  int64_t need = (n + h->opt.block - 1) / h->opt.block;
+  int64_t cap = (int64_t)h->num_sms * blocks_per_sm;
+  unsigned grid = (unsigned)(need < cap ? need : cap);
+  if (grid == 0) return PYRO_OK;
+  CUresult r = driver().LaunchKernel(f, grid, 1, 1, h->opt.block, 1, 1, smem, as_stream(stream), params, nullptr);
+  if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
+  return PYRO_OK;
+}
+
+int maybe_checked(const pyro_mech* h, void* stream) {
+  if (!h->opt.checked) return PYRO_OK;
+  int64_t c = 0;
+  int rc = pyro_nonconverged(const_cast<pyro_mech*>(h), stream, &c);
+  if (rc) return rc;
+  if (c) return fail(PYRO_ENOCONV, std::to_string(c) + " point(s) did not converge in the Newton solve");
+  return PYRO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pyro_last_error(void) { return g_last_error.c_str(); }
+
+int pyro_version(void) { return 100; }
+
+int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) {
+  if (!mech_path || !out) return fail(PYRO_EINVAL, "null argument");
+  *out = nullptr;
+  auto* h = new pyro_mech();
+  std::string err;
+  if (!parse_options(options, h->opt, err)) { delete h; return fail(PYRO_EINVAL, err); }
+  if (!parse_mechanism_file(mech_path, h->m, err)) { delete h; return fail(PYRO_EMECH, err); }
+  if (!validate_mechanism(h->m, err)) { delete h; return fail(PYRO_EMECH, err); }
+  for (auto& s : h->m.species) h->W.push_back(s.W);
+  EmitOptions eo;
+  eo.block = h->opt.block;
+  eo.min_blocks = h->opt.block <= 64 ? 4 : (h->opt.block <= 128 ? 2 : 1);
+  eo.mixed_newton = h->opt.mixed;
+  h->emitted = emit_module(h->m, eo);
+
+  // compile (or fetch from the cache)
+  int nv_major = 0, nv_minor = 0;
+  nvrtcVersion(&nv_major, &nv_minor);
+  std::string key_src = h->emitted.source + std::string(kDeviceMathSource) + kArch + std::to_string(nv_major) + "." + std::to_string(nv_minor);
+  char hex[32];
+  std::snprintf(hex, sizeof hex, "%016llx", (unsigned long long)fnv1a(key_src));
+  std::string dir = cache_dir(), path = dir + "/pyro_" + hex + ".cubin";
+  std::vector<char> cubin;
+  if (h->opt.cache) {
+    std::ifstream f(path, std::ios::binary);
+    if (f) cubin.assign(std::istreambuf_iterator<char>(f), std::istreambuf_iterator<char>());
+  }
+  if (cubin.empty()) {
+    std::string log;
+    if (!nvrtc_compile(h->emitted.source, cubin, log)) { delete h; return fail(PYRO_ECOMPILE, "NVRTC: " + log); }
+    if (h->opt.cache) {
+      mkdirs(dir);
+      std::string tmp = path + ".tmp" + std::to_string((long)getpid());
+      std::ofstream f(tmp, std::ios::binary);
+      f.write(cubin.data(), (std::streamsize)cubin.size());
+      f.close();
+      std::rename(tmp.c_str(), path.c_str());
+    }
+  }
+  h->emitted.stats["cubin_bytes"] = (double)cubin.size();
+  if (!h->opt.device) { *out = h; return PYRO_OK; }
+  Driver& d = driver();
+  if (!d.ok) { delete h; return fail(PYRO_ECUDA, d.err); }
+  cudaError_t ce = cudaFree(0);   // make sure a context is current
+  if (ce != cudaSuccess) { delete h; return fail(PYRO_ECUDA, std::string("CUDA init: ") + cudaGetErrorString(ce)); }
+  cudaGetDevice(&h->device);
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
+  if (major * 10 + minor != 103) {
+    delete h;
+    return fail(PYRO_ECUDA, "libpyro is built for sm_103a (GB300); device has sm_" + std::to_string(major * 10 + minor));
+  }
+
+  CUresult r = d.ModuleLoadData(&h->module, cubin.data());
+  if (r != CUDA_SUCCESS) { delete h; return fail(PYRO_ECUDA, "cuModuleLoadData: " + cu_err(r)); }
+  struct { const char* name; CUfunction* f; } fns[] = {
+      {"pyro_omega", &h->f_omega}, {"pyro_temperature", &h->f_temperature}, {"pyro_energy", &h->f_energy},
+      {"pyro_density", &h->f_density}, {"pyro_math", &h->f_math}};
+  for (auto& q : fns) {
+    r = d.ModuleGetFunction(q.f, h->module, q.name);
+    if (r != CUDA_SUCCESS) { pyro_mech_free(h); return fail(PYRO_ECUDA, std::string("missing kernel ") + q.name); }
+  }
+  int smem = h->emitted.smem_dyn_bytes_omega;
+  r = d.FuncSetAttribute(h->f_omega, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem);
+  if (r != CUDA_SUCCESS) { pyro_mech_free(h); return fail(PYRO_ECUDA, "shared memory request of " + std::to_string(smem) + " B: " + cu_err(r)); }
+  int nb = 0;
+  r = d.Occupancy(&nb, h->f_omega, h->opt.block, smem);
+  if (r != CUDA_SUCCESS || nb < 1) { pyro_mech_free(h); return fail(PYRO_ECUDA, "omega kernel does not fit on an SM"); }
+  h->omega_blocks_per_sm = nb;
+  h->emitted.stats["omega_blocks_per_sm"] = nb;
+  if (cudaMalloc(&h->d_fail, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(h->d_fail, 0, sizeof(unsigned long long)) != cudaSuccess) {
+    pyro_mech_free(h);
+    return fail(PYRO_ECUDA, "failure counter allocation");
+  }
+  *out = h;
+  return PYRO_OK;
+}
+
+void pyro_mech_free(pyro_mech* h) {
+  if (!h) return;
+  if (h->module && driver().ModuleUnload) driver().ModuleUnload(h->module);
+  if (h->d_fail) cudaFree(h->d_fail);
+  for (void* p : h->stage) if (p) cudaFree(p);
+  delete h;
+}
+
+int pyro_mech_info(const pyro_mech* h, int* ns, int* nr, const double** W) {
+  if (!h) return fail(PYRO_EINVAL, "null mechanism");
+  if (ns) *ns = h->m.n_species();
+  if (nr) *nr = h->m.n_reactions();
+  if (W) *W = h->W.data();
+  return PYRO_OK;
+}
+
+int pyro_mech_stat(const pyro_mech* h, const char* key, double* value) {
+  if (!h || !key || !value) return fail(PYRO_EINVAL, "null argument");
+  auto it = h->emitted.stats.find(key);
+  if (it == h->emitted.stats.end()) return fail(PYRO_EINVAL, std::string("unknown stat '") + key + "'");
+  *value = it->second;
+  return PYRO_OK;
+}
+
+const char* pyro_mech_source(const pyro_mech* h) { return h ? h->emitted.source.c_str() : ""; }
+
+int pyro_density(const pyro_mech* hc, int64_t n, const double* p, const double* T, const double* Y,
+                 double* rho, void* stream) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n < 0 || (n > 0 && (!p || !T || !Y || !rho))) return fail(PYRO_EINVAL, "pyro_density: bad arguments");
+  if (n == 0) return PYRO_OK;
+  if (int rc = check_device(h)) return rc;
+  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species();
+  return with_args(h, {{p, s1, true, false}, {T, s1, true, false}, {Y, sN, true, false}, {rho, s1, false, true}},
+                   stream, [&](std::vector<void*>& d) {
+                     long long nn = n;
+                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3]};
+                     return launch(h, h->f_density, n, 8, 0, stream, params);
+                   });
+}
+
+int pyro_internal_energy(const pyro_mech* hc, int64_t n, const double* T, const double* Y, double* e,
+                         double* cv, void* stream) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n < 0 || (n > 0 && (!T || !Y || !e))) return fail(PYRO_EINVAL, "pyro_internal_energy: bad arguments");
+  if (n == 0) return PYRO_OK;
+  if (int rc = check_device(h)) return rc;
+  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species();
+  return with_args(h, {{T, s1, true, false}, {Y, sN, true, false}, {e, s1, false, true}, {cv, s1, false, true}},
+                   stream, [&](std::vector<void*>& d) {
+                     long long nn = n;
+                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3]};
+                     return launch(h, h->f_energy, n, 8, 0, stream, params);
+                   });
+}
+
+int pyro_temperature(const pyro_mech* hc, int64_t n, const double* e, const double* Y, const double* T_guess,
+                     int guess_mode, double* T_out, int32_t* iters, void* stream) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n < 0 || (n > 0 && (!e || !Y || !T_out))) return fail(PYRO_EINVAL, "pyro_temperature: bad arguments");
+  if (guess_mode != 0 && guess_mode != 1) return fail(PYRO_EINVAL, "guess_mode must be 0 or 1");
+  if (guess_mode == 1) return fail(PYRO_ENOMLP, "no learned initial guess is loaded");
+  if (n == 0) return PYRO_OK;
+  if (int rc = check_device(h)) return rc;
+  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species(), si = n * sizeof(int32_t);
+  int rc = with_args(h, {{e, s1, true, false}, {Y, sN, true, false}, {T_guess, s1, true, false},
+                         {T_out, s1, false, true}, {iters, si, false, true}},
+                     stream, [&](std::vector<void*>& d) {
+                       long long nn = n;
+                       double Tg = 1200.0, tol = 1e-10;
+                       int max_iter = 50;
+                       void* params[] = {&nn, &d[0], &d[1], &d[2], &Tg, &max_iter, &tol, &d[3], &d[4], &h->d_fail};
+                       return launch(h, h->f_temperature, n, 8, 0, stream, params);
+                     });
+  if (rc) return rc;
+  return maybe_checked(h, stream);
+}
+
+int pyro_net_production_rates(const pyro_mech* hc, int64_t n, const double* rho, const double* T_or_e,
+                              int input_is_energy, const double* Y, double* T_out, double* omega,
+                              void* stream) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n < 0 || (n > 0 && (!rho || !T_or_e || !Y || !omega)))
+    return fail(PYRO_EINVAL, "pyro_net_production_rates: bad arguments");
+  if (input_is_energy && !T_out) return fail(PYRO_EINVAL, "T_out is required when input_is_energy != 0");
+  if (n == 0) return PYRO_OK;
+  if (int rc = check_device(h)) return rc;
+  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species();
+  int rc = with_args(h, {{rho, s1, true, false}, {T_or_e, s1, true, false}, {Y, sN, true, false},
+                         {input_is_energy ? T_out : nullptr, s1, false, true}, {omega, sN, false, true}},
+                     stream, [&](std::vector<void*>& d) {
+                       long long nn = n;
+                       int em = input_is_energy ? 1 : 0;
+                       double Tg = 1200.0, tol = 1e-10;
+                       int max_iter = 50;
+                       void* params[] = {&nn, &d[0], &d[1], &em, &d[2], &d[3], &d[4], &Tg, &max_iter, &tol, &h->d_fail};
+                       return launch(h, h->f_omega, n, h->omega_blocks_per_sm, h->emitted.smem_dyn_bytes_omega,
+                                     stream, params);
+                     });
+  if (rc) return rc;
+  return input_is_energy ? maybe_checked(h, stream) : PYRO_OK;
+}
+
+int pyro_nonconverged(const pyro_mech* hc, void* stream, int64_t* count) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || !count) return fail(PYRO_EINVAL, "null argument");
+  unsigned long long v = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&v, h->d_fail, sizeof v, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemsetAsync(h->d_fail, 0, sizeof v, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(PYRO_ECUDA, "reading the failure counter");
+  *count = (int64_t)v;
+  return PYRO_OK;
+}
+
+int pyro_math_eval(const pyro_mech* hc, int fn, int64_t n, const double* x, double* y, void* stream) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n < 0 || fn < 0 || fn > 2 || (n > 0 && (!x || !y))) return fail(PYRO_EINVAL, "pyro_math_eval: bad arguments");
+  if (n == 0) return PYRO_OK;
+  if (int rc = check_device(h)) return rc;
+  size_t s1 = n * sizeof(double);
+  return with_args(h, {{x, s1, true, false}, {y, s1, false, true}}, stream, [&](std::vector<void*>& d) {
+    long long nn = n;
+    void* params[] = {&fn, &nn, &d[0], &d[1]};
+    return launch(h, h->f_math, n, 8, 0, stream, params);
+  });
+}
+
+}  // extern "C"
