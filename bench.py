@@ -1,0 +1,315 @@
+"""Throughput benchmark of the pointwise thermochemistry hot path on GB300.
+
+One step = one pass of the whole path over one batch resident in HBM: the
+temperature from internal energy by Newton iteration, then species thermo,
+rate and equilibrium constants, rates of progress and net production rates,
+on the synthetic 53-species / 325-reaction mechanism at 2^22 states (FP64).
+The batch (1.85 GB of inputs) is far larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun with one rank per GPU; each rank evaluates its own
+2^22 states (points are independent: weak scaling, no collective on the data
+path); the step time is the maximum over ranks.  --impl reference times the CPU
+oracle on the host cores on bounded samples of the same workload.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "state-evals/sec (T solve + omega_k, FP64)"
+CONFIG_INDEX = 1
+# FP64 pipe of GB300: 2 DFMA lanes per SM per clock (measured by a DFMA
+# microbenchmark: 2.07 lanes/SM/clk), 152 SMs, 2070 MHz maximum SM clock.
+FP64_LANES_PER_SM = 2
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_GFLOPS = 2.0 * FP64_LANES_PER_SM * N_SM * SM_MAX_MHZ / 1e3   # 1258.6 GFLOP/s (DFMA = 2 flops)
+
+# DRAM traffic of one launch of the timed kernel, from an ncu capture of this
+# kernel source (hash of the emitted source); None once the kernel changes.
+PROFILED_TRAFFIC = {
+    # 2^19-state ncu capture scaled by 8 to a 2^22-state launch (profiles/pyro_omega_gri53_energy.md)
+    "953a6879ca9d63b7": 3.334e9,
+}
+
+
+def _dist():
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            import torch
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            dist.init_process_group(backend)
+        return dist
+    return None
+
+
+def rank_world():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    dist = _dist()
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    dist = _dist()
+    if dist is not None:
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = tempfile.TemporaryFile(mode="w+")
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        mx = float(rows[0][2])
+        load = [s for s in sm if s > 0.5 * mx] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+def workload_config(n: int) -> dict:
+    cfg = {"workload": "synthetic GRI-sized mechanism, 53 species / 325 reactions (30 third-body, 25 Troe, "
+                       "28 duplicate pairs); %d states/step; T from internal energy by Newton + omega_k" % n,
+           "mechanism_seed": 2503 + CONFIG_INDEX, "state_seed": 24286 + CONFIG_INDEX,
+           "T_K": [300, 2800], "p_atm": [0.5, 20], "Y": "Dirichlet(0.5)",
+           "n_points": n, "layout": "SoA [species][point] FP64",
+           "l2": "inputs 1.85 GB/step > 129 MB L2 (no flush needed)"}
+    return cfg
+
+
+def cpu_oracle_rate(path: str, n: int, seed_offset: int = 0):
+    """States/s of the CPU oracle (T solve + omega) on an n-point sample of the workload."""
+    from oracle import oracle as O
+    from paper_2503_24286_gb300 import synth
+    O.build()
+    orc = O.Oracle(path)
+    st = synth.config_states(CONFIG_INDEX, n=n, offset_seed=100 + seed_offset)
+    rho = orc.density(st.p, st.T, st.Y)
+    e = orc.internal_energy(st.T, st.Y)
+    t0 = time.perf_counter()
+    T, _, _ = orc.temperature(e, st.Y)
+    orc.net_production_rates(rho, T, st.Y)
+    dt = time.perf_counter() - t0
+    return n / dt, O.threads(), dt
+
+
+def run_reference(args):
+    rank, world = rank_world()
+    if rank != 0:
+        return 0
+    from paper_2503_24286_gb300 import synth
+    d = tempfile.mkdtemp()
+    path = os.path.join(d, "mech.txt")
+    synth.write_mechanism(synth.config_mechanism(CONFIG_INDEX), path)
+    n = args.ref_sample
+    for i in range(args.warmup):
+        cpu_oracle_rate(path, min(n, 4096), i)
+    times = []
+    cores = 1
+    for i in range(args.steps):
+        rate, cores, dt = cpu_oracle_rate(path, n, 1000 + i)
+        times.append(dt)
+    tot = sum(times)
+    value = n * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "states/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(n),
+            "cpu_baseline": {"value": value, "unit": "states/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d states per step of the same workload (seeded), plain FP64 C++ oracle, "
+                                       "OpenMP over points" % n},
+            "e2e": {"value": value, "unit": "states/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2503_24286_gb300 import binding as B
+    from paper_2503_24286_gb300 import build as BLD
+    from paper_2503_24286_gb300 import synth
+
+    rank, world = rank_world()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        BLD.build()
+    barrier()
+    BLD.build()
+    d = tempfile.mkdtemp()
+    path = os.path.join(d, "mech.txt")
+    synth.write_mechanism(synth.config_mechanism(CONFIG_INDEX), path)
+    mech = B.Mechanism(path)
+    n = args.points
+    cfgd = synth.CONFIGS[CONFIG_INDEX]
+    T0, p, Y = synth.generate_states_torch(53, n, cfgd["T"], cfgd["p_atm"],
+                                           synth.STATE_SEED_BASE + CONFIG_INDEX + 7919 * rank, dev)
+    rho = mech.density(p, T0, Y)
+    e = mech.internal_energy(T0, Y)
+    del p
+    omega = torch.empty((53, n), dtype=torch.float64, device=dev)
+    T = torch.empty(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        mech.net_production_rates(rho, Y, e=e, T_out=T, out=omega)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    assert mech.nonconverged() == 0
+    # Newton statistics of this batch (not timed)
+    _, iters = mech.temperature(e, Y, with_iters=True)
+    iters_mean = float(iters.double().mean().item())
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms_max = max_over_ranks(ms, dev)
+    launches = args.steps          # one fused kernel launch per step
+    value = world * n / (ms_max * 1e-3)
+
+    # --- end to end through the C ABI with host buffers (pinned) -------------------
+    h_rho = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    h_e = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    h_Y = torch.empty((53, n), dtype=torch.float64, pin_memory=True)
+    h_rho.copy_(rho); h_e.copy_(e); h_Y.copy_(Y)
+    h_T = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    h_w = torch.empty((53, n), dtype=torch.float64, pin_memory=True)
+    a_rho, a_e, a_Y, a_T, a_w = (x.numpy() for x in (h_rho, h_e, h_Y, h_T, h_w))
+    e2e_steps = max(2, min(args.steps, 5))
+    mech.net_production_rates(a_rho, a_Y, e=a_e, T_out=a_T, out=a_w)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        mech.net_production_rates(a_rho, a_Y, e=a_e, T_out=a_T, out=a_w)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
+    h2d = (n + n + 53 * n) * 8
+    d2h = (53 * n + n) * 8
+
+    # --- roofline of the timed kernel ---------------------------------------------------
+    flops_fwd = mech.stat("omega_fp64_flops_per_point")
+    flops_ts = 2 * mech.stat("tsolve_collapse_fp64_ops") + 3 * 2 * mech.stat("tsolve_iter_fp64_ops_mixed")
+    flops_pt = flops_fwd + flops_ts
+    achieved = flops_pt * n / (ms * 1e-3) / 1e9
+    src_hash = hashlib.sha256(mech.source().encode()).hexdigest()[:16]
+    traffic = PROFILED_TRAFFIC.get(src_hash)
+    clocks = clk.summary()
+
+    line = None
+    if rank == 0:
+        rate_cpu, cores, dt = cpu_oracle_rate(path, args.cpu_sample)
+        line = {"metric": METRIC, "value": value, "unit": "states/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(n),
+                "parallelism": "points sharded across ranks, no collective" if world > 1 else "1 GPU",
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                             "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
+                             "peak_source": "FP64 pipe: 2 lanes/SM/clk x 152 SMs x 2070 MHz x 2 flops/DFMA",
+                             "flops_per_state": flops_pt,
+                             "frac_at_sampled_clock": (achieved / (FP64_PEAK_GFLOPS * clocks["sm_mhz"] / SM_MAX_MHZ)
+                                                       if clocks.get("sm_mhz") else None)},
+                "cpu_baseline": {"value": rate_cpu, "unit": "states/s", "cores": cores, "kind": "oracle",
+                                 "sample": "%d states of the same workload (seeded), T solve + omega, %.1f s"
+                                           % (args.cpu_sample, dt)},
+                "e2e": {"value": world * n / e2e_s, "unit": "states/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches,
+                "clocks": clocks,
+                "newton_iters_mean": iters_mean,
+                "kernel_source_hash": src_hash,
+                "kernel": "pyro_omega (fused Newton T(e,Y) + omega), %d threads/block, %d blocks/SM"
+                          % (int(mech.stat("block")), int(mech.stat("omega_blocks_per_sm")))}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--points", type=int, default=2 ** 22)
+    ap.add_argument("--cpu-sample", type=int, default=2 ** 17)
+    ap.add_argument("--ref-sample", type=int, default=2 ** 15)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rc = run_reference(args) if args.impl == "reference" else run_ours(args)
+    dist = _dist()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,100 @@
+"""Host-side checks of libpyro that need no GPU: the library loads, exports every
+symbol declared in include/pyro.h, parses and validates mechanisms, emits and
+compiles (NVRTC, sm_103a) the specialised kernels, and rejects bad input."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2503_24286_gb300 import binding as B
+from paper_2503_24286_gb300 import build as BLD
+from paper_2503_24286_gb300 import synth
+from tests import handmech
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built(tmp_path_factory):
+    os.environ.setdefault("PYRO_CACHE_DIR", str(tmp_path_factory.mktemp("jit")))
+    BLD.build()
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(pyro_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(B.LIB_PATH)
+    declared = _declared()
+    assert {"pyro_mech_load", "pyro_temperature", "pyro_net_production_rates"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(B.EXPORTS) == declared
+    assert B.lib().pyro_version() >= 100
+
+
+def test_compile_only_handle_and_static_counts(mech_files):
+    paths, objs = mech_files
+    m = B.Mechanism(paths[0], "device=0")
+    assert (m.n_species, m.n_reactions) == (10, 21)
+    W = [sum(c * synth.ATOMIC_WEIGHTS[e] for e, c in s.composition.items()) for s in objs[0].species]
+    assert m.W == pytest.approx(W, rel=1e-15)
+    assert m.stat("omega_fp64_flops_per_point") > 0
+    assert m.stat("cubin_bytes") > 1000
+    src = m.source()
+    assert "pyro_omega" in src and "pyro_tsolve" in src
+    # a compile-only handle cannot launch
+    import numpy as np
+    with pytest.raises(B.PyroError) as ei:
+        m.internal_energy(np.ones(4), np.ones((10, 4)) / 10)
+    assert ei.value.code == B.PYRO_EINVAL
+
+
+def test_unbalanced_mechanism_is_rejected(tmp_path):
+    mech = handmech.abcd_mechanism()
+    mech.reactions[0].products = [(2, 1), (3, 2)]      # H + O2 -> OH + 2 O : O not balanced
+    p = handmech.write(mech, str(tmp_path), "bad.txt")
+    with pytest.raises(B.PyroError) as ei:
+        B.Mechanism(p, "device=0")
+    assert ei.value.code == B.PYRO_EMECH
+    assert "balanced" in str(ei.value)
+
+
+def test_missing_file_and_bad_options(tmp_path, mech_files):
+    with pytest.raises(B.PyroError) as ei:
+        B.Mechanism(str(tmp_path / "nope.txt"), "device=0")
+    assert ei.value.code == B.PYRO_EMECH
+    with pytest.raises(B.PyroError) as ei:
+        B.Mechanism(mech_files[0][0], "device=0;block=33")
+    assert ei.value.code == B.PYRO_EINVAL
+    with pytest.raises(B.PyroError) as ei:
+        B.Mechanism(mech_files[0][0], "device=0;frobnicate=1")
+    assert ei.value.code == B.PYRO_EINVAL
+
+
+def test_cp_margin_validation(tmp_path):
+    mech = handmech.abcd_mechanism()
+    mech.species[0].nasa_low[0] = 0.5          # cp/R = 0.5 < 1: c_v < 0
+    mech.species[0].nasa_high[0] = 0.5
+    p = handmech.write(mech, str(tmp_path), "cp.txt")
+    with pytest.raises(B.PyroError) as ei:
+        B.Mechanism(p, "device=0")
+    assert ei.value.code == B.PYRO_EMECH
+
+
+def test_null_and_negative_arguments_rejected(mech_files):
+    L = B.lib()
+    h = ctypes.c_void_p()
+    assert L.pyro_mech_load(None, None, ctypes.byref(h)) == B.PYRO_EINVAL
+    m = B.Mechanism(mech_files[0][0], "device=0")
+    assert L.pyro_density(m.handle, -1, None, None, None, None, None) == B.PYRO_EINVAL
+    assert L.pyro_temperature(m.handle, 4, None, None, None, 0, None, None, None) == B.PYRO_EINVAL
+    # n == 0 is a no-op even without pointers
+    assert L.pyro_net_production_rates(m.handle, 0, None, None, 0, None, None, None, None) == B.PYRO_OK
