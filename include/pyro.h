@@ -109,6 +109,33 @@ int pyro_net_production_rates(const pyro_mech* mech, int64_t n, const double* rh
                               const double* T_or_e, int input_is_energy, const double* Y,
                               double* T_out, double* omega_out, void* stream);
 
+/* Net production rates for callers that cannot allocate device memory.
+ * No counterpart in the paper: this is a deployment variant of
+ * pyro_net_production_rates.  Some callers cannot call cudaMalloc while they
+ * evaluate the chemistry -- for example a solver whose memory pool already
+ * holds the whole device, or a time-step loop that must not take cudaMalloc's
+ * device-wide synchronisation -- and the host-pointer path above allocates
+ * staging buffers.  This entry point allocates nothing: the arrays (host or
+ * device pointers, same layout and meaning as pyro_net_production_rates) and
+ * the Newton failure counter are staged through one fixed scratch array of
+ * PYRO_NOALLOC_SCRATCH_BYTES that the library holds, as a static device
+ * variable, on every GPU that loads it, until the process exits.
+ *  - Limit: the staged arrays need about 8 (2N + 3) bytes per state (N
+ *    species), so one call takes at most ~32 MiB / (8 (2N + 3)) states
+ *    (about 38 000 for 53 species); larger n returns PYRO_EINVAL with a message
+ *    giving the limit.
+ *  - The first call on a device looks up the scratch address on that device
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call on a device shares the one scratch array, which keeps the
+ *    previous call's contents (the failure counter is cleared by each call):
+ *    calls that overlap on the GPU (other streams, other host threads) race.
+ *  - The call is synchronous (returns after the results are copied out) and
+ *    returns PYRO_ENOCONV if a Newton solve failed (input_is_energy != 0). */
+#define PYRO_NOALLOC_SCRATCH_BYTES (32u << 20)
+int pyro_net_production_rates_noalloc(const pyro_mech* mech, int64_t n, const double* rho,
+                                      const double* T_or_e, int input_is_energy, const double* Y,
+                                      double* T_out, double* omega_out, void* stream);
+
 /* Points whose Newton solve failed since the last call (synchronises `stream`,
  * then resets the device counter). */
 int pyro_nonconverged(const pyro_mech* mech, void* stream, int64_t* count);

@@ -32,6 +32,7 @@ EXPORTS = [
     "pyro_mech_load", "pyro_mech_free", "pyro_mech_info", "pyro_mech_stat", "pyro_mech_source",
     "pyro_density", "pyro_internal_energy", "pyro_temperature", "pyro_net_production_rates",
     "pyro_nonconverged", "pyro_math_eval", "pyro_last_error", "pyro_version",
+    "pyro_net_production_rates_noalloc",
 ]
 
 _lib = None
@@ -63,6 +64,7 @@ def lib() -> ctypes.CDLL:
         L.pyro_internal_energy.argtypes = [P, I64, D, D, D, D, P]
         L.pyro_temperature.argtypes = [P, I64, D, D, D, ctypes.c_int, D, D, P]
         L.pyro_net_production_rates.argtypes = [P, I64, D, D, ctypes.c_int, D, D, D, P]
+        L.pyro_net_production_rates_noalloc.argtypes = [P, I64, D, D, ctypes.c_int, D, D, D, P]
         L.pyro_nonconverged.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64)]
         L.pyro_math_eval.argtypes = [P, ctypes.c_int, I64, D, D, P]
         L.pyro_last_error.restype = ctypes.c_char_p
@@ -186,6 +188,22 @@ class Mechanism:
         ptrs = [_ptr(a)[0] for a in args]
         _check(lib().pyro_net_production_rates(self._h, n, ptrs[0], ptrs[1], 1 if energy else 0, ptrs[2],
                                                ptrs[3], ptrs[4], _stream(args)))
+        return (w, T_out) if energy else w
+
+    def net_production_rates_noalloc(self, rho, Y, T=None, e=None, T_out=None, out=None):
+        """As :meth:`net_production_rates`, through the entry point that allocates no
+        device memory (fixed scratch; synchronous; bounded number of states per call)."""
+        if (T is None) == (e is None):
+            raise ValueError("give exactly one of T or e")
+        n = _n(rho)
+        w = _empty_like(rho, (self.n_species, n)) if out is None else out
+        energy = e is not None
+        if energy and T_out is None:
+            T_out = _empty_like(rho, (n,))
+        args = [rho, e if energy else T, Y, T_out if energy else None, w]
+        ptrs = [_ptr(a)[0] for a in args]
+        _check(lib().pyro_net_production_rates_noalloc(self._h, n, ptrs[0], ptrs[1], 1 if energy else 0,
+                                                       ptrs[2], ptrs[3], ptrs[4], _stream(args)))
         return (w, T_out) if energy else w
 
     def nonconverged(self, stream=None) -> int:

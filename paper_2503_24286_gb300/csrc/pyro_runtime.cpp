@@ -504,3 +504,30 @@ int pyro_math_eval(const pyro_mech* hc, int fn, int64_t n, const double* x, doub
 }
 
 }  // extern "C"
+
+// ---- internal helpers (not part of the C ABI) -------------------------------
+#include "pyro_internal.h"
+
+namespace pyro {
+
+int internal_n_species(const pyro_mech* h) { return h ? h->m.n_species() : 0; }
+
+int internal_check_device(const pyro_mech* h) {
+  if (!h) return fail(PYRO_EINVAL, "null mechanism");
+  return check_device(h);
+}
+
+int internal_fail(int code, const char* msg) { return fail(code, msg); }
+
+int internal_launch_omega(const pyro_mech* h, int64_t n, const void* rho, const void* T_or_e,
+                          int input_is_energy, const void* Y, void* T_out, void* omega,
+                          unsigned long long* fail_ctr, void* stream) {
+  long long nn = n;
+  int em = input_is_energy ? 1 : 0;
+  double Tg = 1200.0, tol = 1e-10;
+  int max_iter = 50;
+  void* params[] = {&nn, &rho, &T_or_e, &em, &Y, &T_out, &omega, &Tg, &max_iter, &tol, &fail_ctr};
+  return launch(h, h->f_omega, n, h->omega_blocks_per_sm, h->emitted.smem_dyn_bytes_omega, stream, params);
+}
+
+}  // namespace pyro
