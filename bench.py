@@ -180,6 +180,50 @@ def run_reference(args):
     return 0
 
 
+
+def derivative_rates(mech, synth, dev, stream, args, rank):
+    """Jacobian-evals/s and JVP/VJP states/s on 2^20 resident states of the same mechanism."""
+    import torch
+    mech.prepare("all")
+    n = args.deriv_points
+    cfg = synth.CONFIGS[2]
+    T, p, Y = synth.generate_states_torch(53, n, cfg["T"], cfg["p_atm"], synth.STATE_SEED_BASE + 2 + 7919 * rank, dev)
+    rho = mech.density(p, T, Y)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    d_rho = torch.randn(n, dtype=torch.float64, device=dev, generator=g) * rho * 1e-3
+    d_T = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+    d_Y = torch.randn((53, n), dtype=torch.float64, device=dev, generator=g) * 1e-4
+    w_bar = torch.randn((53, n), dtype=torch.float64, device=dev, generator=g)
+    J = torch.empty((54 * 54, n), dtype=torch.float64, device=dev)
+    out = torch.empty((53, n), dtype=torch.float64, device=dev)
+    calls = {
+        "jvp": lambda: mech.jvp(rho, T, Y, d_rho, d_T, d_Y, out=out),
+        "vjp": lambda: mech.vjp(rho, T, Y, w_bar),
+        "jacobian": lambda: mech.jacobian(rho, T, Y, out=J),
+        "omega_isothermal": lambda: mech.net_production_rates(rho, Y, T=T, out=out),
+    }
+    res = {"workload": "same mechanism, %d states, T ~ U[300, 2800] K, p ~ U[0.5, 20] atm, Dirichlet Y; "
+                       "Jacobian d(Tdot, omega)/d(T, Y) at fixed rho, [(N+1)^2][n] = %.1f GB out" % (n, 54 * 54 * 8 * n / 1e9)}
+    steps = max(2, min(args.steps, 5))
+    for name, f in calls.items():
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            f()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, dev)
+        res[name + "_ms"] = ms
+        res[name + "_per_s"] = n / (ms * 1e-3)
+    res["jacobian_out_GB_per_s"] = 54 * 54 * 8 * n / (res["jacobian_ms"] * 1e-3) / 1e9
+    del J
+    return res
+
+
 def run_ours(args):
     import torch
     from paper_2503_24286_gb300 import binding as B
@@ -254,6 +298,11 @@ def run_ours(args):
     h2d = (n + n + 53 * n) * 8
     d2h = (53 * n + n) * 8
 
+    # --- derivative kernels on the 2^20-state workload (JVP, VJP, dense Jacobian) ----------
+    deriv = None
+    if not args.no_derivatives:
+        deriv = derivative_rates(mech, synth, dev, stream, args, rank)
+
     # --- roofline of the timed kernel ---------------------------------------------------
     flops_fwd = mech.stat("omega_fp64_flops_per_point")
     flops_ts = 2 * mech.stat("tsolve_collapse_fp64_ops") + 3 * 2 * mech.stat("tsolve_iter_fp64_ops_mixed")
@@ -284,6 +333,8 @@ def run_ours(args):
                 "gpu_launches": launches,
                 "clocks": clocks,
                 "newton_iters_mean": iters_mean,
+                "jacobian_evals_per_s": deriv["jacobian_per_s"] if deriv else None,
+                "derivatives": deriv,
                 "kernel_source_hash": src_hash,
                 "kernel": "pyro_omega (fused Newton T(e,Y) + omega), %d threads/block, %d blocks/SM"
                           % (int(mech.stat("block")), int(mech.stat("omega_blocks_per_sm")))}
@@ -300,6 +351,8 @@ def main():
     ap.add_argument("--points", type=int, default=2 ** 22)
     ap.add_argument("--cpu-sample", type=int, default=2 ** 17)
     ap.add_argument("--ref-sample", type=int, default=2 ** 15)
+    ap.add_argument("--deriv-points", type=int, default=2 ** 20)
+    ap.add_argument("--no-derivatives", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

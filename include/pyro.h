@@ -61,6 +61,9 @@ typedef struct pyro_mech pyro_mech;
  *   cache=0|1           (on-disk cubin cache, default 1; dir $PYRO_CACHE_DIR)
  *   checked=0|1         (1: calls that run Newton synchronise and return
  *                        PYRO_ENOCONV if any point failed to converge)
+ *   deriv_block=<threads per block of the derivative kernels, default 64>
+ *   device=0|1          (0: parse, validate, emit and compile only; no CUDA
+ *                        device is touched and nothing can be launched)
  * On success *out receives a handle to free with pyro_mech_free. */
 int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out);
 void pyro_mech_free(pyro_mech* mech);
@@ -108,6 +111,39 @@ int pyro_temperature(const pyro_mech* mech, int64_t n, const double* e, const do
 int pyro_net_production_rates(const pyro_mech* mech, int64_t n, const double* rho,
                               const double* T_or_e, int input_is_energy, const double* Y,
                               double* T_out, double* omega_out, void* stream);
+
+/* Compile and load derivative kernels ahead of their first use.  kernels:
+ * NULL or "all", or a comma list of "jvp", "vjp", "jacobian".  The groups are
+ * compiled in parallel host threads with NVRTC (cached on disk); without this
+ * call each group is compiled on the first call that needs it. */
+int pyro_mech_prepare(const pyro_mech* mech, const char* kernels);
+
+/* Jacobian-vector product of the net production rates (forward mode):
+ *   d_omega = (d omega/d rho) d_rho + (d omega/d T) d_T + sum_i (d omega/d Y_i) d_Y_i
+ * at the state (rho, T, Y), differentiating Eq. production_rates with
+ * Eq. reaction_rates, Eq. rate_coeff, Eq. equil_constants and the Troe form.
+ * rho, T, d_rho, d_T: [n]; Y, d_Y: [N][n]; d_omega: [N][n] out. */
+int pyro_jvp(const pyro_mech* mech, int64_t n, const double* rho, const double* T, const double* Y,
+             const double* d_rho, const double* d_T, const double* d_Y, double* d_omega, void* stream);
+
+/* Vector-Jacobian product (reverse mode, adjoint) of the same function:
+ *   rho_bar = sum_k omega_bar_k d omega_k/d rho,  T_bar = sum_k omega_bar_k d omega_k/d T,
+ *   Y_bar_i = sum_k omega_bar_k d omega_k/d Y_i.
+ * omega_bar: [N][n]; rho_bar, T_bar: [n] out; Y_bar: [N][n] out.  The
+ * per-reaction intermediates are recomputed, nothing is stored between passes. */
+int pyro_vjp(const pyro_mech* mech, int64_t n, const double* rho, const double* T, const double* Y,
+             const double* omega_bar, double* rho_bar, double* T_bar, double* Y_bar, void* stream);
+
+/* Dense Jacobian for implicit integrators (Eq. jacobian, Eq. chem_jacobian):
+ * J = d(Tdot, omega_1..omega_N)/d(T, Y_1..Y_N) at fixed rho, where Tdot is the
+ * temperature rate of the adiabatic isochoric reactor (Sec. A.1 Eq. massfrac_ode
+ * at fixed internal energy): Tdot = -sum_k (h_k - R T) omega_k / (rho c_v).
+ * J: [(N+1)*(N+1)][n], entry (r, c) at J[(r*(N+1) + c)*n + p]; row 0 = Tdot,
+ * row 1+k = omega_k; column 0 = T, column 1+i = Y_i.  The library keeps a
+ * per-handle scratch buffer for the per-reaction partials (allocated on first
+ * use, grown as needed). */
+int pyro_jacobian(const pyro_mech* mech, int64_t n, const double* rho, const double* T, const double* Y,
+                  double* J, void* stream);
 
 /* Net production rates for callers that cannot allocate device memory.
  * No counterpart in the paper: this is a deployment variant of

@@ -32,7 +32,7 @@ EXPORTS = [
     "pyro_mech_load", "pyro_mech_free", "pyro_mech_info", "pyro_mech_stat", "pyro_mech_source",
     "pyro_density", "pyro_internal_energy", "pyro_temperature", "pyro_net_production_rates",
     "pyro_nonconverged", "pyro_math_eval", "pyro_last_error", "pyro_version",
-    "pyro_net_production_rates_noalloc",
+    "pyro_net_production_rates_noalloc", "pyro_mech_prepare", "pyro_jvp", "pyro_vjp", "pyro_jacobian",
 ]
 
 _lib = None
@@ -65,6 +65,10 @@ def lib() -> ctypes.CDLL:
         L.pyro_temperature.argtypes = [P, I64, D, D, D, ctypes.c_int, D, D, P]
         L.pyro_net_production_rates.argtypes = [P, I64, D, D, ctypes.c_int, D, D, D, P]
         L.pyro_net_production_rates_noalloc.argtypes = [P, I64, D, D, ctypes.c_int, D, D, D, P]
+        L.pyro_mech_prepare.argtypes = [P, ctypes.c_char_p]
+        L.pyro_jvp.argtypes = [P, I64, D, D, D, D, D, D, D, P]
+        L.pyro_vjp.argtypes = [P, I64, D, D, D, D, D, D, D, P]
+        L.pyro_jacobian.argtypes = [P, I64, D, D, D, D, P]
         L.pyro_nonconverged.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64)]
         L.pyro_math_eval.argtypes = [P, ctypes.c_int, I64, D, D, P]
         L.pyro_last_error.restype = ctypes.c_char_p
@@ -205,6 +209,32 @@ class Mechanism:
         _check(lib().pyro_net_production_rates_noalloc(self._h, n, ptrs[0], ptrs[1], 1 if energy else 0,
                                                        ptrs[2], ptrs[3], ptrs[4], _stream(args)))
         return (w, T_out) if energy else w
+
+    def prepare(self, kernels: str = "all"):
+        _check(lib().pyro_mech_prepare(self._h, kernels.encode()))
+
+    def jvp(self, rho, T, Y, d_rho, d_T, d_Y, out=None):
+        """d omega [N, n] = J (d_rho, d_T, d_Y)."""
+        w = _empty_like(rho, (self.n_species, _n(rho))) if out is None else out
+        args = [rho, T, Y, d_rho, d_T, d_Y, w]
+        _check(lib().pyro_jvp(self._h, _n(rho), *[_ptr(a)[0] for a in args], _stream(args)))
+        return w
+
+    def vjp(self, rho, T, Y, omega_bar):
+        """(rho_bar [n], T_bar [n], Y_bar [N, n]) = J^T omega_bar."""
+        n = _n(rho)
+        rb, Tb, Yb = _empty_like(rho, (n,)), _empty_like(rho, (n,)), _empty_like(rho, (self.n_species, n))
+        args = [rho, T, Y, omega_bar, rb, Tb, Yb]
+        _check(lib().pyro_vjp(self._h, n, *[_ptr(a)[0] for a in args], _stream(args)))
+        return rb, Tb, Yb
+
+    def jacobian(self, rho, T, Y, out=None):
+        """J [(N+1)*(N+1), n]: rows (Tdot, omega), columns (T, Y), at fixed rho."""
+        NP = self.n_species + 1
+        J = _empty_like(rho, (NP * NP, _n(rho))) if out is None else out
+        args = [rho, T, Y, J]
+        _check(lib().pyro_jacobian(self._h, _n(rho), *[_ptr(a)[0] for a in args], _stream(args)))
+        return J
 
     def nonconverged(self, stream=None) -> int:
         c = ctypes.c_int64()

@@ -74,6 +74,10 @@ struct SpeciesCoef {
   double cl[2], ci[2], c0[2], c1[2], c2[2], c3[2], c4[2];
   // e_k/R per unit mass fraction: d0 + d1 T + ... + d5 T^5  (= (h_k/R - T)/W_k)
   double d[2][6];
+  // h_k/(R T) = h0 + T*(h1 + T*(h2 + T*(h3 + T*h4))) + h5/T
+  double h[2][6];
+  // cp_k/R = p0 + T*(p1 + T*(p2 + T*(p3 + T*p4))),  d(cp_k/R)/dT = q0 + T*(q1 + T*(q2 + T*q3))
+  double cp[2][5], cpd[2][4];
 };
 
 SpeciesCoef species_coef(const Species& s) {
@@ -96,6 +100,14 @@ SpeciesCoef species_coef(const Species& s) {
     c.d[r][3] = (double)(a[2] / (3 * W));
     c.d[r][4] = (double)(a[3] / (4 * W));
     c.d[r][5] = (double)(a[4] / (5 * W));
+    c.h[r][0] = a[0];
+    c.h[r][1] = (double)((long double)a[1] / 2);
+    c.h[r][2] = (double)((long double)a[2] / 3);
+    c.h[r][3] = (double)((long double)a[3] / 4);
+    c.h[r][4] = (double)((long double)a[4] / 5);
+    c.h[r][5] = a[5];
+    for (int q = 0; q < 5; ++q) c.cp[r][q] = a[q];
+    for (int q = 0; q < 4; ++q) c.cpd[r][q] = (q + 1) * a[q + 1];
   }
   return c;
 }
@@ -124,6 +136,9 @@ void emit_prelude(Src& s, const Mechanism& m, const EmitOptions& opt) {
   }
   s << "};\n";
   s << R"(
+// An opaque copy of a value: keeps the compiler from hoisting and keeping alive
+// hundreds of address computations across the straight-line code.
+__device__ __forceinline__ i64 opq(i64 v) { asm volatile("" : "+l"(v)); return v; }
 __device__ __forceinline__ void pyro_load_tables(double* se, double* sl) {
   for (int i = threadIdx.x; i < 512; i += blockDim.x) se[i] = pyro_tab_exp[i];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) sl[i] = pyro_tab_log[i];
@@ -305,7 +320,7 @@ void emit_third_body(Src& s, const Mechanism& m, const Reaction& r) {
   for (auto& e : r.efficiencies) {
     double c = (e.second - 1.0) / m.species[e.first].W;
     if (c == 0.0) continue;
-    s << " mtb = fma(__ldg(Yp + (i64)" << e.first << " * n), " << lit(c) << ", mtb);";
+    s << " mtb = fma(__ldg(Yp + (i64)" << e.first << " * opq(n)), " << lit(c) << ", mtb);";
     s.fma();
   }
   s << " mtb *= rho;\n";
@@ -414,6 +429,414 @@ std::vector<std::vector<int>> reaction_groups(const Mechanism& m) {
   return g;
 }
 
+// ---------------------------------------------------------------------------
+// derivative kernels (JVP, VJP, dense Jacobian)
+// ---------------------------------------------------------------------------
+//
+// All three differentiate the same expression as the forward kernel:
+//   R_j = kk_j (P'_j - P''_j),  kk_j = exp(x_j) g_j(T, M_j),  P' = prod a^{nu'},
+//   a_i = exp(L_i(T)) rho Y_i,  x_j = lnA'_j + b_j ln T - theta_j / T - sum nu'_ij L_i,
+// with g = 1 (plain), M (third body), Pr/(1+Pr) F (falloff), M_j = rho (sum_i eps_ij Y_i/W_i).
+// Per reaction:  dR/dT = kk [D tau + P'' (S' - S'')],  tau = b/T + theta/T^2 + d ln g/dT,
+// S = sum nu L'_i, L'_i = dL_i/dT = (1 - h_i/RT)/T;  dR/dM = D dkk/dM;  dR/dY_i through a_i
+// (da_i/dY_i = exp(L_i) rho) and through M_j (dM_j/dY_i = rho eps_ij / W_i).
+
+enum class DMode { JVP, VJP, JAC };
+
+// per-species setup of the derivative kernels
+void emit_species_deriv(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, DMode mode) {
+  int N = m.n_species();
+  s << "    double ysum = 0.0;\n";
+  if (mode == DMode::JVP) s << "    double dysum = 0.0;\n";
+  for (int k = 0; k < N; ++k) {
+    const SpeciesCoef& c = C[k];
+    s << "    { const double y = __ldg(Yp + (i64)" << k << " * n);\n";
+    s << "      double q = fma(T, " << sel(c.c4) << ", " << sel(c.c3) << ");\n";
+    s << "      q = fma(T, q, " << sel(c.c2) << "); q = fma(T, q, " << sel(c.c1) << "); q = fma(T, q, " << sel(c.c0) << ");\n";
+    s << "      q = fma(" << sel(c.cl) << ", lnT, q); q = fma(" << sel(c.ci) << ", invT, q);\n";
+    double h4[2] = {c.h[0][4], c.h[1][4]}, h3[2] = {c.h[0][3], c.h[1][3]}, h2[2] = {c.h[0][2], c.h[1][2]};
+    double h1[2] = {c.h[0][1], c.h[1][1]}, h0[2] = {c.h[0][0], c.h[1][0]}, h5[2] = {c.h[0][5], c.h[1][5]};
+    s << "      double hr = fma(T, " << sel(h4) << ", " << sel(h3) << "); hr = fma(T, hr, " << sel(h2)
+      << "); hr = fma(T, hr, " << sel(h1) << "); hr = fma(T, hr, " << sel(h0) << "); hr = fma(" << sel(h5)
+      << ", invT, hr);\n";
+    s << "      const double Lp = fma(-hr, invT, invT);\n";
+    s << "      const double E = pdm::exp(q, s_exp);\n";
+    s << "      const double a = E * (rho * y);\n";
+    s << "      sL" << sidx(k) << " = q; sA" << sidx(k) << " = a;";
+    if (mode == DMode::JAC) s << " sE" << sidx(k) << " = E * rho; sLp" << sidx(k) << " = Lp;";
+    if (mode == DMode::VJP) s << " sLp" << sidx(k) << " = Lp; sC" << sidx(k) << " = 0.0;";
+    if (mode == DMode::JVP) {
+      s << "\n      const double dy = __ldg(dYp + (i64)" << k << " * n);\n";
+      s << "      sdA" << sidx(k) << " = fma(a, fma(Lp, dT, drr), E * (rho * dy)); sdL" << sidx(k) << " = Lp * dT;";
+      s << " dysum = fma(dy, " << lit(1.0 / m.species[k].W) << ", dysum);";
+    }
+    s << "\n      ysum = fma(y, " << lit(1.0 / m.species[k].W) << ", ysum); }\n";
+  }
+}
+
+// factors of a side with multiplicity
+std::vector<int> side_factors(const std::vector<std::pair<int, int>>& side) {
+  std::vector<int> f;
+  for (auto& p : side) for (int i = 0; i < p.second; ++i) f.push_back(p.first);
+  return f;
+}
+
+std::string prod_of(const std::vector<int>& f, const char* arr, int skip = -1) {
+  std::string e;
+  int nf = 0;
+  for (int q = 0; q < (int)f.size(); ++q) {
+    if (q == skip) continue;
+    e += (nf ? " * " : "") + std::string(arr) + sidx(f[q]);
+    ++nf;
+  }
+  return nf ? e : "1.0";
+}
+
+// d(prod a^{nu})/d(something) = sum over factor occurrences of (tangent of that factor) * others
+std::string dprod(const std::vector<int>& f, const char* arr, const char* darr) {
+  std::string e;
+  for (int q = 0; q < (int)f.size(); ++q) {
+    std::string o = prod_of(f, arr, q);
+    e += (q ? " + " : "") + std::string(darr) + sidx(f[q]) + (o == "1.0" ? "" : " * " + o);
+  }
+  return "(" + e + ")";
+}
+
+// emits, inside a reaction block: x, kt, tau, [mS, M, kM], kk, Pf, Pr, D, R
+void emit_reaction_core(Src& s, const Mechanism& m, const Reaction& r) {
+  emit_arg(s, m, r, r.A, r.b, r.theta, "x");
+  s << "      const double kt = pdm::exp(x, s_exp);\n";
+  s << "      double tau = fma(" << lit(r.b) << ", invT, " << lit(r.theta) << " * invT2);\n";
+  if (r.kind == RX_ARRHENIUS) {
+    s << "      const double kk = kt;\n";
+  } else {
+    s << "      double mS = ysum;";
+    for (auto& e : r.efficiencies) {
+      double c = (e.second - 1.0) / m.species[e.first].W;
+      if (c != 0.0) s << " mS = fma(__ldg(Yp + (i64)" << e.first << " * opq(n)), " << lit(c) << ", mS);";
+    }
+    s << "\n      const double M = rho * mS;\n";
+    if (r.kind == RX_THREEBODY) {
+      s << "      const double kk = kt * M; const double kM = kt;\n";
+    } else {
+      const double inv_ln10 = (double)(1.0L / logl(10.0L));
+      s << "      const double lnPr = fma(" << lit(r.b0 - r.b) << ", lnT, " << lit((double)(logl(r.A0) - logl(r.A)))
+        << ") + fma(" << lit(-(r.theta0 - r.theta)) << ", invT, pdm::log(M, s_log));\n";
+      s << "      const double pT = fma(" << lit(r.b0 - r.b) << ", invT, " << lit(r.theta0 - r.theta) << " * invT2);\n";
+      s << "      const double fpr = pdm::rcp(1.0 + pdm::exp(-lnPr, s_exp));\n";
+      if (r.n_troe >= 3) {
+        double a = r.troe[0], T3 = r.troe[1], T1 = r.troe[2];
+        if (a < 1.0)
+          s << "      const double t1 = pdm::exp(fma(T, " << lit(-1.0 / T3) << ", " << lit((double)logl(1.0L - a)) << "), s_exp);\n";
+        else
+          s << "      const double t1 = " << lit(1.0 - a) << " * pdm::exp(T * " << lit(-1.0 / T3) << ", s_exp);\n";
+        if (a > 0.0)
+          s << "      const double t2 = pdm::exp(fma(T, " << lit(-1.0 / T1) << ", " << lit((double)logl((long double)a)) << "), s_exp);\n";
+        else
+          s << "      const double t2 = 0.0;\n";
+        if (r.n_troe == 4)
+          s << "      const double t3 = pdm::exp(" << lit(-r.troe[3]) << " * invT, s_exp);\n";
+        else
+          s << "      const double t3 = 0.0;\n";
+        s << "      const double fc = t1 + t2 + t3;\n";
+        s << "      const double dfc = fma(t1, " << lit(-1.0 / T3) << ", fma(t2, " << lit(-1.0 / T1) << ", t3 * "
+          << lit(r.n_troe == 4 ? r.troe[3] : 0.0) << " * invT2));\n";
+        s << "      const double lfc = pdm::log(fc, s_log) * " << lit(inv_ln10) << ";\n";
+        s << "      const double cc = fma(-0.67, lfc, -0.4); const double nn = fma(-1.27, lfc, 0.75);\n";
+        s << "      const double xx = fma(lnPr, " << lit(inv_ln10) << ", cc); const double den = fma(-0.14, xx, nn);\n";
+        s << "      const double den2 = den * den; const double rD = pdm::rcp(fma(xx, xx, den2));\n";
+        s << "      const double f = den2 * rD; const double F = pdm::exp(lfc * f * " << lit((double)logl(10.0L)) << ", s_exp);\n";
+        s << "      const double rD2 = rD * rD;\n";
+        s << "      const double Axx = lfc * (-2.0 * den2 * xx * rD2); const double Aden = lfc * (2.0 * den * xx * xx * rD2);\n";
+        s << "      const double sPr = (1.0 - fpr) + fma(-0.14, Aden, Axx);\n";
+        s << "      const double sfc = fma(-0.67, Axx, fma(-1.1762, Aden, f));\n";
+        s << "      tau += fma(sPr, pT, sfc * dfc * pdm::rcp(fc));\n";
+        s << "      const double kk = kt * fpr * F;\n";
+      } else {
+        s << "      const double sPr = 1.0 - fpr;\n      tau += sPr * pT;\n      const double kk = kt * fpr;\n";
+      }
+      s << "      const double kM = kk * sPr * pdm::rcp(M);\n";
+    }
+  }
+  s << "      const double Pf = " << prod_of(side_factors(r.reactants), "sA") << ";\n";
+  if (r.reversible)
+    s << "      const double Pr = " << prod_of(side_factors(r.products), "sA") << ";\n";
+  else
+    s << "      const double Pr = 0.0;\n";
+  s << "      const double D = Pf - Pr;\n      const double R = kk * D;\n";
+}
+
+// net (nu'' - nu') over species of a reaction, and the set of species
+std::vector<std::pair<int, int>> reaction_species(const Reaction& r) {
+  std::vector<std::pair<int, int>> v;
+  for (auto& q : net_nu(r)) v.push_back(q);
+  return v;
+}
+
+int nu_of(const std::vector<std::pair<int, int>>& side, int k) {
+  for (auto& p : side) if (p.first == k) return p.second;
+  return 0;
+}
+
+void emit_jvp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, int blk) {
+  int N = m.n_species();
+  s << "\n// JVP: d omega = (d omega/d rho) d rho + (d omega/dT) dT + sum_i (d omega/dY_i) dY_i\n";
+  s << "extern \"C\" __global__ void __launch_bounds__(" << blk << ") pyro_jvp(i64 n, const double* __restrict__ g_rho,\n"
+       "    const double* __restrict__ g_T, const double* __restrict__ g_Y, const double* __restrict__ g_drho,\n"
+       "    const double* __restrict__ g_dT, const double* __restrict__ g_dY, double* __restrict__ g_dw) {\n"
+       "  __shared__ double s_exp[512];\n  __shared__ double s_log[256];\n  extern __shared__ double s_dyn[];\n"
+       "  double* sL = s_dyn; double* sA = sL + NSP * BLKD; double* sdA = sA + NSP * BLKD; double* sdL = sdA + NSP * BLKD;\n"
+       "  pyro_load_tables(s_exp, s_log);\n  __syncthreads();\n  const int t = threadIdx.x;\n"
+       "  for (i64 p = (i64)blockIdx.x * BLKD + t; p < n; p += (i64)gridDim.x * BLKD) {\n"
+       "    const double* Yp = g_Y + p; const double* dYp = g_dY + p;\n"
+       "    const double rho = g_rho[p], T = g_T[p], drho = g_drho[p], dT = g_dT[p];\n"
+       "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
+       "    const double drr = drho * pdm::rcp(rho);\n"
+       "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
+  emit_species_deriv(s, m, C, DMode::JVP);
+  s << "    double ";
+  for (int k = 0; k < N; ++k) s << (k ? ", " : "") << "w" << k << " = 0.0";
+  s << ";\n";
+  for (int j = 0; j < m.n_reactions(); ++j) {
+    const Reaction& r = m.reactions[j];
+    s << "    { // reaction " << j << "\n";
+    emit_reaction_core(s, m, r);
+    s << "      double dx = tau * dT;";
+    for (auto& p : r.reactants) s << " dx = fma(" << lit(-(double)p.second) << ", sdL" << sidx(p.first) << ", dx);";
+    s << "\n";
+    if (r.kind == RX_ARRHENIUS) {
+      s << "      const double dkk = kk * dx;\n";
+    } else {
+      s << "      double dmS = dysum;";
+      for (auto& e : r.efficiencies) {
+        double c = (e.second - 1.0) / m.species[e.first].W;
+        if (c != 0.0) s << " dmS = fma(__ldg(dYp + (i64)" << e.first << " * opq(n)), " << lit(c) << ", dmS);";
+      }
+      s << "\n      const double dM = fma(drho, mS, rho * dmS);\n";
+      s << "      const double dkk = fma(kk, dx, kM * dM);\n";
+    }
+    s << "      const double dPf = " << dprod(side_factors(r.reactants), "sA", "sdA") << ";\n";
+    if (r.reversible) s << "      const double dPr = " << dprod(side_factors(r.products), "sA", "sdA") << ";\n";
+    else s << "      const double dPr = 0.0;\n";
+    s << "      const double dR = fma(dkk, D, kk * (dPf - dPr));\n     ";
+    emit_omega_update(s, r, "dR");
+    s << "    }\n";
+  }
+  for (int k = 0; k < N; ++k) s << "    g_dw[(i64)" << k << " * n + p] = w" << k << ";\n";
+  s << "  }\n}\n";
+}
+
+void emit_vjp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, int blk) {
+  int N = m.n_species();
+  s << "\n// VJP: (rho_bar, T_bar, Y_bar) = (d omega/d(rho, T, Y))^T omega_bar\n";
+  s << "extern \"C\" __global__ void __launch_bounds__(" << blk << ") pyro_vjp(i64 n, const double* __restrict__ g_rho,\n"
+       "    const double* __restrict__ g_T, const double* __restrict__ g_Y, const double* __restrict__ g_wb,\n"
+       "    double* __restrict__ g_rhob, double* __restrict__ g_Tb, double* __restrict__ g_Yb) {\n"
+       "  __shared__ double s_exp[512];\n  __shared__ double s_log[256];\n  extern __shared__ double s_dyn[];\n"
+       "  double* sL = s_dyn; double* sA = sL + NSP * BLKD; double* sLp = sA + NSP * BLKD; double* sC = sLp + NSP * BLKD;\n"
+       "  pyro_load_tables(s_exp, s_log);\n  __syncthreads();\n  const int t = threadIdx.x;\n"
+       "  for (i64 p = (i64)blockIdx.x * BLKD + t; p < n; p += (i64)gridDim.x * BLKD) {\n"
+       "    const double* Yp = g_Y + p; const double* Wb = g_wb + p;\n"
+       "    const double rho = g_rho[p], T = g_T[p];\n"
+       "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
+       "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
+  emit_species_deriv(s, m, C, DMode::VJP);
+  s << "    double Tb = 0.0, Mtot = 0.0, rhobM = 0.0;\n    double ";
+  for (int k = 0; k < N; ++k) s << (k ? ", " : "") << "ab" << k << " = 0.0";
+  s << ";\n";
+  for (int j = 0; j < m.n_reactions(); ++j) {
+    const Reaction& r = m.reactions[j];
+    s << "    { // reaction " << j << "\n";
+    // R_bar = sum_k nu_kj omega_bar_k
+    s << "      double Rb = 0.0;";
+    for (auto& q : net_nu(r)) {
+      if (q.second == 0) continue;
+      s << " Rb = fma(" << lit((double)q.second) << ", __ldg(Wb + (i64)" << q.first << " * opq(n)), Rb);";
+    }
+    s << "\n";
+    emit_reaction_core(s, m, r);
+    s << "      const double xb = Rb * R;\n      Tb = fma(xb, tau, Tb);";
+    for (auto& p : r.reactants) s << " Tb = fma(" << lit(-(double)p.second) << " * xb, sLp" << sidx(p.first) << ", Tb);";
+    s << "\n      const double Db = Rb * kk;\n";
+    auto fr = side_factors(r.reactants);
+    for (int q = 0; q < (int)fr.size(); ++q)
+      s << "      ab" << fr[q] << " = fma(Db, " << prod_of(fr, "sA", q) << ", ab" << fr[q] << ");\n";
+    if (r.reversible) {
+      auto fp = side_factors(r.products);
+      for (int q = 0; q < (int)fp.size(); ++q)
+        s << "      ab" << fp[q] << " = fma(-Db, " << prod_of(fp, "sA", q) << ", ab" << fp[q] << ");\n";
+    }
+    if (r.kind != RX_ARRHENIUS) {
+      s << "      const double Mb = Rb * kM * D; Mtot += Mb; rhobM = fma(Mb, mS, rhobM);\n";
+      for (auto& e : r.efficiencies) {
+        double c = (e.second - 1.0) / m.species[e.first].W;
+        if (c != 0.0) s << "      sC" << sidx(e.first) << " = fma(Mb, " << lit(c) << ", sC" << sidx(e.first) << ");\n";
+      }
+    }
+    s << "    }\n";
+  }
+  s << "    double rhob = 0.0;\n";
+  for (int k = 0; k < N; ++k) {
+    s << "    { const double ta = ab" << k << " * sA" << sidx(k) << "; Tb = fma(ta, sLp" << sidx(k) << ", Tb); rhob += ta;\n";
+    s << "      g_Yb[(i64)" << k << " * n + p] = fma(ab" << k << ", pdm::exp(sL" << sidx(k) << ", s_exp) * rho, rho * fma(Mtot, "
+      << lit(1.0 / m.species[k].W) << ", sC" << sidx(k) << ")); }\n";
+  }
+  s << "    g_Tb[p] = Tb;\n    g_rhob[p] = fma(rhob, pdm::rcp(rho), rhobM);\n  }\n}\n";
+}
+
+struct JacSlots {
+  int n = 0;
+  std::vector<int> R, Rt, RM;                 // per reaction
+  std::vector<std::map<int, int>> Q;          // per reaction: species -> slot
+};
+
+void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, int blk, int* nslots) {
+  int N = m.n_species(), M = m.n_reactions(), NP = N + 1;
+  JacSlots sl;
+  sl.R.resize(M); sl.Rt.resize(M); sl.RM.assign(M, -1); sl.Q.resize(M);
+  for (int j = 0; j < M; ++j) {
+    const Reaction& r = m.reactions[j];
+    sl.R[j] = sl.n++;
+    sl.Rt[j] = sl.n++;
+    if (r.kind != RX_ARRHENIUS) sl.RM[j] = sl.n++;
+    std::set<int> sp;
+    for (auto& p : r.reactants) sp.insert(p.first);
+    if (r.reversible) for (auto& p : r.products) sp.insert(p.first);
+    for (int i : sp) sl.Q[j][i] = sl.n++;
+  }
+  *nslots = sl.n;
+  auto slot = [&](int q) { return "W[" + std::to_string(q) + " * BLKD]"; };
+  s << "\n// Dense Jacobian d(Tdot, omega)/d(T, Y) at fixed rho, [(N+1)^2][n]; row 0 = Tdot of the adiabatic\n"
+       "// isochoric reactor, rows 1..N = omega; column 0 = T, columns 1..N = Y.  Phase 1 writes the\n"
+       "// per-reaction partials to the block's scratch, phase 2 assembles the rows.\n";
+  s << "extern \"C\" __global__ void __launch_bounds__(" << blk << ") pyro_jacobian(i64 n, const double* __restrict__ g_rho,\n"
+       "    const double* __restrict__ g_T, const double* __restrict__ g_Y, double* __restrict__ g_J,\n"
+       "    double* __restrict__ g_scratch) {\n"
+       "  __shared__ double s_exp[512];\n  __shared__ double s_log[256];\n  extern __shared__ double s_dyn[];\n"
+       "  double* sL = s_dyn; double* sA = sL + NSP * BLKD; double* sE = sA + NSP * BLKD; double* sLp = sE + NSP * BLKD;\n"
+       "  pyro_load_tables(s_exp, s_log);\n  __syncthreads();\n  const int t = threadIdx.x;\n"
+       "  double* W = g_scratch + (i64)blockIdx.x * " << sl.n << " * BLKD + t;\n"
+       "  for (i64 p = (i64)blockIdx.x * BLKD + t; p < n; p += (i64)gridDim.x * BLKD) {\n"
+       "    const double* Yp = g_Y + p;\n    double* Jp = g_J + p;\n"
+       "    const double rho = g_rho[p], T = g_T[p];\n"
+       "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
+       "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
+  emit_species_deriv(s, m, C, DMode::JAC);
+  // ---- phase 1
+  for (int j = 0; j < M; ++j) {
+    const Reaction& r = m.reactions[j];
+    s << "    { // reaction " << j << "\n";
+    emit_reaction_core(s, m, r);
+    // S' - S'' = sum_i (nu'_i - nu''_i) L'_i
+    s << "      double dS = 0.0;";
+    std::set<int> sp;
+    for (auto& p : r.reactants) sp.insert(p.first);
+    if (r.reversible) for (auto& p : r.products) sp.insert(p.first);
+    for (int i : sp) {
+      int c = nu_of(r.reactants, i) - (r.reversible ? nu_of(r.products, i) : 0);
+      if (c) s << " dS = fma(" << lit((double)c) << ", sLp" << sidx(i) << ", dS);";
+    }
+    s << "\n      " << slot(sl.R[j]) << " = R; " << slot(sl.Rt[j]) << " = kk * fma(D, tau, Pr * dS);\n";
+    if (sl.RM[j] >= 0) s << "      " << slot(sl.RM[j]) << " = kM * D;\n";
+    auto fr = side_factors(r.reactants);
+    auto fp = side_factors(r.products);
+    for (int i : sp) {
+      std::string e;
+      for (int q = 0; q < (int)fr.size(); ++q)
+        if (fr[q] == i) { e = " + " + prod_of(fr, "sA", q); break; }
+      int nr_ = nu_of(r.reactants, i);
+      std::string termf = e.empty() ? "" : "(" + lit((double)nr_) + " * " + e.substr(3) + ")";
+      std::string termr;
+      if (r.reversible)
+        for (int q = 0; q < (int)fp.size(); ++q)
+          if (fp[q] == i) { termr = "(" + lit((double)nu_of(r.products, i)) + " * " + prod_of(fp, "sA", q) + ")"; break; }
+      std::string diff = termf.empty() ? "-" + termr : termr.empty() ? termf : termf + " - " + termr;
+      s << "      " << slot(sl.Q[j][i]) << " = kk * sE" << sidx(i) << " * (" << diff << ");\n";
+    }
+    s << "    }\n";
+  }
+  // ---- phase 2: rows.  sL becomes s_i = rho/W_i, sA the Tdot column accumulators.
+  // The barrier keeps the compiler from forwarding phase-1 values through registers.
+  s << "    asm volatile(\"\" ::: \"memory\");\n";
+  for (int i = 0; i < N; ++i)
+    s << "    sL" << sidx(i) << " = rho * " << lit(1.0 / m.species[i].W) << "; sA" << sidx(i) << " = 0.0;\n";
+  s << "    const double RT = " << lit((double)R_GAS) << " * T;\n";
+  s << "    double sum_ew = 0.0, sum_cpw = 0.0, sum_ejt = 0.0, U = 0.0;\n";
+  // per-species row lists
+  std::vector<std::vector<std::pair<int, int>>> rows(N);
+  for (int j = 0; j < M; ++j)
+    for (auto& q : net_nu(m.reactions[j])) if (q.second) rows[q.first].push_back({j, q.second});
+  for (int k = 0; k < N; ++k) {
+    const SpeciesCoef& c = C[k];
+    s << "    { // row of species " << k << "\n      double w = 0.0, jt = 0.0, u = 0.0;\n";
+    std::map<int, std::string> acc, cr;
+    for (auto& jn : rows[k]) {
+      int j = jn.first;
+      std::string nu = lit((double)jn.second);
+      s << "      w = fma(" << nu << ", " << slot(sl.R[j]) << ", w); jt = fma(" << nu << ", " << slot(sl.Rt[j]) << ", jt);";
+      if (sl.RM[j] >= 0) s << " u = fma(" << nu << ", " << slot(sl.RM[j]) << ", u);";
+      s << "\n";
+      for (auto& qi : sl.Q[j]) {
+        std::string name = "q" + std::to_string(qi.first);
+        if (!acc.count(qi.first)) { acc[qi.first] = name; s << "      double " << name << " = 0.0;\n"; }
+        s << "      " << name << " = fma(" << nu << ", " << slot(qi.second) << ", " << name << ");\n";
+      }
+      if (sl.RM[j] >= 0) {
+        for (auto& e : m.reactions[j].efficiencies) {
+          if (e.second == 1.0) continue;
+          std::string name = "c" + std::to_string(e.first);
+          if (!cr.count(e.first)) { cr[e.first] = name; s << "      double " << name << " = 0.0;\n"; }
+          s << "      " << name << " = fma(" << nu << " * " << lit(e.second - 1.0) << ", " << slot(sl.RM[j]) << ", " << name << ");\n";
+        }
+      }
+    }
+    double h4[2] = {c.h[0][4], c.h[1][4]}, h3[2] = {c.h[0][3], c.h[1][3]}, h2[2] = {c.h[0][2], c.h[1][2]};
+    double h1[2] = {c.h[0][1], c.h[1][1]}, h0[2] = {c.h[0][0], c.h[1][0]}, h5[2] = {c.h[0][5], c.h[1][5]};
+    double p4[2] = {c.cp[0][4], c.cp[1][4]}, p3[2] = {c.cp[0][3], c.cp[1][3]}, p2[2] = {c.cp[0][2], c.cp[1][2]};
+    double p1[2] = {c.cp[0][1], c.cp[1][1]}, p0[2] = {c.cp[0][0], c.cp[1][0]};
+    s << "      double hr = fma(T, " << sel(h4) << ", " << sel(h3) << "); hr = fma(T, hr, " << sel(h2)
+      << "); hr = fma(T, hr, " << sel(h1) << "); hr = fma(T, hr, " << sel(h0) << "); hr = fma(" << sel(h5) << ", invT, hr);\n";
+    s << "      double cp = fma(T, " << sel(p4) << ", " << sel(p3) << "); cp = fma(T, cp, " << sel(p2)
+      << "); cp = fma(T, cp, " << sel(p1) << "); cp = fma(T, cp, " << sel(p0) << ");\n";
+    s << "      const double eh = fma(RT, hr, -RT); const double cpm = " << lit((double)R_GAS) << " * (cp - 1.0);\n";
+    s << "      sum_ew = fma(eh, w, sum_ew); sum_cpw = fma(cpm, w, sum_cpw); sum_ejt = fma(eh, jt, sum_ejt); U = fma(eh, u, U);\n";
+    s << "      const i64 nr = opq(n);\n      double* Jr = Jp + (i64)" << (k + 1) * NP << " * nr;\n      Jr[0] = jt;\n";
+    s << "      #pragma unroll 1\n      for (int i = 0; i < NSP; ++i) Jr[(i64)(1 + i) * nr] = sL[i * BLKD + t] * u;\n";
+    for (int i = 0; i < N; ++i) {
+      std::string si = "sL" + sidx(i);
+      std::string dst = "Jr[(i64)" + std::to_string(1 + i) + " * nr]";
+      bool hs = acc.count(i), hc = cr.count(i);
+      if (hs || hc) {
+        std::string tv = hc ? "fma(" + si + ", " + cr[i] + ", " + (hs ? acc[i] : std::string("0.0")) + ")" : acc[i];
+        s << "      { const double tv = " << tv << "; " << dst << " = fma(" << si << ", u, tv); sA" << sidx(i)
+          << " = fma(eh, tv, sA" << sidx(i) << "); }\n";
+      }
+    }
+    s << "    }\n";
+  }
+  // Tdot row
+  s << "    double cv = 0.0, cvT = 0.0;\n";
+  for (int k = 0; k < N; ++k) {
+    const SpeciesCoef& c = C[k];
+    double p4[2] = {c.cp[0][4], c.cp[1][4]}, p3[2] = {c.cp[0][3], c.cp[1][3]}, p2[2] = {c.cp[0][2], c.cp[1][2]};
+    double p1[2] = {c.cp[0][1], c.cp[1][1]}, p0[2] = {c.cp[0][0], c.cp[1][0]};
+    double q3[2] = {c.cpd[0][3], c.cpd[1][3]}, q2[2] = {c.cpd[0][2], c.cpd[1][2]}, q1[2] = {c.cpd[0][1], c.cpd[1][1]};
+    double q0[2] = {c.cpd[0][0], c.cpd[1][0]};
+    s << "    { const double yw = __ldg(Yp + (i64)" << k << " * n) * " << lit((double)R_GAS / m.species[k].W) << ";\n";
+    s << "      double cp = fma(T, " << sel(p4) << ", " << sel(p3) << "); cp = fma(T, cp, " << sel(p2)
+      << "); cp = fma(T, cp, " << sel(p1) << "); cp = fma(T, cp, " << sel(p0) << ");\n";
+    s << "      double cd = fma(T, " << sel(q3) << ", " << sel(q2) << "); cd = fma(T, cd, " << sel(q1) << "); cd = fma(T, cd, " << sel(q0) << ");\n";
+    s << "      cv = fma(yw, cp - 1.0, cv); cvT = fma(yw, cd, cvT);\n";
+    s << "      sE" << sidx(k) << " = (cp - 1.0) * " << lit((double)R_GAS / m.species[k].W) << "; }\n";
+  }
+  s << "    const double rcv = pdm::rcp(rho * cv);\n    const double Tdot = -sum_ew * rcv;\n"
+       "    const double tcv = Tdot * pdm::rcp(cv);\n"
+       "    Jp[0] = fma(-(sum_cpw + sum_ejt), rcv, -tcv * cvT);\n";
+  s << "    #pragma unroll 1\n    for (int i = 0; i < NSP; ++i) Jp[(i64)(1 + i) * n] = "
+       "fma(-fma(sL[i * BLKD + t], U, sA[i * BLKD + t]), rcv, -tcv * sE[i * BLKD + t]);\n";
+  s << "  }\n}\n";
+}
+
 }  // namespace
 
 EmitResult emit_module(const Mechanism& m, const EmitOptions& opt) {
@@ -515,6 +938,29 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature(i64 n, const 
   r << "  }\n}\n";
   s << r.o.str();
 
+  // ---- derivative kernels: separate translation units (compiled on first use) -------
+  // the derivative translation units index shared memory with BLK as well, so
+  // their prelude sets BLK to the derivative block size
+  Src pre;
+  EmitOptions dopt = opt;
+  dopt.block = opt.deriv_block;
+  emit_prelude(pre, m, dopt);
+  pre << "#define BLKD " << opt.deriv_block << "\n";
+  {
+    Src d; d << pre.o.str(); emit_jvp_kernel(d, m, C, opt.deriv_block); out.group_sources["jvp"] = d.o.str();
+  }
+  {
+    Src d; d << pre.o.str(); emit_vjp_kernel(d, m, C, opt.deriv_block); out.group_sources["vjp"] = d.o.str();
+  }
+  int nslots = 0;
+  {
+    Src d; d << pre.o.str(); emit_jacobian_kernel(d, m, C, opt.deriv_block, &nslots); out.group_sources["jac"] = d.o.str();
+  }
+  out.jac_slots = nslots;
+  out.smem_dyn_bytes_deriv = 4 * N * opt.deriv_block * (int)sizeof(double);
+  out.stats["jacobian_scratch_doubles_per_point"] = nslots;
+  out.stats["deriv_block"] = opt.deriv_block;
+
   out.stats["omega_fp64_ops_per_point"] = r.ops();
   out.stats["omega_fp64_flops_per_point"] = r.flops();
   out.stats["omega_dfma_per_point"] = r.dfma;
@@ -525,6 +971,7 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature(i64 n, const 
   out.stats["block"] = opt.block;
   out.smem_dyn_bytes_omega = 2 * N * opt.block * (int)sizeof(double);
   out.source = s.o.str();
+  out.group_sources["fwd"] = out.source;
   return out;
 }
 

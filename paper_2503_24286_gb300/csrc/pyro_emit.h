@@ -12,12 +12,17 @@ struct EmitOptions {
   int block = 128;            // threads per block (one point per thread)
   int min_blocks = 2;         // __launch_bounds__ minimum resident blocks
   bool mixed_newton = true;   // FP32 Newton to ~1e-5, then FP64 Newton (else FP64 only)
+  int deriv_block = 64;       // threads per block of the JVP / VJP / Jacobian kernels
 };
 
 struct EmitResult {
-  std::string source;                     // CUDA C translation unit
+  std::string source;                     // CUDA C of the forward kernels
+  std::map<std::string, std::string> group_sources;   // "fwd", "jvp", "vjp", "jac"
+
   std::map<std::string, double> stats;    // static FP64-pipe op counts per point etc.
   int smem_dyn_bytes_omega = 0;           // dynamic shared memory of the omega kernel
+  int smem_dyn_bytes_deriv = 0;           // dynamic shared memory of the derivative kernels
+  int jac_slots = 0;                      // scratch doubles per point of the Jacobian kernel
 };
 
 EmitResult emit_module(const Mechanism& m, const EmitOptions& opt);

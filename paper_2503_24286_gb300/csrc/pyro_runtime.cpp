@@ -9,6 +9,7 @@
 #include <sys/stat.h>
 #include <unistd.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -17,6 +18,7 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pyro_emit.h"
@@ -128,12 +130,50 @@ bool nvrtc_compile(const std::string& src, std::vector<char>& cubin, std::string
   return true;
 }
 
+
+// Compile CUDA C for sm_103a with NVRTC, or fetch the cubin from the on-disk
+// cache keyed by a hash of the source, the device-math header, the arch and the
+// NVRTC version.
+int compile_cached(const std::string& src, bool use_cache, std::vector<char>& cubin) {
+  if (const char* dump = std::getenv("PYRO_DUMP_DIR")) {   // debugging aid: keep the emitted sources
+    mkdirs(dump);
+    std::ofstream f(std::string(dump) + "/pyro_" + std::to_string(fnv1a(src) & 0xffffff) + ".cu");
+    f << src;
+  }
+  int nv_major = 0, nv_minor = 0;
+  nvrtcVersion(&nv_major, &nv_minor);
+  std::string key_src = src + std::string(kDeviceMathSource) + kArch + std::to_string(nv_major) + "." +
+                        std::to_string(nv_minor);
+  char hex[32];
+  std::snprintf(hex, sizeof hex, "%016llx", (unsigned long long)fnv1a(key_src));
+  std::string dir = cache_dir(), path = dir + "/pyro_" + hex + ".cubin";
+  cubin.clear();
+  if (use_cache) {
+    std::ifstream f(path, std::ios::binary);
+    if (f) cubin.assign(std::istreambuf_iterator<char>(f), std::istreambuf_iterator<char>());
+  }
+  if (!cubin.empty()) return PYRO_OK;
+  std::string log;
+  if (!nvrtc_compile(src, cubin, log)) return fail(PYRO_ECOMPILE, "NVRTC: " + log);
+  if (use_cache) {
+    mkdirs(dir);
+    std::string tmp = path + ".tmp" + std::to_string((long)getpid()) + "_" +
+                      std::to_string((unsigned long long)std::hash<std::string>()(src) & 0xffff);
+    std::ofstream f(tmp, std::ios::binary);
+    f.write(cubin.data(), (std::streamsize)cubin.size());
+    f.close();
+    std::rename(tmp.c_str(), path.c_str());
+  }
+  return PYRO_OK;
+}
+
 struct Options {
   int block = 128;
   bool mixed = true;
   bool cache = true;
   bool checked = false;
   bool device = true;     // false: parse, validate, emit and compile only (no CUDA device needed)
+  int deriv_block = 64;   // threads per block of the derivative kernels
 };
 
 bool parse_options(const char* s, Options& o, std::string& err) {
@@ -152,6 +192,7 @@ bool parse_options(const char* s, Options& o, std::string& err) {
     else if (k == "cache") o.cache = v != "0";
     else if (k == "checked") o.checked = v != "0";
     else if (k == "device") o.device = v != "0";
+    else if (k == "deriv_block") { o.deriv_block = std::atoi(v.c_str()); if (o.deriv_block < 32 || o.deriv_block > 256 || o.deriv_block % 32) { err = "deriv_block must be a multiple of 32 in [32, 256]"; return false; } }
     else { err = "unknown option '" + k + "'"; return false; }
   }
   return true;
@@ -171,6 +212,18 @@ struct pyro_mech {
              f_math = nullptr;
   int omega_blocks_per_sm = 1;
   unsigned long long* d_fail = nullptr;
+  // derivative kernels: compiled and loaded on first use (or by pyro_mech_prepare)
+  struct Group {
+    CUmodule module = nullptr;
+    CUfunction f = nullptr;
+    int blocks_per_sm = 0;
+    bool failed = false;
+    std::string err;
+  };
+  std::map<std::string, Group> groups;
+  std::mutex group_mu;
+  double* d_jac_scratch = nullptr;
+  size_t jac_scratch_bytes = 0;
   // staging buffers for host-pointer calls
   std::vector<void*> stage;
   std::vector<size_t> stage_bytes;
@@ -286,6 +339,73 @@ int maybe_checked(const pyro_mech* h, void* stream) {
   return PYRO_OK;
 }
 
+
+const char* group_kernel(const std::string& g) {
+  return g == "jvp" ? "pyro_jvp" : g == "vjp" ? "pyro_vjp" : "pyro_jacobian";
+}
+
+// Compile (in parallel threads, cached on disk) and load the named derivative
+// kernel groups that are not loaded yet.
+int ensure_groups(pyro_mech* h, const std::vector<std::string>& names) {
+  std::lock_guard<std::mutex> lock(h->group_mu);
+  std::vector<std::string> todo;
+  for (auto& g : names) {
+    auto& G = h->groups[g];
+    if (G.failed) return fail(PYRO_ECOMPILE, G.err);
+    if (!G.module && !(h->module == nullptr && G.blocks_per_sm < 0)) todo.push_back(g);
+  }
+  if (todo.empty()) return PYRO_OK;
+  std::vector<std::vector<char>> cubins(todo.size());
+  std::vector<int> rcs(todo.size(), PYRO_OK);
+  std::vector<std::string> errs(todo.size());
+  std::vector<std::thread> th;
+  for (size_t i = 0; i < todo.size(); ++i) {
+    th.emplace_back([&, i] {
+      rcs[i] = compile_cached(h->emitted.group_sources.at(todo[i]), h->opt.cache, cubins[i]);
+      if (rcs[i]) errs[i] = pyro_last_error();
+    });
+  }
+  for (auto& t : th) t.join();
+  if (!h->module) {   // compile-only handle: record the build, load nothing
+    for (size_t i = 0; i < todo.size(); ++i) {
+      auto& G = h->groups[todo[i]];
+      if (rcs[i]) { G.failed = true; G.err = errs[i]; return fail(rcs[i], errs[i]); }
+      G.blocks_per_sm = -1;
+      h->emitted.stats[todo[i] + "_cubin_bytes"] = (double)cubins[i].size();
+    }
+    return PYRO_OK;
+  }
+  Driver& d = driver();
+  for (size_t i = 0; i < todo.size(); ++i) {
+    auto& G = h->groups[todo[i]];
+    if (rcs[i]) { G.failed = true; G.err = errs[i]; return fail(rcs[i], errs[i]); }
+    CUresult r = d.ModuleLoadData(&G.module, cubins[i].data());
+    if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "cuModuleLoadData: " + cu_err(r));
+    r = d.ModuleGetFunction(&G.f, G.module, group_kernel(todo[i]));
+    if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, std::string("missing kernel ") + group_kernel(todo[i]));
+    int smem = h->emitted.smem_dyn_bytes_deriv;
+    r = d.FuncSetAttribute(G.f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem);
+    if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "shared memory request: " + cu_err(r));
+    int nb = 0;
+    r = d.Occupancy(&nb, G.f, h->opt.deriv_block, smem);
+    if (r != CUDA_SUCCESS || nb < 1) return fail(PYRO_ECUDA, std::string(group_kernel(todo[i])) + " does not fit on an SM");
+    G.blocks_per_sm = nb;
+    h->emitted.stats[todo[i] + "_blocks_per_sm"] = nb;
+    h->emitted.stats[todo[i] + "_cubin_bytes"] = (double)cubins[i].size();
+  }
+  return PYRO_OK;
+}
+
+int launch_deriv(const pyro_mech* h, const pyro_mech::Group& G, int64_t n, void* stream, void** params) {
+  int64_t need = (n + h->opt.deriv_block - 1) / h->opt.deriv_block;
+  int64_t cap = (int64_t)h->num_sms * G.blocks_per_sm;
+  unsigned grid = (unsigned)(need < cap ? need : cap);
+  if (grid == 0) return PYRO_OK;
+  CUresult r = driver().LaunchKernel(G.f, grid, 1, 1, h->opt.deriv_block, 1, 1, h->emitted.smem_dyn_bytes_deriv,
+                                     as_stream(stream), params, nullptr);
+  if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
+  return PYRO_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -307,32 +427,12 @@ int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) 
   eo.block = h->opt.block;
   eo.min_blocks = h->opt.block <= 64 ? 4 : (h->opt.block <= 128 ? 2 : 1);
   eo.mixed_newton = h->opt.mixed;
+  eo.deriv_block = h->opt.deriv_block;
   h->emitted = emit_module(h->m, eo);
 
   // compile (or fetch from the cache)
-  int nv_major = 0, nv_minor = 0;
-  nvrtcVersion(&nv_major, &nv_minor);
-  std::string key_src = h->emitted.source + std::string(kDeviceMathSource) + kArch + std::to_string(nv_major) + "." + std::to_string(nv_minor);
-  char hex[32];
-  std::snprintf(hex, sizeof hex, "%016llx", (unsigned long long)fnv1a(key_src));
-  std::string dir = cache_dir(), path = dir + "/pyro_" + hex + ".cubin";
   std::vector<char> cubin;
-  if (h->opt.cache) {
-    std::ifstream f(path, std::ios::binary);
-    if (f) cubin.assign(std::istreambuf_iterator<char>(f), std::istreambuf_iterator<char>());
-  }
-  if (cubin.empty()) {
-    std::string log;
-    if (!nvrtc_compile(h->emitted.source, cubin, log)) { delete h; return fail(PYRO_ECOMPILE, "NVRTC: " + log); }
-    if (h->opt.cache) {
-      mkdirs(dir);
-      std::string tmp = path + ".tmp" + std::to_string((long)getpid());
-      std::ofstream f(tmp, std::ios::binary);
-      f.write(cubin.data(), (std::streamsize)cubin.size());
-      f.close();
-      std::rename(tmp.c_str(), path.c_str());
-    }
-  }
+  if (int rc = compile_cached(h->emitted.source, h->opt.cache, cubin)) { delete h; return rc; }
   h->emitted.stats["cubin_bytes"] = (double)cubin.size();
   if (!h->opt.device) { *out = h; return PYRO_OK; }
   Driver& d = driver();
@@ -379,6 +479,8 @@ void pyro_mech_free(pyro_mech* h) {
   if (!h) return;
   if (h->module && driver().ModuleUnload) driver().ModuleUnload(h->module);
   if (h->d_fail) cudaFree(h->d_fail);
+  if (h->d_jac_scratch) cudaFree(h->d_jac_scratch);
+  for (auto& g : h->groups) if (g.second.module && driver().ModuleUnload) driver().ModuleUnload(g.second.module);
   for (void* p : h->stage) if (p) cudaFree(p);
   delete h;
 }
@@ -476,6 +578,94 @@ int pyro_net_production_rates(const pyro_mech* hc, int64_t n, const double* rho,
                      });
   if (rc) return rc;
   return input_is_energy ? maybe_checked(h, stream) : PYRO_OK;
+}
+
+
+int pyro_mech_prepare(const pyro_mech* hc, const char* kernels) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h) return fail(PYRO_EINVAL, "null mechanism");
+  std::string k = kernels ? kernels : "all";
+  std::vector<std::string> names;
+  if (k == "all") names = {"jvp", "vjp", "jac"};
+  else {
+    std::string item;
+    std::stringstream ss(k);
+    while (std::getline(ss, item, ',')) {
+      if (item == "jvp" || item == "vjp") names.push_back(item);
+      else if (item == "jacobian" || item == "jac") names.push_back("jac");
+      else if (!item.empty()) return fail(PYRO_EINVAL, "unknown kernel group '" + item + "'");
+    }
+  }
+  return ensure_groups(h, names);
+}
+
+int pyro_jvp(const pyro_mech* hc, int64_t n, const double* rho, const double* T, const double* Y,
+             const double* d_rho, const double* d_T, const double* d_Y, double* d_omega, void* stream) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n < 0 || (n > 0 && (!rho || !T || !Y || !d_rho || !d_T || !d_Y || !d_omega)))
+    return fail(PYRO_EINVAL, "pyro_jvp: bad arguments");
+  if (n == 0) return PYRO_OK;
+  if (int rc = check_device(h)) return rc;
+  if (int rc = ensure_groups(h, {"jvp"})) return rc;
+  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species();
+  return with_args(h, {{rho, s1, true, false}, {T, s1, true, false}, {Y, sN, true, false}, {d_rho, s1, true, false},
+                       {d_T, s1, true, false}, {d_Y, sN, true, false}, {d_omega, sN, false, true}},
+                   stream, [&](std::vector<void*>& d) {
+                     long long nn = n;
+                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &d[4], &d[5], &d[6]};
+                     return launch_deriv(h, h->groups["jvp"], n, stream, params);
+                   });
+}
+
+int pyro_vjp(const pyro_mech* hc, int64_t n, const double* rho, const double* T, const double* Y,
+             const double* omega_bar, double* rho_bar, double* T_bar, double* Y_bar, void* stream) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n < 0 || (n > 0 && (!rho || !T || !Y || !omega_bar || !rho_bar || !T_bar || !Y_bar)))
+    return fail(PYRO_EINVAL, "pyro_vjp: bad arguments");
+  if (n == 0) return PYRO_OK;
+  if (int rc = check_device(h)) return rc;
+  if (int rc = ensure_groups(h, {"vjp"})) return rc;
+  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species();
+  return with_args(h, {{rho, s1, true, false}, {T, s1, true, false}, {Y, sN, true, false}, {omega_bar, sN, true, false},
+                       {rho_bar, s1, false, true}, {T_bar, s1, false, true}, {Y_bar, sN, false, true}},
+                   stream, [&](std::vector<void*>& d) {
+                     long long nn = n;
+                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &d[4], &d[5], &d[6]};
+                     return launch_deriv(h, h->groups["vjp"], n, stream, params);
+                   });
+}
+
+int pyro_jacobian(const pyro_mech* hc, int64_t n, const double* rho, const double* T, const double* Y,
+                  double* J, void* stream) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n < 0 || (n > 0 && (!rho || !T || !Y || !J))) return fail(PYRO_EINVAL, "pyro_jacobian: bad arguments");
+  if (n == 0) return PYRO_OK;
+  if (int rc = check_device(h)) return rc;
+  if (int rc = ensure_groups(h, {"jac"})) return rc;
+  const pyro_mech::Group& G = h->groups["jac"];
+  int NP = h->m.n_species() + 1;
+  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species(), sJ = s1 * (size_t)NP * NP;
+  // per-block scratch for the per-reaction partials (grows on demand)
+  {
+    std::lock_guard<std::mutex> lock(h->mu);
+    int64_t need = (n + h->opt.deriv_block - 1) / h->opt.deriv_block;
+    int64_t grid = std::min<int64_t>(need, (int64_t)h->num_sms * G.blocks_per_sm);
+    size_t bytes = (size_t)grid * h->emitted.jac_slots * h->opt.deriv_block * sizeof(double);
+    if (bytes > h->jac_scratch_bytes) {
+      if (h->d_jac_scratch) cudaFree(h->d_jac_scratch);
+      h->d_jac_scratch = nullptr;
+      h->jac_scratch_bytes = 0;
+      cudaError_t e = cudaMalloc(&h->d_jac_scratch, bytes);
+      if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("Jacobian scratch allocation: ") + cudaGetErrorString(e));
+      h->jac_scratch_bytes = bytes;
+    }
+  }
+  return with_args(h, {{rho, s1, true, false}, {T, s1, true, false}, {Y, sN, true, false}, {J, sJ, false, true}},
+                   stream, [&](std::vector<void*>& d) {
+                     long long nn = n;
+                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &h->d_jac_scratch};
+                     return launch_deriv(h, G, n, stream, params);
+                   });
 }
 
 int pyro_nonconverged(const pyro_mech* hc, void* stream, int64_t* count) {

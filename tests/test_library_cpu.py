@@ -57,6 +57,16 @@ def test_compile_only_handle_and_static_counts(mech_files):
     assert ei.value.code == B.PYRO_EINVAL
 
 
+def test_derivative_kernels_compile_without_gpu(mech_files):
+    m = B.Mechanism(mech_files[0][0], "device=0")
+    m.prepare("jvp,vjp,jacobian")
+    for g in ("jvp", "vjp", "jac"):
+        assert m.stat(g + "_cubin_bytes") > 1000
+    assert m.stat("jacobian_scratch_doubles_per_point") > 0
+    with pytest.raises(B.PyroError):
+        m.prepare("hessian")
+
+
 def test_unbalanced_mechanism_is_rejected(tmp_path):
     mech = handmech.abcd_mechanism()
     mech.reactions[0].products = [(2, 1), (3, 2)]      # H + O2 -> OH + 2 O : O not balanced
