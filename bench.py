@@ -224,6 +224,61 @@ def derivative_rates(mech, synth, dev, stream, args, rank):
     return res
 
 
+
+def learned_guess_rates(mech, path, synth, dev, stream, args, rank):
+    """Train the guess network on 2^24 states, then time the temperature solve on 2^22
+    held-out states with the fixed 1200 K guess and with the learned guess, in the
+    library's default (FP32 then FP64) and the paper's FP64-only Newton."""
+    import time as _t
+    import torch
+    from paper_2503_24286_gb300 import binding as B
+    cfg = synth.CONFIGS[3]
+    res = {"workload": "train %d states (T ~ U[300, 2800] K, Dirichlet Y, e by the library's energy kernel), "
+                       "infer %d held-out states; MLP 54-64-64-1 SiLU, BF16 tensor-core inference"
+                       % (args.train_points, args.points)}
+    T, p, Y = synth.generate_states_torch(53, args.train_points, cfg["T"], cfg["p_atm"],
+                                          synth.STATE_SEED_BASE + 3 + 7919 * rank, dev)
+    del p
+    torch.cuda.synchronize(dev)
+    t0 = _t.perf_counter()
+    loss = mech.mlp_train(T, Y, "epochs=1;batch=1024;lr=1e-2;seed=1")
+    res["train_s"] = _t.perf_counter() - t0
+    res["train_final_loss"] = loss
+    del T, Y
+    T, p, Y = synth.generate_states_torch(53, args.points, cfg["T"], cfg["p_atm"],
+                                          synth.STATE_SEED_BASE + 3 + 104729 + 7919 * rank, dev)
+    e = mech.internal_energy(T, Y)
+    _, Tg = mech.mlp_guess(e, Y)
+    res["guess_rms_K"] = float(((Tg - T) ** 2).mean().sqrt().item())
+    out = torch.empty_like(T)
+    f = os.path.join(os.path.dirname(path), "guess.bin")
+    mech.mlp_save(f)
+    m64 = B.Mechanism(path, "newton=fp64")
+    m64.mlp_load(f)
+    steps = max(2, min(args.steps, 5))
+    for tag, m in (("newton_mixed", mech), ("newton_fp64", m64)):
+        r = {}
+        for guess in ("fixed", "learned"):
+            learned = guess == "learned"
+            _, it = m.temperature(e, Y, learned=learned, with_iters=True)
+            r[guess + "_iters_mean"] = float(it.double().mean().item())
+            for _ in range(3):
+                m.temperature(e, Y, learned=learned, out=out)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                m.temperature(e, Y, learned=learned, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = max_over_ranks(e0.elapsed_time(e1) / steps, dev)
+            r[guess + "_ms"] = ms
+            r[guess + "_states_per_s"] = args.points / (ms * 1e-3)
+            assert (torch.abs(out - T) / T).max().item() < 1e-10
+        res[tag] = r
+    return res
+
+
 def run_ours(args):
     import torch
     from paper_2503_24286_gb300 import binding as B
@@ -302,6 +357,9 @@ def run_ours(args):
     deriv = None
     if not args.no_derivatives:
         deriv = derivative_rates(mech, synth, dev, stream, args, rank)
+    learned = None
+    if not args.no_learned:
+        learned = learned_guess_rates(mech, path, synth, dev, stream, args, rank)
 
     # --- roofline of the timed kernel ---------------------------------------------------
     flops_fwd = mech.stat("omega_fp64_flops_per_point")
@@ -335,6 +393,7 @@ def run_ours(args):
                 "newton_iters_mean": iters_mean,
                 "jacobian_evals_per_s": deriv["jacobian_per_s"] if deriv else None,
                 "derivatives": deriv,
+                "learned_guess": learned,
                 "kernel_source_hash": src_hash,
                 "kernel": "pyro_omega (fused Newton T(e,Y) + omega), %d threads/block, %d blocks/SM"
                           % (int(mech.stat("block")), int(mech.stat("omega_blocks_per_sm")))}
@@ -353,6 +412,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=2 ** 15)
     ap.add_argument("--deriv-points", type=int, default=2 ** 20)
     ap.add_argument("--no-derivatives", action="store_true")
+    ap.add_argument("--train-points", type=int, default=2 ** 24)
+    ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

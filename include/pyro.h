@@ -93,8 +93,10 @@ int pyro_internal_energy(const pyro_mech* mech, int64_t n, const double* T, cons
 /* Temperature from internal energy by Newton iteration (Sec. A.3.1 Eq. delta_temp).
  * e: [n]; Y: [N][n]; T_out: [n].
  * guess_mode 0: start from T_guess[p] if T_guess != NULL, else 1200 K.
- * guess_mode 1: start from the learned initial guess (BF16 MLP, see
- *   pyro_mlp_load); PYRO_ENOMLP if none is loaded.
+ * guess_mode 1: start from the learned initial guess (BF16 MLP on the tensor
+ *   cores, see pyro_mlp_train / pyro_mlp_load); PYRO_ENOMLP if none is
+ *   loaded.  Points whose iteration from the guess fails restart from 1200 K
+ *   (their count then includes the failed attempt plus max_iter + 1).
  * Stops when |dT| <= 1e-10 T, then takes one more step; at most 50 FP64 steps.
  * iters_out (nullable, int32 [n]): Newton steps taken, -1 where the stop rule
  * was not met (T_out then holds the last iterate).  Non-convergence is also
@@ -144,6 +146,48 @@ int pyro_vjp(const pyro_mech* mech, int64_t n, const double* rho, const double* 
  * use, grown as needed). */
 int pyro_jacobian(const pyro_mech* mech, int64_t n, const double* rho, const double* T, const double* Y,
                   double* J, void* stream);
+
+/* ---- Learned initial guess for the Newton temperature solve ----------------
+ * Not in the paper (its Newton starts from a fixed guess, Sec. 4.3 listing of
+ * the JAX source term): a small MLP x -> 64 -> 64 -> 1 with SiLU, where the
+ * D = N+1 features are x_0 = (e - e_mean)/e_std and x_{1+k} = N Y_k (Y_k
+ * truncated to float first), and the output y gives
+ * T_guess = clip(T_mean + T_std y, 200 K, 3500 K).  BF16
+ * weights and activations (inputs, both hidden layers) with FP32 accumulation;
+ * inference runs on the tensor cores inside the temperature kernel
+ * (pyro_temperature with guess_mode 1), which still runs the full FP64 Newton
+ * solve to the same tolerance and falls back to 1200 K where the iteration from
+ * the guess fails.  Parameters (FP32 master copy, count pyro_mlp_n_params):
+ *   W1[64][D], b1[64], W2[64][64], b2[64], w3[64], b3   (row-major)
+ * norm4 = (e_mean, e_std, T_mean, T_std).  Supported for N <= 63 species. */
+int pyro_mlp_n_params(const pyro_mech* mech);
+int pyro_mlp_set_params(pyro_mech* mech, const double* params, const double* norm4);
+int pyro_mlp_get_params(const pyro_mech* mech, double* params, double* norm4);
+
+/* Train the network on device arrays T[n], Y[N][n]: the library computes e from
+ * (T, Y) with its energy kernel, sets the normalisation from the data,
+ * initialises the weights (seeded) and runs Adam on the mean squared error of
+ * the normalised temperature with hand-written forward/backward kernels.
+ * options: NULL or "epochs=1;batch=1024;lr=1e-2;seed=1" (the defaults;
+ * cosine-decayed learning rate).  final_loss
+ * (nullable) receives the last batch's loss.  Synchronous. */
+int pyro_mlp_train(pyro_mech* mech, int64_t n, const double* T, const double* Y, const char* options,
+                   double* final_loss, void* stream);
+
+/* Loss (mean squared error of y against (T - T_mean)/T_std) and its gradient
+ * over the n device states (e, Y, T), with the training kernel's arithmetic;
+ * grad is a host array of pyro_mlp_n_params doubles.  Synchronous. */
+int pyro_mlp_grad(const pyro_mech* mech, int64_t n, const double* e, const double* Y, const double* T,
+                  double* loss, double* grad);
+
+/* The network alone on the tensor cores: y_out[n] (normalised output) and
+ * T_guess[n]. */
+int pyro_mlp_guess(const pyro_mech* mech, int64_t n, const double* e, const double* Y, double* y_out,
+                   double* T_guess, void* stream);
+
+/* Save / load the parameters and normalisation (versioned binary "PYROMLP1"). */
+int pyro_mlp_save(const pyro_mech* mech, const char* path);
+int pyro_mlp_load(pyro_mech* mech, const char* path);
 
 /* Net production rates for callers that cannot allocate device memory.
  * No counterpart in the paper: this is a deployment variant of

@@ -33,6 +33,8 @@ EXPORTS = [
     "pyro_density", "pyro_internal_energy", "pyro_temperature", "pyro_net_production_rates",
     "pyro_nonconverged", "pyro_math_eval", "pyro_last_error", "pyro_version",
     "pyro_net_production_rates_noalloc", "pyro_mech_prepare", "pyro_jvp", "pyro_vjp", "pyro_jacobian",
+    "pyro_mlp_n_params", "pyro_mlp_set_params", "pyro_mlp_get_params", "pyro_mlp_train", "pyro_mlp_grad",
+    "pyro_mlp_guess", "pyro_mlp_save", "pyro_mlp_load",
 ]
 
 _lib = None
@@ -69,6 +71,14 @@ def lib() -> ctypes.CDLL:
         L.pyro_jvp.argtypes = [P, I64, D, D, D, D, D, D, D, P]
         L.pyro_vjp.argtypes = [P, I64, D, D, D, D, D, D, D, P]
         L.pyro_jacobian.argtypes = [P, I64, D, D, D, D, P]
+        L.pyro_mlp_n_params.argtypes = [P]
+        L.pyro_mlp_set_params.argtypes = [P, D, D]
+        L.pyro_mlp_get_params.argtypes = [P, D, D]
+        L.pyro_mlp_train.argtypes = [P, I64, D, D, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), P]
+        L.pyro_mlp_grad.argtypes = [P, I64, D, D, D, ctypes.POINTER(ctypes.c_double), D]
+        L.pyro_mlp_guess.argtypes = [P, I64, D, D, D, D, P]
+        L.pyro_mlp_save.argtypes = [P, ctypes.c_char_p]
+        L.pyro_mlp_load.argtypes = [P, ctypes.c_char_p]
         L.pyro_nonconverged.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64)]
         L.pyro_math_eval.argtypes = [P, ctypes.c_int, I64, D, D, P]
         L.pyro_last_error.restype = ctypes.c_char_p
@@ -235,6 +245,47 @@ class Mechanism:
         args = [rho, T, Y, J]
         _check(lib().pyro_jacobian(self._h, _n(rho), *[_ptr(a)[0] for a in args], _stream(args)))
         return J
+
+    # --- learned initial guess ---------------------------------------------------
+    def mlp_n_params(self) -> int:
+        return lib().pyro_mlp_n_params(self._h)
+
+    def mlp_set_params(self, params, norm4):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        nm = np.ascontiguousarray(norm4, dtype=np.float64)
+        _check(lib().pyro_mlp_set_params(self._h, ctypes.c_void_p(p.ctypes.data), ctypes.c_void_p(nm.ctypes.data)))
+
+    def mlp_get_params(self):
+        p = np.zeros(self.mlp_n_params())
+        nm = np.zeros(4)
+        _check(lib().pyro_mlp_get_params(self._h, ctypes.c_void_p(p.ctypes.data), ctypes.c_void_p(nm.ctypes.data)))
+        return p, nm
+
+    def mlp_train(self, T, Y, options: str = "", stream=None) -> float:
+        loss = ctypes.c_double()
+        args = [T, Y]
+        _check(lib().pyro_mlp_train(self._h, _n(T), _ptr(T)[0], _ptr(Y)[0], options.encode() if options else None,
+                                    ctypes.byref(loss), _stream(args)))
+        return loss.value
+
+    def mlp_grad(self, e, Y, T):
+        g = np.zeros(self.mlp_n_params())
+        loss = ctypes.c_double()
+        _check(lib().pyro_mlp_grad(self._h, _n(e), _ptr(e)[0], _ptr(Y)[0], _ptr(T)[0], ctypes.byref(loss),
+                                   ctypes.c_void_p(g.ctypes.data)))
+        return loss.value, g
+
+    def mlp_guess(self, e, Y):
+        y, Tg = _empty_like(e, (_n(e),)), _empty_like(e, (_n(e),))
+        args = [e, Y, y, Tg]
+        _check(lib().pyro_mlp_guess(self._h, _n(e), *[_ptr(a)[0] for a in args], _stream(args)))
+        return y, Tg
+
+    def mlp_save(self, path: str):
+        _check(lib().pyro_mlp_save(self._h, path.encode()))
+
+    def mlp_load(self, path: str):
+        _check(lib().pyro_mlp_load(self._h, path.encode()))
 
     def nonconverged(self, stream=None) -> int:
         c = ctypes.c_int64()

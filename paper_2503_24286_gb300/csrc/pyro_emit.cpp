@@ -837,6 +837,183 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
   s << "  }\n}\n";
 }
 
+// ---------------------------------------------------------------------------
+// learned initial guess: BF16 tensor-core MLP inference fused into the
+// temperature kernel (mma.sync m16n8k16, FP32 accumulation)
+// ---------------------------------------------------------------------------
+void emit_mlp(Src& s, const Mechanism& m) {
+  int N = m.n_species();
+  if (N + 1 > 64) return;       // the learned guess supports up to 63 species
+  s << "\n#define MLP_D " << (N + 1) << "\n";
+  s << R"(
+// bf16 helpers on bit patterns (round to nearest even for finite values)
+__device__ __forceinline__ unsigned pyro_f2bf(float f) {
+  unsigned u = __float_as_uint(f);
+  return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
+}
+__device__ __forceinline__ float pyro_bf2f(unsigned h) { return __uint_as_float(h << 16); }
+__device__ __forceinline__ float pyro_silu(float z) { return z / (1.0f + expf(-z)); }
+
+// one 16x8x16 BF16 MMA with FP32 accumulation
+__device__ __forceinline__ void pyro_mma(float* c, unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};\n"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+#define MLP_LD 36   // 32-bit words per staged row (64 bf16 + 8 pad): conflict-free fragments
+
+struct PyroMlpSmem {
+  unsigned W1[64 * MLP_LD];     // [out][in] bf16 pairs
+  unsigned W2[64 * MLP_LD];
+  float b1[64], b2[64], w3[64];
+  float b3, e_mean, e_inv, T_mean, T_std;
+  unsigned act[BLK / 32][32 * MLP_LD];   // per warp: 32 points x 64 features (bf16 pairs)
+};
+
+__device__ __forceinline__ void pyro_mlp_load(PyroMlpSmem& S, const unsigned short* __restrict__ wb,
+                                              const float* __restrict__ wf, const float* __restrict__ norm) {
+  const int D = MLP_D;
+  const int oW1 = 0, ob1 = 64 * D, oW2 = ob1 + 64, ob2 = oW2 + 64 * 64, ow3 = ob2 + 64, ob3 = ow3 + 64;
+  for (int q = threadIdx.x; q < 64 * 32; q += blockDim.x) {
+    int o = q >> 5, w = q & 31, i0 = 2 * w, i1 = 2 * w + 1;
+    unsigned lo = i0 < D ? wb[oW1 + o * D + i0] : 0u, hi = i1 < D ? wb[oW1 + o * D + i1] : 0u;
+    S.W1[o * MLP_LD + w] = lo | (hi << 16);
+    S.W2[o * MLP_LD + w] = (unsigned)wb[oW2 + o * 64 + i0] | ((unsigned)wb[oW2 + o * 64 + i1] << 16);
+  }
+  for (int o = threadIdx.x; o < 64; o += blockDim.x) {
+    S.b1[o] = wf[ob1 + o]; S.b2[o] = wf[ob2 + o]; S.w3[o] = pyro_bf2f(wb[ow3 + o]);
+  }
+  if (threadIdx.x == 0) {
+    S.b3 = wf[ob3]; S.e_mean = norm[0]; S.e_inv = 1.0f / norm[1]; S.T_mean = norm[2]; S.T_std = norm[3];
+  }
+}
+
+// one layer for the warp's 32 points: act (K = 64) -> act, y = bf16(silu(W act + b))
+__device__ __forceinline__ void pyro_mlp_layer(unsigned* act, const unsigned* W, const float* b, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  float c[2][8][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c[mt][nt][q] = 0.0f;
+#pragma unroll
+  for (int kt = 0; kt < 4; ++kt) {
+    unsigned a[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const unsigned* r0 = act + (mt * 16 + g) * MLP_LD + kt * 8 + t;
+      const unsigned* r1 = r0 + 8 * MLP_LD;
+      a[mt][0] = r0[0]; a[mt][1] = r1[0]; a[mt][2] = r0[4]; a[mt][3] = r1[4];
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const unsigned* wr = W + (nt * 8 + g) * MLP_LD + kt * 8 + t;
+      unsigned b0 = wr[0], b1 = wr[4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) pyro_mma(c[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      int col = nt * 8 + 2 * t;
+      float y0 = pyro_silu(c[mt][nt][0] + b[col]), y1 = pyro_silu(c[mt][nt][1] + b[col + 1]);
+      float y2 = pyro_silu(c[mt][nt][2] + b[col]), y3 = pyro_silu(c[mt][nt][3] + b[col + 1]);
+      act[(mt * 16 + g) * MLP_LD + nt * 4 + t] = pyro_f2bf(y0) | (pyro_f2bf(y1) << 16);
+      act[(mt * 16 + g + 8) * MLP_LD + nt * 4 + t] = pyro_f2bf(y2) | (pyro_f2bf(y3) << 16);
+    }
+  __syncwarp();
+}
+
+// Network output y (normalised) for this lane's point; all 32 lanes must call.
+__device__ __forceinline__ float pyro_mlp_eval(PyroMlpSmem& S, double e, const double* __restrict__ Yp, i64 n,
+                                               bool valid) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned* act = S.act[warp];
+  unsigned* row = act + lane * MLP_LD;
+  float x0 = valid ? (float)((e - (double)S.e_mean) * (double)S.e_inv) : 0.0f;
+  unsigned prev = pyro_f2bf(x0);
+)";
+  // features: x_0 = normalised e, x_{1+k} = Y_k; packed in bf16 pairs
+  for (int i = 1; i < 64; ++i) {
+    std::string v = i <= N ? "(valid ? pyro_f2bf(pdm::to_float_trunc(__ldg(Yp + (i64)" + std::to_string(i - 1) +
+                                 " * n)) * " + std::to_string(N) + ".0f) : 0u)" : "0u";
+    if (i % 2 == 1) s << "  row[" << (i / 2) << "] = prev | (" << v << " << 16);\n";
+    else s << "  prev = " << v << ";\n";
+  }
+  s << R"(  __syncwarp();
+  pyro_mlp_layer(act, S.W1, S.b1, lane);
+  pyro_mlp_layer(act, S.W2, S.b2, lane);
+  float y = S.b3;
+#pragma unroll 8
+  for (int w = 0; w < 32; ++w) {
+    unsigned v = row[w];
+    y = fmaf(S.w3[2 * w], pyro_bf2f(v & 0xffffu), y);
+    y = fmaf(S.w3[2 * w + 1], pyro_bf2f(v >> 16), y);
+  }
+  __syncwarp();
+  return y;
+}
+
+// Guess of the network alone (raw normalised output and the clipped temperature)
+extern "C" __global__ void __launch_bounds__(BLK) pyro_mlp_guess(i64 n, const double* __restrict__ g_e,
+    const double* __restrict__ g_Y, const unsigned short* __restrict__ wb, const float* __restrict__ wf,
+    const float* __restrict__ norm, double* __restrict__ g_y, double* __restrict__ g_T) {
+  __shared__ PyroMlpSmem S;
+  pyro_mlp_load(S, wb, wf, norm);
+  __syncthreads();
+  for (i64 base = (i64)blockIdx.x * BLK; base < n; base += (i64)gridDim.x * BLK) {
+    i64 p = base + threadIdx.x;
+    bool valid = p < n;
+    i64 pp = valid ? p : n - 1;
+    float y = pyro_mlp_eval(S, g_e[pp], g_Y + pp, n, valid);
+    if (valid) {
+      g_y[p] = (double)y;
+      g_T[p] = (double)fminf(fmaxf(fmaf(S.T_std, y, S.T_mean), 200.0f), 3500.0f);
+    }
+  }
+}
+
+// Temperature with the learned initial guess; falls back to 1200 K where the
+// Newton iteration from the guess does not converge.
+extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_mlp(i64 n, const double* __restrict__ g_e,
+    const double* __restrict__ g_Y, const unsigned short* __restrict__ wb, const float* __restrict__ wf,
+    const float* __restrict__ norm, int max_iter, double tol, double* __restrict__ g_T, int* __restrict__ g_iters,
+    unsigned long long* __restrict__ g_fail) {
+  __shared__ PyroMlpSmem S;
+  pyro_mlp_load(S, wb, wf, norm);
+  __syncthreads();
+  const float tolf = (float)tol;
+  for (i64 base = (i64)blockIdx.x * BLK; base < n; base += (i64)gridDim.x * BLK) {
+    i64 p = base + threadIdx.x;
+    bool valid = p < n;
+    i64 pp = valid ? p : n - 1;
+    double e = g_e[pp];
+    float y = pyro_mlp_eval(S, e, g_Y + pp, n, valid);
+    if (!valid) continue;
+    double T0 = (double)fminf(fmaxf(fmaf(S.T_std, y, S.T_mean), 200.0f), 3500.0f);
+    int it;
+    double T = pyro_tsolve(g_Y + p, n, e, T0, max_iter, tolf, &it);
+    if (it < 0) {
+      int it2;
+      T = pyro_tsolve(g_Y + p, n, e, 1200.0, max_iter, tolf, &it2);
+      it = it2 < 0 ? -1 : it2 + max_iter + 1;
+    }
+    g_T[p] = T;
+    if (g_iters) g_iters[p] = it;
+    if (it < 0) atomicAdd(g_fail, 1ull);
+  }
+}
+)";
+}
+
 }  // namespace
 
 EmitResult emit_module(const Mechanism& m, const EmitOptions& opt) {
@@ -907,6 +1084,10 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature(i64 n, const 
   }
 }
 )";
+
+  // ---- learned initial guess (inference fused into the temperature kernel) --------
+  emit_mlp(s, m);
+  out.stats["mlp_supported"] = (N + 1 <= 64) ? 1 : 0;
 
   // ---- net production rates (Eq. production_rates) ------------------------------
   Src r;   // count the forward per-point path separately

@@ -2,6 +2,7 @@
 // units of libpyro.
 #pragma once
 
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 struct pyro_mech;
@@ -23,5 +24,23 @@ int internal_fail(int code, const char* msg);
 int internal_launch_omega(const pyro_mech* h, int64_t n, const void* rho, const void* T_or_e,
                           int input_is_energy, const void* Y, void* T_out, void* omega,
                           unsigned long long* fail, void* stream);
+
+// ---- learned initial guess (pyro_mlp.cu) ----
+struct MlpState;
+int mlp_n_params(int D);
+int mlp_create(int D, MlpState** out);
+void mlp_free(MlpState* s);
+int mlp_set(MlpState* s, const double* params, const double* norm4);
+int mlp_get(MlpState* s, double* params, double* norm4);
+int mlp_grad(MlpState* s, int64_t n, int64_t start, int B, int N, const double* e, const double* Y,
+             const double* T, double* loss_out, double* grad_out, cudaStream_t st);
+int mlp_train(MlpState* s, int64_t n, int N, const double* e, const double* Y, const double* T, int epochs,
+              int batch, double lr, unsigned seed, double* final_loss, cudaStream_t st);
+int mlp_save(const MlpState* s, const char* path);
+int mlp_load(MlpState* s, const char* path);
+const void* mlp_device_bf16(const MlpState* s);
+const float* mlp_device_params(const MlpState* s);
+const float* mlp_host_norm(const MlpState* s);
+bool mlp_ready(const MlpState* s);
 
 }  // namespace pyro

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "pyro_emit.h"
+#include "pyro_internal.h"
 #include "pyro_mech.h"
 
 using namespace pyro;
@@ -224,6 +225,10 @@ struct pyro_mech {
   std::mutex group_mu;
   double* d_jac_scratch = nullptr;
   size_t jac_scratch_bytes = 0;
+  // learned initial guess
+  pyro::MlpState* mlp = nullptr;
+  float* mlp_norm_dev = nullptr;   // device copy of (e_mean, e_std, T_mean, T_std)
+  CUfunction f_mlp_guess = nullptr, f_temperature_mlp = nullptr;
   // staging buffers for host-pointer calls
   std::vector<void*> stage;
   std::vector<size_t> stage_bytes;
@@ -458,6 +463,13 @@ int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) 
     r = d.ModuleGetFunction(q.f, h->module, q.name);
     if (r != CUDA_SUCCESS) { pyro_mech_free(h); return fail(PYRO_ECUDA, std::string("missing kernel ") + q.name); }
   }
+  if (h->emitted.stats["mlp_supported"] > 0) {
+    if (d.ModuleGetFunction(&h->f_mlp_guess, h->module, "pyro_mlp_guess") != CUDA_SUCCESS ||
+        d.ModuleGetFunction(&h->f_temperature_mlp, h->module, "pyro_temperature_mlp") != CUDA_SUCCESS) {
+      pyro_mech_free(h);
+      return fail(PYRO_ECUDA, "missing learned-guess kernels");
+    }
+  }
   int smem = h->emitted.smem_dyn_bytes_omega;
   r = d.FuncSetAttribute(h->f_omega, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem);
   if (r != CUDA_SUCCESS) { pyro_mech_free(h); return fail(PYRO_ECUDA, "shared memory request of " + std::to_string(smem) + " B: " + cu_err(r)); }
@@ -480,6 +492,8 @@ void pyro_mech_free(pyro_mech* h) {
   if (h->module && driver().ModuleUnload) driver().ModuleUnload(h->module);
   if (h->d_fail) cudaFree(h->d_fail);
   if (h->d_jac_scratch) cudaFree(h->d_jac_scratch);
+  if (h->mlp) pyro::mlp_free(h->mlp);
+  if (h->mlp_norm_dev) cudaFree(h->mlp_norm_dev);
   for (auto& g : h->groups) if (g.second.module && driver().ModuleUnload) driver().ModuleUnload(g.second.module);
   for (void* p : h->stage) if (p) cudaFree(p);
   delete h;
@@ -538,9 +552,9 @@ int pyro_temperature(const pyro_mech* hc, int64_t n, const double* e, const doub
   pyro_mech* h = const_cast<pyro_mech*>(hc);
   if (!h || n < 0 || (n > 0 && (!e || !Y || !T_out))) return fail(PYRO_EINVAL, "pyro_temperature: bad arguments");
   if (guess_mode != 0 && guess_mode != 1) return fail(PYRO_EINVAL, "guess_mode must be 0 or 1");
-  if (guess_mode == 1) return fail(PYRO_ENOMLP, "no learned initial guess is loaded");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
+  if (guess_mode == 1 && !pyro::mlp_ready(h->mlp)) return fail(PYRO_ENOMLP, "no learned initial guess is loaded");
   size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species(), si = n * sizeof(int32_t);
   int rc = with_args(h, {{e, s1, true, false}, {Y, sN, true, false}, {T_guess, s1, true, false},
                          {T_out, s1, false, true}, {iters, si, false, true}},
@@ -548,6 +562,13 @@ int pyro_temperature(const pyro_mech* hc, int64_t n, const double* e, const doub
                        long long nn = n;
                        double Tg = 1200.0, tol = 1e-10;
                        int max_iter = 50;
+                       if (guess_mode == 1) {
+                         const void* wb = pyro::mlp_device_bf16(h->mlp);
+                         const float* wf = pyro::mlp_device_params(h->mlp);
+                         const float* nm = h->mlp_norm_dev;
+                         void* pm[] = {&nn, &d[0], &d[1], &wb, &wf, &nm, &max_iter, &tol, &d[3], &d[4], &h->d_fail};
+                         return launch(h, h->f_temperature_mlp, n, 8, 0, stream, pm);
+                       }
                        void* params[] = {&nn, &d[0], &d[1], &d[2], &Tg, &max_iter, &tol, &d[3], &d[4], &h->d_fail};
                        return launch(h, h->f_temperature, n, 8, 0, stream, params);
                      });
@@ -653,6 +674,8 @@ int pyro_jacobian(const pyro_mech* hc, int64_t n, const double* rho, const doubl
     size_t bytes = (size_t)grid * h->emitted.jac_slots * h->opt.deriv_block * sizeof(double);
     if (bytes > h->jac_scratch_bytes) {
       if (h->d_jac_scratch) cudaFree(h->d_jac_scratch);
+  if (h->mlp) pyro::mlp_free(h->mlp);
+  if (h->mlp_norm_dev) cudaFree(h->mlp_norm_dev);
       h->d_jac_scratch = nullptr;
       h->jac_scratch_bytes = 0;
       cudaError_t e = cudaMalloc(&h->d_jac_scratch, bytes);
@@ -666,6 +689,121 @@ int pyro_jacobian(const pyro_mech* hc, int64_t n, const double* rho, const doubl
                      void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &h->d_jac_scratch};
                      return launch_deriv(h, G, n, stream, params);
                    });
+}
+
+
+// ---- learned initial guess ---------------------------------------------------
+namespace {
+int ensure_mlp(pyro_mech* h) {
+  if (h->emitted.stats["mlp_supported"] <= 0) return fail(PYRO_EINVAL, "the learned guess supports at most 63 species");
+  if (!h->mlp) {
+    if (int rc = pyro::mlp_create(h->m.n_species() + 1, &h->mlp)) return rc;
+    if (cudaMalloc(&h->mlp_norm_dev, 4 * sizeof(float)) != cudaSuccess) return fail(PYRO_ECUDA, "MLP allocation");
+  }
+  return PYRO_OK;
+}
+int sync_norm(pyro_mech* h) {
+  if (cudaMemcpy(h->mlp_norm_dev, pyro::mlp_host_norm(h->mlp), 4 * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(PYRO_ECUDA, "MLP normalisation upload");
+  return PYRO_OK;
+}
+}  // namespace
+
+int pyro_mlp_n_params(const pyro_mech* h) { return h ? pyro::mlp_n_params(h->m.n_species() + 1) : 0; }
+
+int pyro_mlp_set_params(pyro_mech* h, const double* params, const double* norm4) {
+  if (!h || !params || !norm4) return fail(PYRO_EINVAL, "null argument");
+  if (int rc = check_device(h)) return rc;
+  if (int rc = ensure_mlp(h)) return rc;
+  if (int rc = pyro::mlp_set(h->mlp, params, norm4)) return rc;
+  return sync_norm(h);
+}
+
+int pyro_mlp_get_params(const pyro_mech* hc, double* params, double* norm4) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || !pyro::mlp_ready(h->mlp)) return fail(PYRO_ENOMLP, "no learned initial guess is loaded");
+  return pyro::mlp_get(h->mlp, params, norm4);
+}
+
+int pyro_mlp_train(pyro_mech* h, int64_t n, const double* T, const double* Y, const char* options,
+                   double* final_loss, void* stream) {
+  if (!h || n <= 0 || !T || !Y) return fail(PYRO_EINVAL, "pyro_mlp_train: bad arguments");
+  if (int rc = check_device(h)) return rc;
+  if (classify({T, Y}) != 1) return fail(PYRO_EINVAL, "pyro_mlp_train takes device arrays");
+  int epochs = 1, batch = 1024;
+  double lr = 1e-2;
+  unsigned seed = 1;
+  if (options) {
+    std::string str(options);
+    for (char& c : str) if (c == ',') c = ';';
+    std::stringstream ss(str);
+    std::string kv;
+    while (std::getline(ss, kv, ';')) {
+      if (kv.empty()) continue;
+      size_t eq = kv.find('=');
+      if (eq == std::string::npos) return fail(PYRO_EINVAL, "option without '='");
+      std::string k = kv.substr(0, eq), v = kv.substr(eq + 1);
+      if (k == "epochs") epochs = std::atoi(v.c_str());
+      else if (k == "batch") batch = std::atoi(v.c_str());
+      else if (k == "lr") lr = std::atof(v.c_str());
+      else if (k == "seed") seed = (unsigned)std::atol(v.c_str());
+      else return fail(PYRO_EINVAL, "unknown training option '" + k + "'");
+    }
+  }
+  if (epochs < 1 || batch < 64 || batch % 64 || !(lr > 0)) return fail(PYRO_EINVAL, "bad training options");
+  if (int rc = ensure_mlp(h)) return rc;
+  // internal energies of the training states by the library's energy kernel
+  double* e = nullptr;
+  if (cudaMalloc(&e, n * sizeof(double)) != cudaSuccess) return fail(PYRO_ECUDA, "training scratch allocation");
+  int rc = pyro_internal_energy(h, n, T, Y, e, nullptr, stream);
+  if (!rc) rc = pyro::mlp_train(h->mlp, n, h->m.n_species(), e, Y, T, epochs, batch, lr, seed, final_loss,
+                                (cudaStream_t)stream);
+  cudaFree(e);
+  if (rc) return rc;
+  return sync_norm(h);
+}
+
+int pyro_mlp_grad(const pyro_mech* hc, int64_t n, const double* e, const double* Y, const double* T,
+                  double* loss, double* grad) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n <= 0 || n > (1 << 30) || !e || !Y || !T) return fail(PYRO_EINVAL, "pyro_mlp_grad: bad arguments");
+  if (int rc = check_device(h)) return rc;
+  if (!pyro::mlp_ready(h->mlp)) return fail(PYRO_ENOMLP, "no learned initial guess is loaded");
+  if (classify({e, Y, T}) != 1) return fail(PYRO_EINVAL, "pyro_mlp_grad takes device arrays");
+  return pyro::mlp_grad(h->mlp, n, 0, (int)n, h->m.n_species(), e, Y, T, loss, grad, 0);
+}
+
+int pyro_mlp_guess(const pyro_mech* hc, int64_t n, const double* e, const double* Y, double* y_out,
+                   double* T_guess, void* stream) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n < 0 || (n > 0 && (!e || !Y || !y_out || !T_guess))) return fail(PYRO_EINVAL, "pyro_mlp_guess: bad arguments");
+  if (n == 0) return PYRO_OK;
+  if (int rc = check_device(h)) return rc;
+  if (!pyro::mlp_ready(h->mlp)) return fail(PYRO_ENOMLP, "no learned initial guess is loaded");
+  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species();
+  return with_args(h, {{e, s1, true, false}, {Y, sN, true, false}, {y_out, s1, false, true}, {T_guess, s1, false, true}},
+                   stream, [&](std::vector<void*>& d) {
+                     long long nn = n;
+                     const void* wb = pyro::mlp_device_bf16(h->mlp);
+                     const float* wf = pyro::mlp_device_params(h->mlp);
+                     const float* nm = h->mlp_norm_dev;
+                     void* pm[] = {&nn, &d[0], &d[1], &wb, &wf, &nm, &d[2], &d[3]};
+                     return launch(h, h->f_mlp_guess, n, 8, 0, stream, pm);
+                   });
+}
+
+int pyro_mlp_save(const pyro_mech* h, const char* path) {
+  if (!h || !path) return fail(PYRO_EINVAL, "null argument");
+  if (!pyro::mlp_ready(h->mlp)) return fail(PYRO_ENOMLP, "no learned initial guess is loaded");
+  return pyro::mlp_save(h->mlp, path);
+}
+
+int pyro_mlp_load(pyro_mech* h, const char* path) {
+  if (!h || !path) return fail(PYRO_EINVAL, "null argument");
+  if (int rc = check_device(h)) return rc;
+  if (int rc = ensure_mlp(h)) return rc;
+  if (int rc = pyro::mlp_load(h->mlp, path)) return rc;
+  return sync_norm(h);
 }
 
 int pyro_nonconverged(const pyro_mech* hc, void* stream, int64_t* count) {
