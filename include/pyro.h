@@ -62,6 +62,11 @@ typedef struct pyro_mech pyro_mech;
  *   checked=0|1         (1: calls that run Newton synchronise and return
  *                        PYRO_ENOCONV if any point failed to converge)
  *   deriv_block=<threads per block of the derivative kernels, default 64>
+ *   store=auto|shared|global  (where each thread keeps its state's species
+ *                        arrays: shared memory, or -- automatic when they do
+ *                        not fit, e.g. 160 species -- a library-owned global
+ *                        scratch per kernel; calls of the same kernel on one
+ *                        handle must then not overlap on the GPU)
  *   device=0|1          (0: parse, validate, emit and compile only; no CUDA
  *                        device is touched and nothing can be launched)
  * On success *out receives a handle to free with pyro_mech_free. */

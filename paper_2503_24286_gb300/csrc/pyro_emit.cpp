@@ -304,12 +304,37 @@ void emit_arg(Src& s, const Mechanism& m, const Reaction& r, double A, double b,
   s << "\n";
 }
 
+// Accumulators of the per-species sums (production rates, tangents, adjoints):
+// named registers, or -- for large mechanisms -- the kernel's output array
+// itself (read-modify-write through an opaque stride, L2-resident per block).
+struct AccCfg {
+  bool mem = false;
+  std::string base;   // pointer to the point's entry of the output array
+};
+AccCfg g_acc;
+
+std::string acc(const std::string& name, int k) {
+  if (!g_acc.mem) return name + std::to_string(k);
+  return g_acc.base + "[(i64)" + std::to_string(k) + " * opq(n)]";
+}
+
+void emit_acc_init(Src& s, const std::string& name, int N) {
+  if (!g_acc.mem) {
+    s << "    double ";
+    for (int k = 0; k < N; ++k) s << (k ? ", " : "") << name << k << " = 0.0";
+    s << ";\n";
+  } else {
+    s << "    #pragma unroll 1\n    for (int k = 0; k < NSP; ++k) " << g_acc.base << "[(i64)k * n] = 0.0;\n";
+  }
+}
+
 void emit_omega_update(Src& s, const Reaction& r, const std::string& R) {
   for (auto& q : net_nu(r)) {
     if (q.second == 0) continue;
-    if (q.second == 1) { s << " w" << q.first << " += " << R << ";"; s.add(); }
-    else if (q.second == -1) { s << " w" << q.first << " -= " << R << ";"; s.add(); }
-    else { s << " w" << q.first << " = fma(" << lit((double)q.second) << ", " << R << ", w" << q.first << ");"; s.fma(); }
+    std::string a = acc("w", q.first);
+    if (q.second == 1) { s << " " << a << " += " << R << ";"; s.add(); }
+    else if (q.second == -1) { s << " " << a << " -= " << R << ";"; s.add(); }
+    else { s << " " << a << " = fma(" << lit((double)q.second) << ", " << R << ", " << a << ");"; s.fma(); }
   }
   s << "\n";
 }
@@ -578,14 +603,16 @@ int nu_of(const std::vector<std::pair<int, int>>& side, int k) {
   return 0;
 }
 
-void emit_jvp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, int blk) {
+void emit_jvp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, int blk, const EmitOptions& opt) {
   int N = m.n_species();
   s << "\n// JVP: d omega = (d omega/d rho) d rho + (d omega/dT) dT + sum_i (d omega/dY_i) dY_i\n";
   s << "extern \"C\" __global__ void __launch_bounds__(" << blk << ") pyro_jvp(i64 n, const double* __restrict__ g_rho,\n"
        "    const double* __restrict__ g_T, const double* __restrict__ g_Y, const double* __restrict__ g_drho,\n"
-       "    const double* __restrict__ g_dT, const double* __restrict__ g_dY, double* __restrict__ g_dw) {\n"
+       "    const double* __restrict__ g_dT, const double* __restrict__ g_dY, double* __restrict__ g_dw,\n"
+       "    double* __restrict__ g_store) {\n"
        "  __shared__ double s_exp[512];\n  __shared__ double s_log[256];\n  extern __shared__ double s_dyn[];\n"
-       "  double* sL = s_dyn; double* sA = sL + NSP * BLKD; double* sdA = sA + NSP * BLKD; double* sdL = sdA + NSP * BLKD;\n"
+       "  double* sL = " << (opt.dgstore ? "g_store + (i64)blockIdx.x * 4 * NSP * BLKD" : "s_dyn") << ";\n"
+       "  double* sA = sL + NSP * BLKD; double* sdA = sA + NSP * BLKD; double* sdL = sdA + NSP * BLKD;\n"
        "  pyro_load_tables(s_exp, s_log);\n  __syncthreads();\n  const int t = threadIdx.x;\n"
        "  for (i64 p = (i64)blockIdx.x * BLKD + t; p < n; p += (i64)gridDim.x * BLKD) {\n"
        "    const double* Yp = g_Y + p; const double* dYp = g_dY + p;\n"
@@ -594,9 +621,10 @@ void emit_jvp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
        "    const double drr = drho * pdm::rcp(rho);\n"
        "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
   emit_species_deriv(s, m, C, DMode::JVP);
-  s << "    double ";
-  for (int k = 0; k < N; ++k) s << (k ? ", " : "") << "w" << k << " = 0.0";
-  s << ";\n";
+  g_acc.mem = opt.acc_mem;
+  g_acc.base = "Wp";
+  if (opt.acc_mem) s << "    double* Wp = g_dw + p;\n";
+  emit_acc_init(s, "w", N);
   for (int j = 0; j < m.n_reactions(); ++j) {
     const Reaction& r = m.reactions[j];
     s << "    { // reaction " << j << "\n";
@@ -622,18 +650,22 @@ void emit_jvp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
     emit_omega_update(s, r, "dR");
     s << "    }\n";
   }
-  for (int k = 0; k < N; ++k) s << "    g_dw[(i64)" << k << " * n + p] = w" << k << ";\n";
+  if (!opt.acc_mem)
+    for (int k = 0; k < N; ++k) s << "    g_dw[(i64)" << k << " * n + p] = w" << k << ";\n";
+  g_acc.mem = false;
   s << "  }\n}\n";
 }
 
-void emit_vjp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, int blk) {
+void emit_vjp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, int blk, const EmitOptions& opt) {
   int N = m.n_species();
   s << "\n// VJP: (rho_bar, T_bar, Y_bar) = (d omega/d(rho, T, Y))^T omega_bar\n";
   s << "extern \"C\" __global__ void __launch_bounds__(" << blk << ") pyro_vjp(i64 n, const double* __restrict__ g_rho,\n"
        "    const double* __restrict__ g_T, const double* __restrict__ g_Y, const double* __restrict__ g_wb,\n"
-       "    double* __restrict__ g_rhob, double* __restrict__ g_Tb, double* __restrict__ g_Yb) {\n"
+       "    double* __restrict__ g_rhob, double* __restrict__ g_Tb, double* __restrict__ g_Yb,\n"
+       "    double* __restrict__ g_store) {\n"
        "  __shared__ double s_exp[512];\n  __shared__ double s_log[256];\n  extern __shared__ double s_dyn[];\n"
-       "  double* sL = s_dyn; double* sA = sL + NSP * BLKD; double* sLp = sA + NSP * BLKD; double* sC = sLp + NSP * BLKD;\n"
+       "  double* sL = " << (opt.dgstore ? "g_store + (i64)blockIdx.x * 4 * NSP * BLKD" : "s_dyn") << ";\n"
+       "  double* sA = sL + NSP * BLKD; double* sLp = sA + NSP * BLKD; double* sC = sLp + NSP * BLKD;\n"
        "  pyro_load_tables(s_exp, s_log);\n  __syncthreads();\n  const int t = threadIdx.x;\n"
        "  for (i64 p = (i64)blockIdx.x * BLKD + t; p < n; p += (i64)gridDim.x * BLKD) {\n"
        "    const double* Yp = g_Y + p; const double* Wb = g_wb + p;\n"
@@ -641,9 +673,11 @@ void emit_vjp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
        "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
        "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
   emit_species_deriv(s, m, C, DMode::VJP);
-  s << "    double Tb = 0.0, Mtot = 0.0, rhobM = 0.0;\n    double ";
-  for (int k = 0; k < N; ++k) s << (k ? ", " : "") << "ab" << k << " = 0.0";
-  s << ";\n";
+  s << "    double Tb = 0.0, Mtot = 0.0, rhobM = 0.0;\n";
+  g_acc.mem = opt.acc_mem;
+  g_acc.base = "Ab";
+  if (opt.acc_mem) s << "    double* Ab = g_Yb + p;\n";
+  emit_acc_init(s, "ab", N);
   for (int j = 0; j < m.n_reactions(); ++j) {
     const Reaction& r = m.reactions[j];
     s << "    { // reaction " << j << "\n";
@@ -660,11 +694,11 @@ void emit_vjp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
     s << "\n      const double Db = Rb * kk;\n";
     auto fr = side_factors(r.reactants);
     for (int q = 0; q < (int)fr.size(); ++q)
-      s << "      ab" << fr[q] << " = fma(Db, " << prod_of(fr, "sA", q) << ", ab" << fr[q] << ");\n";
+      s << "      " << acc("ab", fr[q]) << " = fma(Db, " << prod_of(fr, "sA", q) << ", " << acc("ab", fr[q]) << ");\n";
     if (r.reversible) {
       auto fp = side_factors(r.products);
       for (int q = 0; q < (int)fp.size(); ++q)
-        s << "      ab" << fp[q] << " = fma(-Db, " << prod_of(fp, "sA", q) << ", ab" << fp[q] << ");\n";
+        s << "      " << acc("ab", fp[q]) << " = fma(-Db, " << prod_of(fp, "sA", q) << ", " << acc("ab", fp[q]) << ");\n";
     }
     if (r.kind != RX_ARRHENIUS) {
       s << "      const double Mb = Rb * kM * D; Mtot += Mb; rhobM = fma(Mb, mS, rhobM);\n";
@@ -677,10 +711,12 @@ void emit_vjp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
   }
   s << "    double rhob = 0.0;\n";
   for (int k = 0; k < N; ++k) {
-    s << "    { const double ta = ab" << k << " * sA" << sidx(k) << "; Tb = fma(ta, sLp" << sidx(k) << ", Tb); rhob += ta;\n";
-    s << "      g_Yb[(i64)" << k << " * n + p] = fma(ab" << k << ", pdm::exp(sL" << sidx(k) << ", s_exp) * rho, rho * fma(Mtot, "
+    s << "    { const double abk = " << acc("ab", k) << "; const double ta = abk * sA" << sidx(k)
+      << "; Tb = fma(ta, sLp" << sidx(k) << ", Tb); rhob += ta;\n";
+    s << "      g_Yb[(i64)" << k << " * n + p] = fma(abk, pdm::exp(sL" << sidx(k) << ", s_exp) * rho, rho * fma(Mtot, "
       << lit(1.0 / m.species[k].W) << ", sC" << sidx(k) << ")); }\n";
   }
+  g_acc.mem = false;
   s << "    g_Tb[p] = Tb;\n    g_rhob[p] = fma(rhob, pdm::rcp(rho), rhobM);\n  }\n}\n";
 }
 
@@ -1094,10 +1130,11 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature(i64 n, const 
   r << "\nextern \"C\" __global__ void __launch_bounds__(BLK, MINB) pyro_omega(i64 n, const double* __restrict__ g_rho,\n"
        "    const double* __restrict__ g_Tin, int energy_mode, const double* __restrict__ g_Y,\n"
        "    double* __restrict__ g_Tout, double* __restrict__ g_omega, double T_guess, int max_iter, double tol,\n"
-       "    unsigned long long* __restrict__ g_fail) {\n"
+       "    unsigned long long* __restrict__ g_fail, double* __restrict__ g_store) {\n"
        "  __shared__ double s_exp[512];\n  __shared__ double s_log[256];\n"
        "  extern __shared__ double s_dyn[];\n"
-       "  double* sL = s_dyn;\n  double* sA = s_dyn + NSP * BLK;\n"
+       "  double* sL = " << (opt.gstore ? "g_store + (i64)blockIdx.x * 2 * NSP * BLK" : "s_dyn") << ";\n"
+       "  double* sA = sL + NSP * BLK;\n"
        "  pyro_load_tables(s_exp, s_log);\n  __syncthreads();\n"
        "  const int t = threadIdx.x;\n  const float tolf = (float)tol;\n"
        "  for (i64 p = (i64)blockIdx.x * BLK + t; p < n; p += (i64)gridDim.x * BLK) {\n"
@@ -1111,11 +1148,14 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature(i64 n, const 
        "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
   r.log_(); r.rcp_();
   emit_species_forward(r, m, C);
-  r << "    double ";
-  for (int k = 0; k < N; ++k) r << (k ? ", " : "") << "w" << k << " = 0.0";
-  r << ";\n";
+  g_acc.mem = opt.acc_mem;
+  g_acc.base = "Wp";
+  if (opt.acc_mem) r << "    double* Wp = g_omega + p;\n";
+  emit_acc_init(r, "w", N);
   for (auto& grp : reaction_groups(m)) emit_reaction_group(r, m, grp);
-  for (int k = 0; k < N; ++k) r << "    g_omega[(i64)" << k << " * n + p] = w" << k << ";\n";
+  if (!opt.acc_mem)
+    for (int k = 0; k < N; ++k) r << "    g_omega[(i64)" << k << " * n + p] = w" << k << ";\n";
+  g_acc.mem = false;
   r << "  }\n}\n";
   s << r.o.str();
 
@@ -1128,17 +1168,17 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature(i64 n, const 
   emit_prelude(pre, m, dopt);
   pre << "#define BLKD " << opt.deriv_block << "\n";
   {
-    Src d; d << pre.o.str(); emit_jvp_kernel(d, m, C, opt.deriv_block); out.group_sources["jvp"] = d.o.str();
+    Src d; d << pre.o.str(); emit_jvp_kernel(d, m, C, opt.deriv_block, opt); out.group_sources["jvp"] = d.o.str();
   }
   {
-    Src d; d << pre.o.str(); emit_vjp_kernel(d, m, C, opt.deriv_block); out.group_sources["vjp"] = d.o.str();
+    Src d; d << pre.o.str(); emit_vjp_kernel(d, m, C, opt.deriv_block, opt); out.group_sources["vjp"] = d.o.str();
   }
   int nslots = 0;
   {
     Src d; d << pre.o.str(); emit_jacobian_kernel(d, m, C, opt.deriv_block, &nslots); out.group_sources["jac"] = d.o.str();
   }
   out.jac_slots = nslots;
-  out.smem_dyn_bytes_deriv = 4 * N * opt.deriv_block * (int)sizeof(double);
+  out.smem_dyn_bytes_deriv = opt.dgstore ? 0 : 4 * N * opt.deriv_block * (int)sizeof(double);
   out.stats["jacobian_scratch_doubles_per_point"] = nslots;
   out.stats["deriv_block"] = opt.deriv_block;
 
@@ -1150,7 +1190,10 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature(i64 n, const 
   out.stats["n_species"] = N;
   out.stats["n_reactions"] = m.n_reactions();
   out.stats["block"] = opt.block;
-  out.smem_dyn_bytes_omega = 2 * N * opt.block * (int)sizeof(double);
+  out.smem_dyn_bytes_omega = opt.gstore ? 0 : 2 * N * opt.block * (int)sizeof(double);
+  out.stats["omega_store_global"] = opt.gstore ? 1 : 0;
+  out.stats["deriv_store_global"] = opt.dgstore ? 1 : 0;
+  out.stats["accumulators_in_memory"] = opt.acc_mem ? 1 : 0;
   out.source = s.o.str();
   out.group_sources["fwd"] = out.source;
   return out;

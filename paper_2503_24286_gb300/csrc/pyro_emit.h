@@ -13,6 +13,12 @@ struct EmitOptions {
   int min_blocks = 2;         // __launch_bounds__ minimum resident blocks
   bool mixed_newton = true;   // FP32 Newton to ~1e-5, then FP64 Newton (else FP64 only)
   int deriv_block = 64;       // threads per block of the JVP / VJP / Jacobian kernels
+  // large mechanisms: per-point species arrays in a global scratch instead of
+  // shared memory (forward / derivative kernels), species accumulators in the
+  // output arrays instead of registers
+  bool gstore = false;
+  bool dgstore = false;
+  bool acc_mem = false;
 };
 
 struct EmitResult {

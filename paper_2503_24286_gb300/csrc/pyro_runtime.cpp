@@ -175,6 +175,7 @@ struct Options {
   bool checked = false;
   bool device = true;     // false: parse, validate, emit and compile only (no CUDA device needed)
   int deriv_block = 64;   // threads per block of the derivative kernels
+  int store = 0;          // 0 auto, 1 shared memory, 2 global scratch (per-state species arrays)
 };
 
 bool parse_options(const char* s, Options& o, std::string& err) {
@@ -193,6 +194,7 @@ bool parse_options(const char* s, Options& o, std::string& err) {
     else if (k == "cache") o.cache = v != "0";
     else if (k == "checked") o.checked = v != "0";
     else if (k == "device") o.device = v != "0";
+    else if (k == "store") { if (v == "auto") o.store = 0; else if (v == "shared") o.store = 1; else if (v == "global") o.store = 2; else { err = "store=auto|shared|global"; return false; } }
     else if (k == "deriv_block") { o.deriv_block = std::atoi(v.c_str()); if (o.deriv_block < 32 || o.deriv_block > 256 || o.deriv_block % 32) { err = "deriv_block must be a multiple of 32 in [32, 256]"; return false; } }
     else { err = "unknown option '" + k + "'"; return false; }
   }
@@ -220,11 +222,14 @@ struct pyro_mech {
     int blocks_per_sm = 0;
     bool failed = false;
     std::string err;
+    double* store = nullptr;   // per-block species arrays of this group (large mechanisms)
   };
   std::map<std::string, Group> groups;
   std::mutex group_mu;
   double* d_jac_scratch = nullptr;
   size_t jac_scratch_bytes = 0;
+  double* d_store = nullptr;       // per-block species arrays when they do not fit in shared memory
+  size_t store_bytes = 0;
   // learned initial guess
   pyro::MlpState* mlp = nullptr;
   float* mlp_norm_dev = nullptr;   // device copy of (e_mean, e_std, T_mean, T_std)
@@ -345,6 +350,18 @@ int maybe_checked(const pyro_mech* h, void* stream) {
 }
 
 
+// grow the per-block species-array store to `bytes` (allocation at load / first use)
+int ensure_store(pyro_mech* h, size_t bytes) {
+  if (bytes <= h->store_bytes) return PYRO_OK;
+  if (h->d_store) cudaFree(h->d_store);
+  h->d_store = nullptr;
+  h->store_bytes = 0;
+  cudaError_t e = cudaMalloc(&h->d_store, bytes);
+  if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("species-array store allocation: ") + cudaGetErrorString(e));
+  h->store_bytes = bytes;
+  return PYRO_OK;
+}
+
 const char* group_kernel(const std::string& g) {
   return g == "jvp" ? "pyro_jvp" : g == "vjp" ? "pyro_vjp" : "pyro_jacobian";
 }
@@ -396,6 +413,11 @@ int ensure_groups(pyro_mech* h, const std::vector<std::string>& names) {
     if (r != CUDA_SUCCESS || nb < 1) return fail(PYRO_ECUDA, std::string(group_kernel(todo[i])) + " does not fit on an SM");
     G.blocks_per_sm = nb;
     h->emitted.stats[todo[i] + "_blocks_per_sm"] = nb;
+    if (h->emitted.stats["deriv_store_global"] > 0 && todo[i] != "jac") {
+      size_t bytes = (size_t)h->num_sms * nb * 4 * h->m.n_species() * h->opt.deriv_block * sizeof(double);
+      cudaError_t e = cudaMalloc(&G.store, bytes);
+      if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("species-array store allocation: ") + cudaGetErrorString(e));
+    }
     h->emitted.stats[todo[i] + "_cubin_bytes"] = (double)cubins[i].size();
   }
   return PYRO_OK;
@@ -433,6 +455,14 @@ int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) 
   eo.min_blocks = h->opt.block <= 64 ? 4 : (h->opt.block <= 128 ? 2 : 1);
   eo.mixed_newton = h->opt.mixed;
   eo.deriv_block = h->opt.deriv_block;
+  {
+    const int N = h->m.n_species();
+    const size_t lim = 160 * 1024;
+    eo.gstore = h->opt.store == 2 || (h->opt.store == 0 && (size_t)2 * N * eo.block * 8 > lim);
+    eo.dgstore = h->opt.store == 2 || (h->opt.store == 0 && (size_t)4 * N * eo.deriv_block * 8 > lim);
+    eo.acc_mem = N > 64;
+    if (eo.gstore && eo.block > 64) eo.min_blocks = 1;
+  }
   h->emitted = emit_module(h->m, eo);
 
   // compile (or fetch from the cache)
@@ -478,6 +508,10 @@ int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) 
   if (r != CUDA_SUCCESS || nb < 1) { pyro_mech_free(h); return fail(PYRO_ECUDA, "omega kernel does not fit on an SM"); }
   h->omega_blocks_per_sm = nb;
   h->emitted.stats["omega_blocks_per_sm"] = nb;
+  if (h->emitted.stats["omega_store_global"] > 0) {
+    size_t bytes = (size_t)h->num_sms * nb * 2 * h->m.n_species() * h->opt.block * sizeof(double);
+    if (int rc = ensure_store(h, bytes)) { pyro_mech_free(h); return rc; }
+  }
   if (cudaMalloc(&h->d_fail, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(h->d_fail, 0, sizeof(unsigned long long)) != cudaSuccess) {
     pyro_mech_free(h);
@@ -492,9 +526,13 @@ void pyro_mech_free(pyro_mech* h) {
   if (h->module && driver().ModuleUnload) driver().ModuleUnload(h->module);
   if (h->d_fail) cudaFree(h->d_fail);
   if (h->d_jac_scratch) cudaFree(h->d_jac_scratch);
+  if (h->d_store) cudaFree(h->d_store);
   if (h->mlp) pyro::mlp_free(h->mlp);
   if (h->mlp_norm_dev) cudaFree(h->mlp_norm_dev);
-  for (auto& g : h->groups) if (g.second.module && driver().ModuleUnload) driver().ModuleUnload(g.second.module);
+  for (auto& g : h->groups) {
+    if (g.second.module && driver().ModuleUnload) driver().ModuleUnload(g.second.module);
+    if (g.second.store) cudaFree(g.second.store);
+  }
   for (void* p : h->stage) if (p) cudaFree(p);
   delete h;
 }
@@ -593,7 +631,8 @@ int pyro_net_production_rates(const pyro_mech* hc, int64_t n, const double* rho,
                        int em = input_is_energy ? 1 : 0;
                        double Tg = 1200.0, tol = 1e-10;
                        int max_iter = 50;
-                       void* params[] = {&nn, &d[0], &d[1], &em, &d[2], &d[3], &d[4], &Tg, &max_iter, &tol, &h->d_fail};
+                       void* params[] = {&nn, &d[0], &d[1], &em, &d[2], &d[3], &d[4], &Tg, &max_iter, &tol, &h->d_fail,
+                                         &h->d_store};
                        return launch(h, h->f_omega, n, h->omega_blocks_per_sm, h->emitted.smem_dyn_bytes_omega,
                                      stream, params);
                      });
@@ -607,7 +646,10 @@ int pyro_mech_prepare(const pyro_mech* hc, const char* kernels) {
   if (!h) return fail(PYRO_EINVAL, "null mechanism");
   std::string k = kernels ? kernels : "all";
   std::vector<std::string> names;
-  if (k == "all") names = {"jvp", "vjp", "jac"};
+  if (k == "all") {
+    names = {"jvp", "vjp"};
+    if (h->emitted.stats["deriv_store_global"] <= 0) names.push_back("jac");
+  }
   else {
     std::string item;
     std::stringstream ss(k);
@@ -633,7 +675,7 @@ int pyro_jvp(const pyro_mech* hc, int64_t n, const double* rho, const double* T,
                        {d_T, s1, true, false}, {d_Y, sN, true, false}, {d_omega, sN, false, true}},
                    stream, [&](std::vector<void*>& d) {
                      long long nn = n;
-                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &d[4], &d[5], &d[6]};
+                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &d[4], &d[5], &d[6], &h->groups["jvp"].store};
                      return launch_deriv(h, h->groups["jvp"], n, stream, params);
                    });
 }
@@ -651,7 +693,7 @@ int pyro_vjp(const pyro_mech* hc, int64_t n, const double* rho, const double* T,
                        {rho_bar, s1, false, true}, {T_bar, s1, false, true}, {Y_bar, sN, false, true}},
                    stream, [&](std::vector<void*>& d) {
                      long long nn = n;
-                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &d[4], &d[5], &d[6]};
+                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &d[4], &d[5], &d[6], &h->groups["vjp"].store};
                      return launch_deriv(h, h->groups["vjp"], n, stream, params);
                    });
 }
@@ -662,6 +704,9 @@ int pyro_jacobian(const pyro_mech* hc, int64_t n, const double* rho, const doubl
   if (!h || n < 0 || (n > 0 && (!rho || !T || !Y || !J))) return fail(PYRO_EINVAL, "pyro_jacobian: bad arguments");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
+  if (h->emitted.stats["deriv_store_global"] > 0)
+    return fail(PYRO_EINVAL, "the dense Jacobian needs the per-state species arrays in shared memory "
+                             "(4 N deriv_block 8 B <= 160 KB); use pyro_jvp / pyro_vjp for this mechanism");
   if (int rc = ensure_groups(h, {"jac"})) return rc;
   const pyro_mech::Group& G = h->groups["jac"];
   int NP = h->m.n_species() + 1;
@@ -674,8 +719,6 @@ int pyro_jacobian(const pyro_mech* hc, int64_t n, const double* rho, const doubl
     size_t bytes = (size_t)grid * h->emitted.jac_slots * h->opt.deriv_block * sizeof(double);
     if (bytes > h->jac_scratch_bytes) {
       if (h->d_jac_scratch) cudaFree(h->d_jac_scratch);
-  if (h->mlp) pyro::mlp_free(h->mlp);
-  if (h->mlp_norm_dev) cudaFree(h->mlp_norm_dev);
       h->d_jac_scratch = nullptr;
       h->jac_scratch_bytes = 0;
       cudaError_t e = cudaMalloc(&h->d_jac_scratch, bytes);
@@ -854,7 +897,8 @@ int internal_launch_omega(const pyro_mech* h, int64_t n, const void* rho, const 
   int em = input_is_energy ? 1 : 0;
   double Tg = 1200.0, tol = 1e-10;
   int max_iter = 50;
-  void* params[] = {&nn, &rho, &T_or_e, &em, &Y, &T_out, &omega, &Tg, &max_iter, &tol, &fail_ctr};
+  void* store = h->d_store;
+  void* params[] = {&nn, &rho, &T_or_e, &em, &Y, &T_out, &omega, &Tg, &max_iter, &tol, &fail_ctr, &store};
   return launch(h, h->f_omega, n, h->omega_blocks_per_sm, h->emitted.smem_dyn_bytes_omega, stream, params);
 }
 
