@@ -279,6 +279,47 @@ def learned_guess_rates(mech, path, synth, dev, stream, args, rank):
     return res
 
 
+
+def large_mechanism_rates(synth, dev, stream, args, rank):
+    """160 species / 1100 reactions at 2^21 states (energy input): one thread per
+    state (emitted, species arrays in global scratch) against one warp per state
+    (table-driven); also the warp variant on the 53-species workload."""
+    import torch
+    from paper_2503_24286_gb300 import binding as B
+    d = tempfile.mkdtemp()
+    path = os.path.join(d, "mech4.txt")
+    synth.write_mechanism(synth.config_mechanism(4), path)
+    cfg = synth.CONFIGS[4]
+    n = args.large_points
+    res = {"workload": "synthetic 160 species / 1100 reactions (80 third-body, 60 Troe), %d states, "
+                       "T ~ U[300, 2800] K, p ~ U[1, 40] atm, T from e + omega" % n}
+    mt = B.Mechanism(path)
+    mw = B.Mechanism(path, "variant=warp")
+    T, p, Y = synth.generate_states_torch(160, n, cfg["T"], cfg["p_atm"], synth.STATE_SEED_BASE + 4 + 7919 * rank, dev)
+    rho = mt.density(p, T, Y)
+    e = mt.internal_energy(T, Y)
+    del p
+    w = torch.empty((160, n), dtype=torch.float64, device=dev)
+    To = torch.empty(n, dtype=torch.float64, device=dev)
+    steps = max(2, min(args.steps, 5))
+    for tag, m in (("thread_per_state", mt), ("warp_per_state", mw)):
+        for _ in range(3):
+            m.net_production_rates(rho, Y, e=e, T_out=To, out=w)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            m.net_production_rates(rho, Y, e=e, T_out=To, out=w)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, dev)
+        res[tag + "_ms"] = ms
+        res[tag + "_states_per_s"] = n / (ms * 1e-3)
+        assert m.nonconverged() == 0
+    res["fp64_flops_per_state_static"] = mt.stat("omega_fp64_flops_per_point")
+    return res
+
+
 def run_ours(args):
     import torch
     from paper_2503_24286_gb300 import binding as B
@@ -360,6 +401,22 @@ def run_ours(args):
     learned = None
     if not args.no_learned:
         learned = learned_guess_rates(mech, path, synth, dev, stream, args, rank)
+    warp53 = None
+    large = None
+    if not args.no_large:
+        mw = B.Mechanism(path, "variant=warp")
+        for _ in range(3):
+            mw.net_production_rates(rho, Y, e=e, T_out=T, out=omega)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            mw.net_production_rates(rho, Y, e=e, T_out=T, out=omega)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_w = max_over_ranks(e0.elapsed_time(e1) / 3, dev)
+        warp53 = {"ms": ms_w, "states_per_s": n / (ms_w * 1e-3)}
+        large = large_mechanism_rates(synth, dev, stream, args, rank)
 
     # --- roofline of the timed kernel ---------------------------------------------------
     flops_fwd = mech.stat("omega_fp64_flops_per_point")
@@ -394,6 +451,8 @@ def run_ours(args):
                 "jacobian_evals_per_s": deriv["jacobian_per_s"] if deriv else None,
                 "derivatives": deriv,
                 "learned_guess": learned,
+                "warp_per_state_53sp": warp53,
+                "large_mechanism": large,
                 "kernel_source_hash": src_hash,
                 "kernel": "pyro_omega (fused Newton T(e,Y) + omega), %d threads/block, %d blocks/SM"
                           % (int(mech.stat("block")), int(mech.stat("omega_blocks_per_sm")))}
@@ -414,6 +473,8 @@ def main():
     ap.add_argument("--no-derivatives", action="store_true")
     ap.add_argument("--train-points", type=int, default=2 ** 24)
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--large-points", type=int, default=2 ** 21)
+    ap.add_argument("--no-large", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -62,6 +62,10 @@ typedef struct pyro_mech pyro_mech;
  *   checked=0|1         (1: calls that run Newton synchronise and return
  *                        PYRO_ENOCONV if any point failed to converge)
  *   deriv_block=<threads per block of the derivative kernels, default 64>
+ *   variant=thread|warp (net production rates: one thread per state with
+ *                        mechanism-specialised straight-line code (default),
+ *                        or one warp per state, lanes splitting species and
+ *                        reactions, driven by tables (no specialisation))
  *   store=auto|shared|global  (where each thread keeps its state's species
  *                        arrays: shared memory, or -- automatic when they do
  *                        not fit, e.g. 160 species -- a library-owned global

@@ -176,6 +176,7 @@ struct Options {
   bool device = true;     // false: parse, validate, emit and compile only (no CUDA device needed)
   int deriv_block = 64;   // threads per block of the derivative kernels
   int store = 0;          // 0 auto, 1 shared memory, 2 global scratch (per-state species arrays)
+  bool warp = false;      // net production rates: warp per state (table-driven) instead of thread per state
 };
 
 bool parse_options(const char* s, Options& o, std::string& err) {
@@ -194,6 +195,7 @@ bool parse_options(const char* s, Options& o, std::string& err) {
     else if (k == "cache") o.cache = v != "0";
     else if (k == "checked") o.checked = v != "0";
     else if (k == "device") o.device = v != "0";
+    else if (k == "variant") { if (v == "thread") o.warp = false; else if (v == "warp") o.warp = true; else { err = "variant=thread|warp"; return false; } }
     else if (k == "store") { if (v == "auto") o.store = 0; else if (v == "shared") o.store = 1; else if (v == "global") o.store = 2; else { err = "store=auto|shared|global"; return false; } }
     else if (k == "deriv_block") { o.deriv_block = std::atoi(v.c_str()); if (o.deriv_block < 32 || o.deriv_block > 256 || o.deriv_block % 32) { err = "deriv_block must be a multiple of 32 in [32, 256]"; return false; } }
     else { err = "unknown option '" + k + "'"; return false; }
@@ -231,6 +233,7 @@ struct pyro_mech {
   double* d_store = nullptr;       // per-block species arrays when they do not fit in shared memory
   size_t store_bytes = 0;
   // learned initial guess
+  pyro::WarpTables* warp = nullptr;
   pyro::MlpState* mlp = nullptr;
   float* mlp_norm_dev = nullptr;   // device copy of (e_mean, e_std, T_mean, T_std)
   CUfunction f_mlp_guess = nullptr, f_temperature_mlp = nullptr;
@@ -512,6 +515,10 @@ int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) 
     size_t bytes = (size_t)h->num_sms * nb * 2 * h->m.n_species() * h->opt.block * sizeof(double);
     if (int rc = ensure_store(h, bytes)) { pyro_mech_free(h); return rc; }
   }
+  if (h->opt.warp) {
+    if (int rc = pyro::warp_build(h->m, h->num_sms, &h->warp)) { pyro_mech_free(h); return rc; }
+    h->emitted.stats["variant_warp"] = 1;
+  }
   if (cudaMalloc(&h->d_fail, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(h->d_fail, 0, sizeof(unsigned long long)) != cudaSuccess) {
     pyro_mech_free(h);
@@ -528,6 +535,7 @@ void pyro_mech_free(pyro_mech* h) {
   if (h->d_jac_scratch) cudaFree(h->d_jac_scratch);
   if (h->d_store) cudaFree(h->d_store);
   if (h->mlp) pyro::mlp_free(h->mlp);
+  if (h->warp) pyro::warp_free(h->warp);
   if (h->mlp_norm_dev) cudaFree(h->mlp_norm_dev);
   for (auto& g : h->groups) {
     if (g.second.module && driver().ModuleUnload) driver().ModuleUnload(g.second.module);
@@ -631,6 +639,10 @@ int pyro_net_production_rates(const pyro_mech* hc, int64_t n, const double* rho,
                        int em = input_is_energy ? 1 : 0;
                        double Tg = 1200.0, tol = 1e-10;
                        int max_iter = 50;
+                       if (h->warp)
+                         return pyro::warp_launch_omega(h->warp, h->num_sms, n, (const double*)d[0], (const double*)d[1],
+                                                        em, (const double*)d[2], (double*)d[3], (double*)d[4],
+                                                        h->d_fail, (cudaStream_t)stream);
                        void* params[] = {&nn, &d[0], &d[1], &em, &d[2], &d[3], &d[4], &Tg, &max_iter, &tol, &h->d_fail,
                                          &h->d_store};
                        return launch(h, h->f_omega, n, h->omega_blocks_per_sm, h->emitted.smem_dyn_bytes_omega,

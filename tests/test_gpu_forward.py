@@ -224,3 +224,22 @@ def test_full_size_workload_sampled(mechs, dev):
     assert bad == 0
     assert np.max(np.abs(T[ii].cpu().numpy() - oT) / oT) <= TOL_T
     assert np.all(np.abs(w[:, ii].cpu().numpy() - ow) <= TOL_W * G + 1e-300)
+
+
+@pytest.mark.parametrize("idx", [0, 1])
+def test_warp_variant_parity(mechs, dev, mech_files, idx):
+    """One warp per state (table-driven) gives the oracle's results as well."""
+    from paper_2503_24286_gb300 import binding as B
+    _, orc = mechs[idx]
+    m = B.Mechanism(mech_files[0][idx], "variant=warp")
+    assert m.stat("variant_warp") == 1
+    st, rho, e = _inputs(idx, 777, orc, seed_offset=11)
+    w = m.net_production_rates(_t(rho, dev), _t(st.Y, dev), T=_t(st.T, dev)).cpu().numpy()
+    ow, G = orc.net_production_rates(rho, st.T, st.Y, with_gross=True)
+    assert np.all(np.abs(w - ow) <= TOL_W * G + 1e-300)
+    w2, T2 = m.net_production_rates(_t(rho, dev), _t(st.Y, dev), e=_t(e, dev))
+    oT, _, _ = orc.temperature(e, st.Y)
+    assert m.nonconverged() == 0
+    assert np.max(np.abs(T2.cpu().numpy() - oT) / oT) <= TOL_T
+    ow2, G2 = orc.net_production_rates(rho, oT, st.Y, with_gross=True)
+    assert np.all(np.abs(w2.cpu().numpy() - ow2) <= TOL_W * G2 + 1e-300)

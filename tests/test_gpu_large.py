@@ -112,3 +112,28 @@ def test_large_full_size_sampled(large, dev):
     ow, G = orc.net_production_rates(rs, oT, Ys, with_gross=True)
     assert bad == 0
     assert np.all(np.abs(w[:, ii].cpu().numpy() - ow) <= TOL_W * G + 1e-300)
+
+
+def test_large_warp_variant(large, dev, mech_files):
+    """Warp per state on the large mechanism: oracle parity, and the same results as
+    the thread-per-state kernels on the full-size workload."""
+    from paper_2503_24286_gb300 import binding as B
+    m, orc = large
+    mw = B.Mechanism(mech_files[0][4], "variant=warp")
+    st = synth.config_states(4, n=300, offset_seed=2)
+    rho = orc.density(st.p, st.T, st.Y)
+    e = orc.internal_energy(st.T, st.Y)
+    w, T = mw.net_production_rates(_t(rho, dev), _t(st.Y, dev), e=_t(e, dev))
+    oT, _, _ = orc.temperature(e, st.Y)
+    ow, G = orc.net_production_rates(rho, oT, st.Y, with_gross=True)
+    assert mw.nonconverged() == 0
+    assert np.max(np.abs(T.cpu().numpy() - oT) / oT) <= 1e-10
+    assert np.all(np.abs(w.cpu().numpy() - ow) <= TOL_W * G + 1e-300)
+    n = 2 ** 16
+    cfg = synth.CONFIGS[4]
+    T0, p, Y = synth.generate_states_torch(160, n, cfg["T"], cfg["p_atm"], 99, dev)
+    r = m.density(p, T0, Y)
+    ww = mw.net_production_rates(r, Y, T=T0)
+    wt = m.net_production_rates(r, Y, T=T0)
+    scale = wt.abs().amax(dim=0, keepdim=True) + 1e-300
+    assert ((ww - wt).abs() <= 1e-9 * scale).all().item()
