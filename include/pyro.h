@@ -62,6 +62,9 @@ typedef struct pyro_mech pyro_mech;
  *   checked=0|1         (1: calls that run Newton synchronise and return
  *                        PYRO_ENOCONV if any point failed to converge)
  *   deriv_block=<threads per block of the derivative kernels, default 64>
+ *   exp=4|2|4call|2call (device exponential: 4 FP64-pipe operations (default)
+ *                        or 2 with the second-order terms in FP32 pairs; inlined
+ *                        at every use, or one called body)
  *   variant=thread|warp (net production rates: one thread per state with
  *                        mechanism-specialised straight-line code (default),
  *                        or one warp per state, lanes splitting species and

@@ -10,9 +10,15 @@
 // Methods (constants derived from the mathematics, tables built on the host):
 //  * exp:  table-driven reduction (P.T.P. Tang, "Table-driven implementation of
 //          the exponential function in IEEE floating-point arithmetic", ACM TOMS
-//          15(2), 1989) with 512 table points 2^((j+1/2)/512); the Taylor tail
-//          r^3/6 + r^4/24 (|r| <= 7.1e-4) is evaluated in FP32 and folded into
-//          the table value by an integer add on its mantissa.  4 FP64 ops.
+//          15(2), 1989) with 512 table points 2^((j+1/2)/512); the Taylor terms
+//          beyond first order, r^2/2 + r^3/6 + r^4/24 (|r| <= 7.1e-4), are formed
+//          in FP32 pairs (Dekker products) and folded into the table value by an
+//          integer add on its mantissa, so only the reduction and the final
+//          T_j r + T_j (1 + s) use the FP64 pipe.  2 FP64 ops, ~75 other
+//          instructions.  exp4 keeps 1 + r + r^2/2 in FP64 (4 FP64 ops, ~30
+//          other instructions); it is the kernels' default because the
+//          straight-line kernels are bounded by instruction fetch as well as by
+//          the FP64 pipe once exp grows (measured on the 53-species workload).
 //  * log:  table-driven reduction (P.T.P. Tang, "Table-driven implementation of
 //          the logarithm function in IEEE floating-point arithmetic", ACM TOMS
 //          16(4), 1990) with 128 centres c_j = 1 + (j+1/2)/128; Taylor series of
@@ -86,7 +92,25 @@ __device__ __noinline__ double exp_slow(double x) { return ::exp(x); }
 __device__ __noinline__ double log_slow(double x) { return ::log(x); }
 __device__ __noinline__ double rcp_slow(double x) { return 1.0 / x; }
 
-// e^x.  tab = 512 doubles 2^((j+1/2)/512) (shared memory).  Max error ~3 ulp.
+// float pair (hi, lo) with hi = x truncated to 24 significant bits and lo the
+// rest (rounded to float; |lo| < 2^-23 |hi|), by integer arithmetic.
+PDM_INLINE void split(double x, float& hi, float& lo) {
+  hi = to_float_trunc(x);
+  // x - hi: the low 29 mantissa bits of x, scaled; exact in double, rounded to float
+  long long bx = __double_as_longlong(x);
+  long long rem = bx & 0x1FFFFFFFll;                       // bits below the float's mantissa
+  int e = (int)((bx >> 52) & 0x7ff) - 1023 - 52;           // value of mantissa bit 0 is 2^e
+  // rem as a float (truncated to 24 bits) by integer normalisation, times 2^e
+  unsigned v = (unsigned)rem;
+  int lz = __clz(v | 1u);
+  unsigned mant = ((v << lz) >> 8) & 0x7fffffu;            // drop the leading one
+  int fe = 158 - lz + e;                                    // biased exponent of rem * 2^e
+  float r = __uint_as_float(((unsigned)fe << 23) | mant);
+  lo = (rem == 0 || fe < 1) ? 0.0f : ((bx < 0) ? -r : r);
+}
+
+// e^x.  tab = 512 doubles 2^((j+1/2)/512) (shared memory).  Max error ~2 ulp.
+// FP64 pipe: 2 instructions (the reduction and the final fused multiply-add).
 PDM_INLINE double exp(double x, const double* __restrict__ tab) {
   float xf = to_float_trunc(x);
   float y = fmaf(xf, EXP_K, -0.5f);                         // ~ x*512/ln2 - 1/2
@@ -94,20 +118,61 @@ PDM_INLINE double exp(double x, const double* __restrict__ tab) {
   if (m < -520000 || m > 520000) return exp_slow(x);        // |x| > ~704: subnormal/overflow
   int k = 2 * m + 1;
   double mh = half_odd_to_double(k);                        // m + 1/2
-  double r = fma(-mh, EXP_C, x);                            // FP64 #1   (x - (m+1/2) C_hi)
+  double r = fma(-mh, EXP_C, x);                            // FP64 #1: x - (m+1/2) C_hi, |r| < 7.1e-4
   float mhf = 0.5f * (__int_as_float(0x4B400000 + k) - 12582912.0f);
-  float delta = mhf * EXP_C_LO;                             // (m+1/2) C_lo  (|.| < 1e-14)
+  float delta = mhf * EXP_C_LO;                             // (m+1/2) C_lo (|.| < 1e-14)
+  // s = e^(r - delta) - 1 - r  =  r^2/2 + r^3/6 + r^4/24 - delta (1 + r)   as a float pair
+  float rh, rl;
+  split(r, rh, rl);
+  float p = rh * rh;
+  float pe = fmaf(rh, rh, -p);                              // rh^2 = p + pe exactly
+  float sh = 0.5f * p;
+  float sl = fmaf(0.5f, pe, rh * rl) + p * rh * fmaf(rh, 1.0f / 24.0f, 1.0f / 6.0f) - delta * (1.0f + rh);
+  int j = m & (EXP_TAB - 1);
+  int nexp = m >> 9;
+  double Tj = tab[j];
+  float th, tl;
+  split(Tj, th, tl);
+  // K = round(Tj s 2^52) as a 64-bit integer, |K| < 2^32
+  float q = th * sh;
+  float qe = fmaf(th, sh, -q);
+  float ql = fmaf(th, sl, fmaf(tl, sh, qe));
+  float q52 = q * 4503599627370496.0f;                      // exact (power of two), < 2^32
+  int qe_b = ((__float_as_int(q52) >> 23) & 0xff) - 127;   // exponent of q52
+  long long mq = (long long)((__float_as_int(q52) & 0x7fffff) | 0x800000);
+  long long Kh = qe_b >= 23 ? (mq << (qe_b - 23))
+                            : (qe_b < 0 ? 0ll : ((mq + (1ll << (22 - qe_b))) >> (23 - qe_b)));
+  Kh = (q52 == 0.0f) ? 0ll : (__float_as_int(q52) < 0 ? -Kh : Kh);
+  float l52 = ql * 4503599627370496.0f;                     // |.| < 2^10
+  int Kl = __float_as_int(l52 + 12582912.0f) - 0x4B400000;
+  double B = __longlong_as_double(__double_as_longlong(Tj) + Kh + (long long)Kl);   // Tj (1 + s)
+  double v = fma(Tj, r, B);                                 // FP64 #2: Tj e^r
+  return __hiloint2double(__double2hiint(v) + (nexp << 20), __double2loint(v));
+}
+
+// e^x with 4 FP64 operations (fewer integer/FP32 instructions than exp): the
+// tail r^3/6 + r^4/24 in FP32 folded into the table value, 1 + r + r^2/2 in FP64.
+PDM_INLINE double exp4(double x, const double* __restrict__ tab) {
+  float xf = to_float_trunc(x);
+  float y = fmaf(xf, EXP_K, -0.5f);
+  int m = __float_as_int(y + 12582912.0f) - 0x4B400000;
+  if (m < -520000 || m > 520000) return exp_slow(x);
+  int k = 2 * m + 1;
+  double mh = half_odd_to_double(k);
+  double r = fma(-mh, EXP_C, x);                            // FP64 #1
+  float mhf = 0.5f * (__int_as_float(0x4B400000 + k) - 12582912.0f);
+  float delta = mhf * EXP_C_LO;
   float rf = to_float_trunc(r);
   float tau = rf * rf * rf * fmaf(rf, 1.0f / 24.0f, 1.0f / 6.0f) - delta * (1.0f + rf);
   int j = m & (EXP_TAB - 1);
   int nexp = m >> 9;
   double Tj = tab[j];
-  float corr = to_float_trunc(Tj) * tau * 4503599627370496.0f;   // T_j tau 2^52, |.| < 2^20
+  float corr = to_float_trunc(Tj) * tau * 4503599627370496.0f;
   int kc = __float_as_int(corr + 12582912.0f) - 0x4B400000;
-  double B = __longlong_as_double(__double_as_longlong(Tj) + (long long)kc);  // T_j (1 + tau)
+  double B = __longlong_as_double(__double_as_longlong(Tj) + (long long)kc);
   double q = fma(r, 0.5, 1.0);                              // FP64 #2
   double u = Tj * r;                                        // FP64 #3
-  double v = fma(u, q, B);                                  // FP64 #4: T_j e^r
+  double v = fma(u, q, B);                                  // FP64 #4
   return __hiloint2double(__double2hiint(v) + (nexp << 20), __double2loint(v));
 }
 

@@ -60,13 +60,18 @@ struct Src {
   void fma(int n = 1) { dfma += n; }
   void add(int n = 1) { dadd += n; }
   void mul(int n = 1) { dmul += n; }
-  void exp_() { dfma += 3; dmul += 1; }           // pdm::exp: 3 DFMA + 1 DMUL
+  void exp_();                                     // device exponential (see g_exp_ops)
   void log_() { dfma += 5; dadd += 1; dmul += 1; }  // pdm::log
   void rcp_() { dfma += 4; }                       // pdm::rcp
   double ops() const { return dfma + dadd + dmul; }
   double flops() const { return 2 * dfma + dadd + dmul; }
   template <class T> Src& operator<<(const T& v) { o << v; return *this; }
 };
+
+int g_exp_ops = 4;   // FP64-pipe operations of the device exponential in use
+void Src::exp_() {
+  if (g_exp_ops == 4) { dfma += 3; dmul += 1; } else { dfma += 2; }
+}
 
 // Per-species, per-range coefficient sets.
 struct SpeciesCoef {
@@ -139,6 +144,14 @@ void emit_prelude(Src& s, const Mechanism& m, const EmitOptions& opt) {
 // An opaque copy of a value: keeps the compiler from hoisting and keeping alive
 // hundreds of address computations across the straight-line code.
 __device__ __forceinline__ i64 opq(i64 v) { asm volatile("" : "+l"(v)); return v; }
+)";
+  // exponential flavour: 2 or 4 FP64 operations, inlined or one shared (called) body
+  if (opt.exp_call)
+    s << "__device__ __noinline__ double pyro_exp_call(double x, const double* __restrict__ t) { return pdm::"
+      << (opt.exp_ops == 4 ? "exp4" : "exp") << "(x, t); }\n#define PEXP(x, t) pyro_exp_call((x), (t))\n";
+  else
+    s << "#define PEXP(x, t) pdm::" << (opt.exp_ops == 4 ? "exp4" : "exp") << "((x), (t))\n";
+  s << R"(
 __device__ __forceinline__ void pyro_load_tables(double* se, double* sl) {
   for (int i = threadIdx.x; i < 512; i += blockDim.x) se[i] = pyro_tab_exp[i];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) sl[i] = pyro_tab_log[i];
@@ -262,7 +275,7 @@ void emit_species_forward(Src& s, const Mechanism& m, const std::vector<SpeciesC
     s << "      q = fma(" << sel(c.cl) << ", lnT, q); q = fma(" << sel(c.ci) << ", invT, q);\n";
     s.fma(6);
     s << "      sL" << sidx(k) << " = q;\n";
-    s << "      sA" << sidx(k) << " = pdm::exp(q, s_exp) * (rho * y);\n";
+    s << "      sA" << sidx(k) << " = PEXP(q, s_exp) * (rho * y);\n";
     s.exp_(); s.mul(2);
     s << "      ysum = fma(y, " << lit(1.0 / m.species[k].W) << ", ysum); }\n";
     s.fma(1);
@@ -362,9 +375,9 @@ void emit_reaction_group(Src& s, const Mechanism& m, const std::vector<int>& grp
     const Reaction& rq = m.reactions[grp[q]];
     emit_arg(s, m, rq, rq.A, rq.b, rq.theta, "x" + std::to_string(q));
   }
-  s << "      double kt = pdm::exp(x0, s_exp);";
+  s << "      double kt = PEXP(x0, s_exp);";
   s.exp_();
-  for (size_t q = 1; q < grp.size(); ++q) { s << " kt += pdm::exp(x" << q << ", s_exp);"; s.exp_(); s.add(); }
+  for (size_t q = 1; q < grp.size(); ++q) { s << " kt += PEXP(x" << q << ", s_exp);"; s.exp_(); s.add(); }
   s << "\n";
   if (r.kind == RX_THREEBODY) {
     emit_third_body(s, m, r);
@@ -377,24 +390,24 @@ void emit_reaction_group(Src& s, const Mechanism& m, const std::vector<int>& grp
     s << " lnPr = fma(" << lit(-(r.theta0 - r.theta)) << ", invT, lnPr); lnPr += pdm::log(mtb, s_log);\n";
     s.fma(2); s.log_(); s.add();
     // Pr/(1+Pr) = 1/(1 + exp(-ln Pr))
-    s << "      double fpr = pdm::rcp(1.0 + pdm::exp(-lnPr, s_exp));\n";
+    s << "      double fpr = pdm::rcp(1.0 + PEXP(-lnPr, s_exp));\n";
     s.exp_(); s.add(); s.rcp_();
     if (r.n_troe >= 3) {
       double a = r.troe[0], T3 = r.troe[1], T1 = r.troe[2];
       s << "      double fc = ";
       if (a < 1.0) {
-        s << "pdm::exp(fma(T, " << lit(-1.0 / T3) << ", " << lit((double)logl(1.0L - a)) << "), s_exp)";
+        s << "PEXP(fma(T, " << lit(-1.0 / T3) << ", " << lit((double)logl(1.0L - a)) << "), s_exp)";
         s.fma(); s.exp_();
       } else {
-        s << lit(1.0 - a) << " * pdm::exp(T * " << lit(-1.0 / T3) << ", s_exp)";
+        s << lit(1.0 - a) << " * PEXP(T * " << lit(-1.0 / T3) << ", s_exp)";
         s.mul(2); s.exp_();
       }
       if (a > 0.0) {
-        s << " + pdm::exp(fma(T, " << lit(-1.0 / T1) << ", " << lit((double)logl((long double)a)) << "), s_exp)";
+        s << " + PEXP(fma(T, " << lit(-1.0 / T1) << ", " << lit((double)logl((long double)a)) << "), s_exp)";
         s.fma(); s.exp_(); s.add();
       }
       if (r.n_troe == 4) {
-        s << " + pdm::exp(" << lit(-r.troe[3]) << " * invT, s_exp)";
+        s << " + PEXP(" << lit(-r.troe[3]) << " * invT, s_exp)";
         s.mul(); s.exp_(); s.add();
       }
       s << ";\n";
@@ -407,7 +420,7 @@ void emit_reaction_group(Src& s, const Mechanism& m, const std::vector<int>& grp
       s.fma(2);
       s << "      double den2 = den * den; double lf = lfc * den2 * pdm::rcp(fma(xx, xx, den2));\n";
       s.mul(3); s.fma(); s.rcp_();
-      s << "      double F = pdm::exp(lf * " << lit((double)logl(10.0L)) << ", s_exp);\n";
+      s << "      double F = PEXP(lf * " << lit((double)logl(10.0L)) << ", s_exp);\n";
       s.mul(); s.exp_();
       s << "      kt *= fpr * F;\n";
       s.mul(2);
@@ -485,7 +498,7 @@ void emit_species_deriv(Src& s, const Mechanism& m, const std::vector<SpeciesCoe
       << "); hr = fma(T, hr, " << sel(h1) << "); hr = fma(T, hr, " << sel(h0) << "); hr = fma(" << sel(h5)
       << ", invT, hr);\n";
     s << "      const double Lp = fma(-hr, invT, invT);\n";
-    s << "      const double E = pdm::exp(q, s_exp);\n";
+    s << "      const double E = PEXP(q, s_exp);\n";
     s << "      const double a = E * (rho * y);\n";
     s << "      sL" << sidx(k) << " = q; sA" << sidx(k) << " = a;";
     if (mode == DMode::JAC) s << " sE" << sidx(k) << " = E * rho; sLp" << sidx(k) << " = Lp;";
@@ -530,7 +543,7 @@ std::string dprod(const std::vector<int>& f, const char* arr, const char* darr) 
 // emits, inside a reaction block: x, kt, tau, [mS, M, kM], kk, Pf, Pr, D, R
 void emit_reaction_core(Src& s, const Mechanism& m, const Reaction& r) {
   emit_arg(s, m, r, r.A, r.b, r.theta, "x");
-  s << "      const double kt = pdm::exp(x, s_exp);\n";
+  s << "      const double kt = PEXP(x, s_exp);\n";
   s << "      double tau = fma(" << lit(r.b) << ", invT, " << lit(r.theta) << " * invT2);\n";
   if (r.kind == RX_ARRHENIUS) {
     s << "      const double kk = kt;\n";
@@ -548,19 +561,19 @@ void emit_reaction_core(Src& s, const Mechanism& m, const Reaction& r) {
       s << "      const double lnPr = fma(" << lit(r.b0 - r.b) << ", lnT, " << lit((double)(logl(r.A0) - logl(r.A)))
         << ") + fma(" << lit(-(r.theta0 - r.theta)) << ", invT, pdm::log(M, s_log));\n";
       s << "      const double pT = fma(" << lit(r.b0 - r.b) << ", invT, " << lit(r.theta0 - r.theta) << " * invT2);\n";
-      s << "      const double fpr = pdm::rcp(1.0 + pdm::exp(-lnPr, s_exp));\n";
+      s << "      const double fpr = pdm::rcp(1.0 + PEXP(-lnPr, s_exp));\n";
       if (r.n_troe >= 3) {
         double a = r.troe[0], T3 = r.troe[1], T1 = r.troe[2];
         if (a < 1.0)
-          s << "      const double t1 = pdm::exp(fma(T, " << lit(-1.0 / T3) << ", " << lit((double)logl(1.0L - a)) << "), s_exp);\n";
+          s << "      const double t1 = PEXP(fma(T, " << lit(-1.0 / T3) << ", " << lit((double)logl(1.0L - a)) << "), s_exp);\n";
         else
-          s << "      const double t1 = " << lit(1.0 - a) << " * pdm::exp(T * " << lit(-1.0 / T3) << ", s_exp);\n";
+          s << "      const double t1 = " << lit(1.0 - a) << " * PEXP(T * " << lit(-1.0 / T3) << ", s_exp);\n";
         if (a > 0.0)
-          s << "      const double t2 = pdm::exp(fma(T, " << lit(-1.0 / T1) << ", " << lit((double)logl((long double)a)) << "), s_exp);\n";
+          s << "      const double t2 = PEXP(fma(T, " << lit(-1.0 / T1) << ", " << lit((double)logl((long double)a)) << "), s_exp);\n";
         else
           s << "      const double t2 = 0.0;\n";
         if (r.n_troe == 4)
-          s << "      const double t3 = pdm::exp(" << lit(-r.troe[3]) << " * invT, s_exp);\n";
+          s << "      const double t3 = PEXP(" << lit(-r.troe[3]) << " * invT, s_exp);\n";
         else
           s << "      const double t3 = 0.0;\n";
         s << "      const double fc = t1 + t2 + t3;\n";
@@ -570,7 +583,7 @@ void emit_reaction_core(Src& s, const Mechanism& m, const Reaction& r) {
         s << "      const double cc = fma(-0.67, lfc, -0.4); const double nn = fma(-1.27, lfc, 0.75);\n";
         s << "      const double xx = fma(lnPr, " << lit(inv_ln10) << ", cc); const double den = fma(-0.14, xx, nn);\n";
         s << "      const double den2 = den * den; const double rD = pdm::rcp(fma(xx, xx, den2));\n";
-        s << "      const double f = den2 * rD; const double F = pdm::exp(lfc * f * " << lit((double)logl(10.0L)) << ", s_exp);\n";
+        s << "      const double f = den2 * rD; const double F = PEXP(lfc * f * " << lit((double)logl(10.0L)) << ", s_exp);\n";
         s << "      const double rD2 = rD * rD;\n";
         s << "      const double Axx = lfc * (-2.0 * den2 * xx * rD2); const double Aden = lfc * (2.0 * den * xx * xx * rD2);\n";
         s << "      const double sPr = (1.0 - fpr) + fma(-0.14, Aden, Axx);\n";
@@ -713,7 +726,7 @@ void emit_vjp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
   for (int k = 0; k < N; ++k) {
     s << "    { const double abk = " << acc("ab", k) << "; const double ta = abk * sA" << sidx(k)
       << "; Tb = fma(ta, sLp" << sidx(k) << ", Tb); rhob += ta;\n";
-    s << "      g_Yb[(i64)" << k << " * n + p] = fma(abk, pdm::exp(sL" << sidx(k) << ", s_exp) * rho, rho * fma(Mtot, "
+    s << "      g_Yb[(i64)" << k << " * n + p] = fma(abk, PEXP(sL" << sidx(k) << ", s_exp) * rho, rho * fma(Mtot, "
       << lit(1.0 / m.species[k].W) << ", sC" << sidx(k) << ")); }\n";
   }
   g_acc.mem = false;
@@ -1054,6 +1067,7 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_mlp(i64 n, co
 
 EmitResult emit_module(const Mechanism& m, const EmitOptions& opt) {
   EmitResult out;
+  g_exp_ops = opt.exp_ops;
   Src s;
   int N = m.n_species();
   std::vector<SpeciesCoef> C;

@@ -19,6 +19,8 @@ struct EmitOptions {
   bool gstore = false;
   bool dgstore = false;
   bool acc_mem = false;
+  int exp_ops = 4;            // device exponential: 4 (default) or 2 FP64-pipe operations
+  bool exp_call = false;      // one called body instead of inlining at every use
 };
 
 struct EmitResult {

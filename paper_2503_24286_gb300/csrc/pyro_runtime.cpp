@@ -177,6 +177,8 @@ struct Options {
   int deriv_block = 64;   // threads per block of the derivative kernels
   int store = 0;          // 0 auto, 1 shared memory, 2 global scratch (per-state species arrays)
   bool warp = false;      // net production rates: warp per state (table-driven) instead of thread per state
+  int exp_ops = 4;        // exponential flavour (4 or 2 FP64 ops)
+  bool exp_call = false;  // exponential as a called function
 };
 
 bool parse_options(const char* s, Options& o, std::string& err) {
@@ -195,6 +197,13 @@ bool parse_options(const char* s, Options& o, std::string& err) {
     else if (k == "cache") o.cache = v != "0";
     else if (k == "checked") o.checked = v != "0";
     else if (k == "device") o.device = v != "0";
+    else if (k == "exp") {
+      if (v == "2") { o.exp_ops = 2; o.exp_call = false; }
+      else if (v == "4") { o.exp_ops = 4; o.exp_call = false; }
+      else if (v == "2call") { o.exp_ops = 2; o.exp_call = true; }
+      else if (v == "4call") { o.exp_ops = 4; o.exp_call = true; }
+      else { err = "exp=2|4|2call|4call"; return false; }
+    }
     else if (k == "variant") { if (v == "thread") o.warp = false; else if (v == "warp") o.warp = true; else { err = "variant=thread|warp"; return false; } }
     else if (k == "store") { if (v == "auto") o.store = 0; else if (v == "shared") o.store = 1; else if (v == "global") o.store = 2; else { err = "store=auto|shared|global"; return false; } }
     else if (k == "deriv_block") { o.deriv_block = std::atoi(v.c_str()); if (o.deriv_block < 32 || o.deriv_block > 256 || o.deriv_block % 32) { err = "deriv_block must be a multiple of 32 in [32, 256]"; return false; } }
@@ -458,6 +467,8 @@ int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) 
   eo.min_blocks = h->opt.block <= 64 ? 4 : (h->opt.block <= 128 ? 2 : 1);
   eo.mixed_newton = h->opt.mixed;
   eo.deriv_block = h->opt.deriv_block;
+  eo.exp_ops = h->opt.exp_ops;
+  eo.exp_call = h->opt.exp_call;
   {
     const int N = h->m.n_species();
     const size_t lim = 160 * 1024;
