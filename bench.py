@@ -44,7 +44,7 @@ FP64_PEAK_GFLOPS = 2.0 * FP64_LANES_PER_SM * N_SM * SM_MAX_MHZ / 1e3   # 1258.6 
 # DRAM traffic of one launch of the timed kernel, from an ncu capture of this
 # kernel source (hash of the emitted source); None once the kernel changes.
 PROFILED_TRAFFIC = {
-    # 2^19-state ncu capture scaled by 8 to a 2^22-state launch (profiles/pyro_omega_gri53_energy.md)
+    # 2^19-state ncu capture scaled by 8 to a 2^22-state launch
     "953a6879ca9d63b7": 3.334e9,
 }
 
@@ -467,7 +467,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--points", type=int, default=2 ** 22)
-    ap.add_argument("--cpu-sample", type=int, default=2 ** 17)
+    ap.add_argument("--cpu-sample", type=int, default=2 ** 20)
     ap.add_argument("--ref-sample", type=int, default=2 ** 15)
     ap.add_argument("--deriv-points", type=int, default=2 ** 20)
     ap.add_argument("--no-derivatives", action="store_true")

@@ -14,7 +14,7 @@
 //   std::complex<double>  -- complex-step derivatives (Jacobian, JVP, VJP).
 //
 // Readings of passages that the paper leaves silent, ambiguous or garbled are
-// marked "reading (cN)" and listed in the design doc.
+// marked "reading (cN)"; each states the interpretation taken and why.
 //
 // Units: SI with kmol.  R = 8314.462618 J/(kmol K), p0 = 1 atm = 101325 Pa.
 

@@ -246,9 +246,13 @@ struct pyro_mech {
   pyro::MlpState* mlp = nullptr;
   float* mlp_norm_dev = nullptr;   // device copy of (e_mean, e_std, T_mean, T_std)
   CUfunction f_mlp_guess = nullptr, f_temperature_mlp = nullptr;
-  // staging buffers for host-pointer calls
-  std::vector<void*> stage;
-  std::vector<size_t> stage_bytes;
+  // host-pointer calls: chunked copy-in / kernel / copy-out pipeline
+  static constexpr int kSlots = 3;
+  cudaStream_t pipe_stream[kSlots] = {};
+  cudaEvent_t pipe_kdone[kSlots] = {};
+  cudaEvent_t pipe_start = nullptr;
+  std::vector<void*> stage[kSlots];
+  std::vector<size_t> stage_bytes[kSlots];
   std::mutex mu;
 };
 
@@ -266,8 +270,9 @@ int pointer_kind(const void* p) {
 }
 
 struct ArgSpec {
-  const void* host;     // caller pointer
-  size_t bytes;
+  const void* host;     // caller pointer (null: argument not used by this call)
+  int64_t rows;         // the array is [rows][n], point index fastest
+  size_t elem;          // bytes per element
   bool in, out;
 };
 
@@ -283,22 +288,68 @@ int classify(const std::vector<const void*>& ptrs) {
   return kind == -2 ? 1 : kind;
 }
 
-int ensure_stage(pyro_mech* h, size_t i, size_t bytes) {
-  if (h->stage.size() <= i) { h->stage.resize(i + 1, nullptr); h->stage_bytes.resize(i + 1, 0); }
-  if (h->stage_bytes[i] < bytes) {
-    if (h->stage[i]) cudaFree(h->stage[i]);
-    h->stage[i] = nullptr;
-    cudaError_t e = cudaMalloc(&h->stage[i], bytes);
-    if (e != cudaSuccess) { h->stage_bytes[i] = 0; return fail(PYRO_ECUDA, std::string("staging allocation: ") + cudaGetErrorString(e)); }
-    h->stage_bytes[i] = bytes;
+int ensure_stage(pyro_mech* h, int slot, size_t i, size_t bytes) {
+  auto& buf = h->stage[slot];
+  auto& have = h->stage_bytes[slot];
+  if (buf.size() <= i) { buf.resize(i + 1, nullptr); have.resize(i + 1, 0); }
+  if (have[i] < bytes) {
+    if (buf[i]) cudaFree(buf[i]);
+    buf[i] = nullptr;
+    have[i] = 0;
+    cudaError_t e = cudaMalloc(&buf[i], bytes);
+    if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("staging allocation: ") + cudaGetErrorString(e));
+    have[i] = bytes;
   }
   return PYRO_OK;
 }
 
-// Run `launch(device pointers)` either directly (device pointers) or through
-// staging buffers (host pointers: copy in, launch, copy out, synchronise).
+int ensure_pipe(pyro_mech* h) {
+  if (h->pipe_start) return PYRO_OK;
+  for (int s = 0; s < pyro_mech::kSlots; ++s) {
+    if (cudaStreamCreateWithFlags(&h->pipe_stream[s], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->pipe_kdone[s], cudaEventDisableTiming) != cudaSuccess)
+      return fail(PYRO_ECUDA, "creating the copy pipeline streams");
+  }
+  if (cudaEventCreateWithFlags(&h->pipe_start, cudaEventDisableTiming) != cudaSuccess)
+    return fail(PYRO_ECUDA, "creating the copy pipeline streams");
+  return PYRO_OK;
+}
+
+// `rows` rows of `width` bytes between pitched arrays: one 2D copy, or one copy
+// per row where a pitch exceeds what a 2D copy accepts (2^31 - 1 bytes).
+cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, int64_t rows,
+                      cudaMemcpyKind kind, cudaStream_t st) {
+  if (rows == 1) return cudaMemcpyAsync(dst, src, width, kind, st);
+  const size_t max_pitch = 2147483647u;
+  if (dpitch <= max_pitch && spitch <= max_pitch)
+    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, (size_t)rows, kind, st);
+  for (int64_t r = 0; r < rows; ++r) {
+    cudaError_t e = cudaMemcpyAsync((char*)dst + r * dpitch, (const char*)src + r * spitch, width, kind, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Points per chunk of a host-pointer call: about 8 chunks, each large enough to
+// fill the GPU, each slot's staging at most 1 GiB.
+int64_t chunk_points(int64_t n, size_t bytes_per_point) {
+  int64_t m = std::max<int64_t>((n + 7) / 8, 65536);
+  int64_t cap = std::max<int64_t>(4096, (int64_t)(((size_t)1 << 30) / std::max<size_t>(bytes_per_point, 1)));
+  m = std::min(m, cap);
+  m = (m + 255) / 256 * 256;
+  return std::min(m, n);
+}
+
+// Run `launch(device pointers, points, stream)` over n points.  Device pointers:
+// one launch on the caller's stream.  Host pointers: chunks of points go through
+// kSlots staging slots, each with its own stream, so that the copy-in of chunk
+// c+1 and the copy-out of chunk c-1 overlap the kernel of chunk c; the kernels
+// themselves run one after another (event chain: they share per-block scratch).
+// A chunk of a [rows][n] array is a pitched 2D copy into a dense [rows][m]
+// staging array, so the kernel sees the chunk as a problem of m points.  The
+// call returns after the last copy-out has completed.
 template <class F>
-int with_args(pyro_mech* h, std::vector<ArgSpec> args, void* stream, F launch) {
+int with_args(pyro_mech* h, int64_t n, std::vector<ArgSpec> args, void* stream, F launch) {
   std::vector<const void*> ptrs;
   for (auto& a : args) ptrs.push_back(a.host);
   int kind = classify(ptrs);
@@ -306,29 +357,56 @@ int with_args(pyro_mech* h, std::vector<ArgSpec> args, void* stream, F launch) {
   std::vector<void*> dev(args.size(), nullptr);
   if (kind == 1) {
     for (size_t i = 0; i < args.size(); ++i) dev[i] = const_cast<void*>(args[i].host);
-    return launch(dev);
+    return launch(dev, n, stream);
   }
   std::lock_guard<std::mutex> lock(h->mu);
-  cudaStream_t s = (cudaStream_t)stream;
-  for (size_t i = 0; i < args.size(); ++i) {
-    if (!args[i].host) continue;
-    int rc = ensure_stage(h, i, args[i].bytes);
-    if (rc) return rc;
-    dev[i] = h->stage[i];
-    if (args[i].in) {
-      cudaError_t e = cudaMemcpyAsync(dev[i], args[i].host, args[i].bytes, cudaMemcpyHostToDevice, s);
-      if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("H2D copy: ") + cudaGetErrorString(e));
+  if (int rc = ensure_pipe(h)) return rc;
+  size_t per_point = 0;
+  for (auto& a : args) if (a.host) per_point += (size_t)a.rows * a.elem;
+  const int64_t m = chunk_points(n, per_point);
+  const int64_t n_chunks = (n + m - 1) / m;
+  const int slots = (int)std::min<int64_t>(pyro_mech::kSlots, n_chunks);
+  for (int s = 0; s < slots; ++s)
+    for (size_t i = 0; i < args.size(); ++i)
+      if (args[i].host)
+        if (int rc = ensure_stage(h, s, i, (size_t)args[i].rows * m * args[i].elem)) return rc;
+  auto drain = [&](int code, const std::string& msg) {
+    for (int s = 0; s < slots; ++s) cudaStreamSynchronize(h->pipe_stream[s]);
+    return fail(code, msg);
+  };
+  // the pipeline starts after the work already queued on the caller's stream
+  if (cudaEventRecord(h->pipe_start, (cudaStream_t)stream) != cudaSuccess) return fail(PYRO_ECUDA, "event record");
+  for (int s = 0; s < slots; ++s)
+    if (cudaStreamWaitEvent(h->pipe_stream[s], h->pipe_start, 0) != cudaSuccess) return drain(PYRO_ECUDA, "stream wait");
+  for (int64_t c = 0; c < n_chunks; ++c) {
+    const int s = (int)(c % slots);
+    cudaStream_t st = h->pipe_stream[s];
+    const int64_t p0 = c * m, nc = std::min(m, n - p0);
+    for (size_t i = 0; i < args.size(); ++i) {
+      if (!args[i].host) continue;
+      dev[i] = h->stage[s][i];
+      if (!args[i].in) continue;
+      const size_t w = (size_t)nc * args[i].elem;
+      const char* src = (const char*)args[i].host + (size_t)p0 * args[i].elem;
+      cudaError_t e = copy_rows(dev[i], w, src, (size_t)n * args[i].elem, w, args[i].rows, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return drain(PYRO_ECUDA, std::string("H2D copy: ") + cudaGetErrorString(e));
+    }
+    if (c > 0 && cudaStreamWaitEvent(st, h->pipe_kdone[(c - 1) % slots], 0) != cudaSuccess)
+      return drain(PYRO_ECUDA, "stream wait");
+    if (int rc = launch(dev, nc, (void*)st)) { for (int q = 0; q < slots; ++q) cudaStreamSynchronize(h->pipe_stream[q]); return rc; }
+    if (cudaEventRecord(h->pipe_kdone[s], st) != cudaSuccess) return drain(PYRO_ECUDA, "event record");
+    for (size_t i = 0; i < args.size(); ++i) {
+      if (!args[i].host || !args[i].out) continue;
+      const size_t w = (size_t)nc * args[i].elem;
+      char* dst = (char*)const_cast<void*>(args[i].host) + (size_t)p0 * args[i].elem;
+      cudaError_t e = copy_rows(dst, (size_t)n * args[i].elem, dev[i], w, w, args[i].rows, cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return drain(PYRO_ECUDA, std::string("D2H copy: ") + cudaGetErrorString(e));
     }
   }
-  int rc = launch(dev);
-  if (rc) return rc;
-  for (size_t i = 0; i < args.size(); ++i) {
-    if (!args[i].host || !args[i].out) continue;
-    cudaError_t e = cudaMemcpyAsync(const_cast<void*>(args[i].host), dev[i], args[i].bytes, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("D2H copy: ") + cudaGetErrorString(e));
+  for (int s = 0; s < slots; ++s) {
+    cudaError_t e = cudaStreamSynchronize(h->pipe_stream[s]);
+    if (e != cudaSuccess) return drain(PYRO_ECUDA, std::string("stream synchronize: ") + cudaGetErrorString(e));
   }
-  cudaError_t e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("stream synchronize: ") + cudaGetErrorString(e));
   return PYRO_OK;
 }
 
@@ -552,7 +630,12 @@ void pyro_mech_free(pyro_mech* h) {
     if (g.second.module && driver().ModuleUnload) driver().ModuleUnload(g.second.module);
     if (g.second.store) cudaFree(g.second.store);
   }
-  for (void* p : h->stage) if (p) cudaFree(p);
+  for (int s = 0; s < pyro_mech::kSlots; ++s) {
+    for (void* p : h->stage[s]) if (p) cudaFree(p);
+    if (h->pipe_stream[s]) cudaStreamDestroy(h->pipe_stream[s]);
+    if (h->pipe_kdone[s]) cudaEventDestroy(h->pipe_kdone[s]);
+  }
+  if (h->pipe_start) cudaEventDestroy(h->pipe_start);
   delete h;
 }
 
@@ -580,12 +663,12 @@ int pyro_density(const pyro_mech* hc, int64_t n, const double* p, const double* 
   if (!h || n < 0 || (n > 0 && (!p || !T || !Y || !rho))) return fail(PYRO_EINVAL, "pyro_density: bad arguments");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
-  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species();
-  return with_args(h, {{p, s1, true, false}, {T, s1, true, false}, {Y, sN, true, false}, {rho, s1, false, true}},
-                   stream, [&](std::vector<void*>& d) {
-                     long long nn = n;
+  const int64_t NS = h->m.n_species();
+  return with_args(h, n, {{p, 1, 8, true, false}, {T, 1, 8, true, false}, {Y, NS, 8, true, false}, {rho, 1, 8, false, true}},
+                   stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
+                     long long nn = nc;
                      void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3]};
-                     return launch(h, h->f_density, n, 8, 0, stream, params);
+                     return launch(h, h->f_density, nc, 8, 0, st, params);
                    });
 }
 
@@ -595,12 +678,12 @@ int pyro_internal_energy(const pyro_mech* hc, int64_t n, const double* T, const 
   if (!h || n < 0 || (n > 0 && (!T || !Y || !e))) return fail(PYRO_EINVAL, "pyro_internal_energy: bad arguments");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
-  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species();
-  return with_args(h, {{T, s1, true, false}, {Y, sN, true, false}, {e, s1, false, true}, {cv, s1, false, true}},
-                   stream, [&](std::vector<void*>& d) {
-                     long long nn = n;
+  const int64_t NS = h->m.n_species();
+  return with_args(h, n, {{T, 1, 8, true, false}, {Y, NS, 8, true, false}, {e, 1, 8, false, true}, {cv, 1, 8, false, true}},
+                   stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
+                     long long nn = nc;
                      void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3]};
-                     return launch(h, h->f_energy, n, 8, 0, stream, params);
+                     return launch(h, h->f_energy, nc, 8, 0, st, params);
                    });
 }
 
@@ -612,11 +695,11 @@ int pyro_temperature(const pyro_mech* hc, int64_t n, const double* e, const doub
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
   if (guess_mode == 1 && !pyro::mlp_ready(h->mlp)) return fail(PYRO_ENOMLP, "no learned initial guess is loaded");
-  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species(), si = n * sizeof(int32_t);
-  int rc = with_args(h, {{e, s1, true, false}, {Y, sN, true, false}, {T_guess, s1, true, false},
-                         {T_out, s1, false, true}, {iters, si, false, true}},
-                     stream, [&](std::vector<void*>& d) {
-                       long long nn = n;
+  const int64_t NS = h->m.n_species();
+  int rc = with_args(h, n, {{e, 1, 8, true, false}, {Y, NS, 8, true, false}, {T_guess, 1, 8, true, false},
+                         {T_out, 1, 8, false, true}, {iters, 1, 4, false, true}},
+                     stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
+                       long long nn = nc;
                        double Tg = 1200.0, tol = 1e-10;
                        int max_iter = 50;
                        if (guess_mode == 1) {
@@ -624,10 +707,10 @@ int pyro_temperature(const pyro_mech* hc, int64_t n, const double* e, const doub
                          const float* wf = pyro::mlp_device_params(h->mlp);
                          const float* nm = h->mlp_norm_dev;
                          void* pm[] = {&nn, &d[0], &d[1], &wb, &wf, &nm, &max_iter, &tol, &d[3], &d[4], &h->d_fail};
-                         return launch(h, h->f_temperature_mlp, n, 8, 0, stream, pm);
+                         return launch(h, h->f_temperature_mlp, nc, 8, 0, st, pm);
                        }
                        void* params[] = {&nn, &d[0], &d[1], &d[2], &Tg, &max_iter, &tol, &d[3], &d[4], &h->d_fail};
-                       return launch(h, h->f_temperature, n, 8, 0, stream, params);
+                       return launch(h, h->f_temperature, nc, 8, 0, st, params);
                      });
   if (rc) return rc;
   return maybe_checked(h, stream);
@@ -642,22 +725,22 @@ int pyro_net_production_rates(const pyro_mech* hc, int64_t n, const double* rho,
   if (input_is_energy && !T_out) return fail(PYRO_EINVAL, "T_out is required when input_is_energy != 0");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
-  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species();
-  int rc = with_args(h, {{rho, s1, true, false}, {T_or_e, s1, true, false}, {Y, sN, true, false},
-                         {input_is_energy ? T_out : nullptr, s1, false, true}, {omega, sN, false, true}},
-                     stream, [&](std::vector<void*>& d) {
-                       long long nn = n;
+  const int64_t NS = h->m.n_species();
+  int rc = with_args(h, n, {{rho, 1, 8, true, false}, {T_or_e, 1, 8, true, false}, {Y, NS, 8, true, false},
+                         {input_is_energy ? T_out : nullptr, 1, 8, false, true}, {omega, NS, 8, false, true}},
+                     stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
+                       long long nn = nc;
                        int em = input_is_energy ? 1 : 0;
                        double Tg = 1200.0, tol = 1e-10;
                        int max_iter = 50;
                        if (h->warp)
-                         return pyro::warp_launch_omega(h->warp, h->num_sms, n, (const double*)d[0], (const double*)d[1],
+                         return pyro::warp_launch_omega(h->warp, h->num_sms, nc, (const double*)d[0], (const double*)d[1],
                                                         em, (const double*)d[2], (double*)d[3], (double*)d[4],
-                                                        h->d_fail, (cudaStream_t)stream);
+                                                        h->d_fail, (cudaStream_t)st);
                        void* params[] = {&nn, &d[0], &d[1], &em, &d[2], &d[3], &d[4], &Tg, &max_iter, &tol, &h->d_fail,
                                          &h->d_store};
-                       return launch(h, h->f_omega, n, h->omega_blocks_per_sm, h->emitted.smem_dyn_bytes_omega,
-                                     stream, params);
+                       return launch(h, h->f_omega, nc, h->omega_blocks_per_sm, h->emitted.smem_dyn_bytes_omega,
+                                     st, params);
                      });
   if (rc) return rc;
   return input_is_energy ? maybe_checked(h, stream) : PYRO_OK;
@@ -693,13 +776,13 @@ int pyro_jvp(const pyro_mech* hc, int64_t n, const double* rho, const double* T,
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
   if (int rc = ensure_groups(h, {"jvp"})) return rc;
-  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species();
-  return with_args(h, {{rho, s1, true, false}, {T, s1, true, false}, {Y, sN, true, false}, {d_rho, s1, true, false},
-                       {d_T, s1, true, false}, {d_Y, sN, true, false}, {d_omega, sN, false, true}},
-                   stream, [&](std::vector<void*>& d) {
-                     long long nn = n;
+  const int64_t NS = h->m.n_species();
+  return with_args(h, n, {{rho, 1, 8, true, false}, {T, 1, 8, true, false}, {Y, NS, 8, true, false}, {d_rho, 1, 8, true, false},
+                       {d_T, 1, 8, true, false}, {d_Y, NS, 8, true, false}, {d_omega, NS, 8, false, true}},
+                   stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
+                     long long nn = nc;
                      void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &d[4], &d[5], &d[6], &h->groups["jvp"].store};
-                     return launch_deriv(h, h->groups["jvp"], n, stream, params);
+                     return launch_deriv(h, h->groups["jvp"], nc, st, params);
                    });
 }
 
@@ -711,13 +794,13 @@ int pyro_vjp(const pyro_mech* hc, int64_t n, const double* rho, const double* T,
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
   if (int rc = ensure_groups(h, {"vjp"})) return rc;
-  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species();
-  return with_args(h, {{rho, s1, true, false}, {T, s1, true, false}, {Y, sN, true, false}, {omega_bar, sN, true, false},
-                       {rho_bar, s1, false, true}, {T_bar, s1, false, true}, {Y_bar, sN, false, true}},
-                   stream, [&](std::vector<void*>& d) {
-                     long long nn = n;
+  const int64_t NS = h->m.n_species();
+  return with_args(h, n, {{rho, 1, 8, true, false}, {T, 1, 8, true, false}, {Y, NS, 8, true, false}, {omega_bar, NS, 8, true, false},
+                       {rho_bar, 1, 8, false, true}, {T_bar, 1, 8, false, true}, {Y_bar, NS, 8, false, true}},
+                   stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
+                     long long nn = nc;
                      void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &d[4], &d[5], &d[6], &h->groups["vjp"].store};
-                     return launch_deriv(h, h->groups["vjp"], n, stream, params);
+                     return launch_deriv(h, h->groups["vjp"], nc, st, params);
                    });
 }
 
@@ -733,7 +816,7 @@ int pyro_jacobian(const pyro_mech* hc, int64_t n, const double* rho, const doubl
   if (int rc = ensure_groups(h, {"jac"})) return rc;
   const pyro_mech::Group& G = h->groups["jac"];
   int NP = h->m.n_species() + 1;
-  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species(), sJ = s1 * (size_t)NP * NP;
+  const int64_t NS = h->m.n_species();
   // per-block scratch for the per-reaction partials (grows on demand)
   {
     std::lock_guard<std::mutex> lock(h->mu);
@@ -749,11 +832,11 @@ int pyro_jacobian(const pyro_mech* hc, int64_t n, const double* rho, const doubl
       h->jac_scratch_bytes = bytes;
     }
   }
-  return with_args(h, {{rho, s1, true, false}, {T, s1, true, false}, {Y, sN, true, false}, {J, sJ, false, true}},
-                   stream, [&](std::vector<void*>& d) {
-                     long long nn = n;
+  return with_args(h, n, {{rho, 1, 8, true, false}, {T, 1, 8, true, false}, {Y, NS, 8, true, false}, {J, (int64_t)NP * NP, 8, false, true}},
+                   stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
+                     long long nn = nc;
                      void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &h->d_jac_scratch};
-                     return launch_deriv(h, G, n, stream, params);
+                     return launch_deriv(h, G, nc, st, params);
                    });
 }
 
@@ -846,15 +929,15 @@ int pyro_mlp_guess(const pyro_mech* hc, int64_t n, const double* e, const double
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
   if (!pyro::mlp_ready(h->mlp)) return fail(PYRO_ENOMLP, "no learned initial guess is loaded");
-  size_t s1 = n * sizeof(double), sN = s1 * h->m.n_species();
-  return with_args(h, {{e, s1, true, false}, {Y, sN, true, false}, {y_out, s1, false, true}, {T_guess, s1, false, true}},
-                   stream, [&](std::vector<void*>& d) {
-                     long long nn = n;
+  const int64_t NS = h->m.n_species();
+  return with_args(h, n, {{e, 1, 8, true, false}, {Y, NS, 8, true, false}, {y_out, 1, 8, false, true}, {T_guess, 1, 8, false, true}},
+                   stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
+                     long long nn = nc;
                      const void* wb = pyro::mlp_device_bf16(h->mlp);
                      const float* wf = pyro::mlp_device_params(h->mlp);
                      const float* nm = h->mlp_norm_dev;
                      void* pm[] = {&nn, &d[0], &d[1], &wb, &wf, &nm, &d[2], &d[3]};
-                     return launch(h, h->f_mlp_guess, n, 8, 0, stream, pm);
+                     return launch(h, h->f_mlp_guess, nc, 8, 0, st, pm);
                    });
 }
 
@@ -889,11 +972,10 @@ int pyro_math_eval(const pyro_mech* hc, int fn, int64_t n, const double* x, doub
   if (!h || n < 0 || fn < 0 || fn > 2 || (n > 0 && (!x || !y))) return fail(PYRO_EINVAL, "pyro_math_eval: bad arguments");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
-  size_t s1 = n * sizeof(double);
-  return with_args(h, {{x, s1, true, false}, {y, s1, false, true}}, stream, [&](std::vector<void*>& d) {
-    long long nn = n;
+  return with_args(h, n, {{x, 1, 8, true, false}, {y, 1, 8, false, true}}, stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
+    long long nn = nc;
     void* params[] = {&fn, &nn, &d[0], &d[1]};
-    return launch(h, h->f_math, n, 8, 0, stream, params);
+    return launch(h, h->f_math, nc, 8, 0, st, params);
   });
 }
 

@@ -9,7 +9,7 @@ the CPU oracle read what it writes and evaluate the method independently.
 Mechanism shape follows the problem statement of the paper's formulation
 appendix (Sec. A.1, Eqs. for reactions / mass action / Arrhenius / Troe falloff
 and the NASA polynomials of Sec. A.1); parameter distributions are those of the
-synthetic workloads described in the design doc:
+synthetic workloads:
 
 * elements with standard atomic weights; species of small compositions;
 * two-range NASA-7 fits (T_mid = 1000 K) to smooth positive cp/R curves built
@@ -115,7 +115,7 @@ class Mechanism:
 
 # ----------------------------------------------------------------------------
 # Workload table (synthetic stand-ins for the paper's H2/air and GRI-3.0-sized
-# mechanisms; see DESIGN.md "Inputs").
+# mechanisms).
 # ----------------------------------------------------------------------------
 
 CONFIGS = {
