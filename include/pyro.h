@@ -117,6 +117,20 @@ int pyro_temperature(const pyro_mech* mech, int64_t n, const double* e, const do
                      const double* T_guess, int guess_mode, double* T_out, int32_t* iters_out,
                      void* stream);
 
+/* Mixture enthalpy h = sum_k Y_k h_k / W_k (per unit mass; h_k from Sec. A.1
+ * Eq. nasa_poly) and, if cp != NULL, c_p = dh/dT.  T: [n]; Y: [N][n]; h, cp: [n]
+ * out. */
+int pyro_enthalpy(const pyro_mech* mech, int64_t n, const double* T, const double* Y,
+                  double* h, double* cp, void* stream);
+
+/* Temperature from the mixture enthalpy (Sec. A.3.1: the Newton inversion with h
+ * and c_p in place of e and c_v, for low-Mach and characteristic-boundary use).
+ * h: [n]; Y: [N][n]; T_guess: nullable [n] (else 1200 K); T_out: [n];
+ * iters_out: nullable int32 [n].  Stop rule, iteration cap, FP32-then-FP64
+ * iteration and failure reporting as in pyro_temperature. */
+int pyro_temperature_enthalpy(const pyro_mech* mech, int64_t n, const double* h, const double* Y,
+                              const double* T_guess, double* T_out, int32_t* iters_out, void* stream);
+
 /* Net production rates omega_k = sum_j nu_kj R_j (Sec. A.1 Eq. production_rates)
  * with R_j by the law of mass action (Eq. reaction_rates).
  * rho: [n]; T_or_e: [n] temperature, or internal energy if input_is_energy != 0

@@ -64,6 +64,18 @@ def lib():
         L.orc_jacobian.argtypes = [P, I64, D, D, D, D]
         L.orc_jvp.argtypes = [P, I64, D, D, D, D, D, D, D]
         L.orc_vjp.argtypes = [P, I64, D, D, D, D, D, D, D]
+        L.orc_enthalpy.argtypes = [P, I64, D, D, D, D]
+        L.orc_temperature_enthalpy.restype = I64
+        L.orc_temperature_enthalpy.argtypes = [P, I64, D, D, D, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_int, D, ctypes.POINTER(ctypes.c_int32)]
+        L.orc_temperature_bisect_enthalpy.argtypes = [P, I64, D, D, ctypes.c_double, ctypes.c_double, D]
+        L.orc_jacobian_adiabatic.argtypes = [P, I64, D, D, D, D]
+        L.orc_source_at_energy.argtypes = [P, I64, D, D, D, D]
+        L.orc_solve_dense.restype = ctypes.c_int
+        L.orc_solve_dense.argtypes = [ctypes.c_int, D, D]
+        L.orc_cn_step.restype = I64
+        L.orc_cn_step.argtypes = [P, I64, ctypes.c_double, D, D, D, ctypes.c_double, ctypes.c_int, D, D,
+                                  ctypes.POINTER(ctypes.c_int32)]
         L.orc_mlp_forward.argtypes = [ctypes.c_int, ctypes.c_int, D, I64, D, D]
         L.orc_mlp_loss_grad.restype = ctypes.c_double
         L.orc_mlp_loss_grad.argtypes = [ctypes.c_int, ctypes.c_int, D, I64, D, D, D]
@@ -154,6 +166,29 @@ class Oracle:
         lib().orc_temperature_bisect(self._h, e.size, _d(e), _d(Y), float(lo), float(hi), _d(T))
         return T
 
+    def enthalpy(self, T, Y, with_cp=False):
+        T, Y = _c(T), _c(Y)
+        h = np.zeros_like(T)
+        cp = np.zeros_like(T) if with_cp else None
+        lib().orc_enthalpy(self._h, T.size, _d(T), _d(Y), _d(h), _d(cp))
+        return (h, cp) if with_cp else h
+
+    def temperature_enthalpy(self, h, Y, guess=None, T_guess=1200.0, tol=1e-10, max_iter=50):
+        h, Y = _c(h), _c(Y)
+        T = np.zeros_like(h)
+        it = np.zeros(h.size, dtype=np.int32)
+        g = _c(guess) if guess is not None else None
+        bad = lib().orc_temperature_enthalpy(self._h, h.size, _d(h), _d(Y), _d(g), float(T_guess),
+                                             float(tol), int(max_iter), _d(T),
+                                             it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        return T, it, int(bad)
+
+    def temperature_bisect_enthalpy(self, h, Y, lo=100.0, hi=5000.0):
+        h, Y = _c(h), _c(Y)
+        T = np.zeros_like(h)
+        lib().orc_temperature_bisect_enthalpy(self._h, h.size, _d(h), _d(Y), float(lo), float(hi), _d(T))
+        return T
+
     # --- kinetics ---------------------------------------------------------
     def reaction_data(self, rho, T, Y):
         rho, T, Y = _c(rho), _c(T), _c(Y)
@@ -190,6 +225,31 @@ class Oracle:
         lib().orc_jacobian(self._h, T.size, _d(rho), _d(T), _d(Y), _d(J))
         return J
 
+    def jacobian_adiabatic(self, rho, T, Y):
+        """[N*N, n]: dS_j/dY_k (row j, column k) of S = W omega at fixed (rho, e)."""
+        rho, T, Y = _c(rho), _c(T), _c(Y)
+        J = np.zeros((self.N * self.N, T.size))
+        lib().orc_jacobian_adiabatic(self._h, T.size, _d(rho), _d(T), _d(Y), _d(J))
+        return J
+
+    def source_at_energy(self, rho, e, Y):
+        """S = W omega [N, n] with T solved from (e, Y)."""
+        rho, e, Y = _c(rho), _c(e), _c(Y)
+        S = np.zeros((self.N, e.size))
+        lib().orc_source_at_energy(self._h, e.size, _d(rho), _d(e), _d(Y), _d(S))
+        return S
+
+    def cn_step(self, dt, rho, T, Y, tol=1e-12, max_newton=20):
+        """One Crank-Nicolson step of dY/dt = S/rho at fixed (rho, e): (Y_next [N, n],
+        T_next [n], Newton steps [n] (-1: failed), number failed)."""
+        rho, T, Y = _c(rho), _c(T), _c(Y)
+        n = T.size
+        Yo, To = np.zeros((self.N, n)), np.zeros(n)
+        it = np.zeros(n, dtype=np.int32)
+        bad = lib().orc_cn_step(self._h, n, float(dt), _d(rho), _d(T), _d(Y), float(tol), int(max_newton),
+                                _d(Yo), _d(To), it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        return Yo, To, it, int(bad)
+
     def jvp(self, rho, T, Y, drho, dT, dY):
         args = [_c(a) for a in (rho, T, Y, drho, dT, dY)]
         out = np.zeros((self.N, args[1].size))
@@ -202,6 +262,15 @@ class Oracle:
         rb, Tb, Yb = np.zeros(n), np.zeros(n), np.zeros((self.N, n))
         lib().orc_vjp(self._h, n, _d(rho), _d(T), _d(Y), _d(wbar), _d(rb), _d(Tb), _d(Yb))
         return rb, Tb, Yb
+
+
+def solve_dense(A, b):
+    """x of A x = b by the oracle's Gaussian elimination with partial pivoting."""
+    A = np.array(A, dtype=np.float64, order="C")
+    x = np.array(b, dtype=np.float64)
+    if lib().orc_solve_dense(x.size, _d(A), _d(x)) != 0:
+        raise ZeroDivisionError("singular matrix")
+    return x
 
 
 # --- MLP (model definition in FP64 with bf16 rounding points) -------------

@@ -240,23 +240,47 @@ template <class S> S cv_mass(const OMech& m, S T, const S* Y) {
   return c;
 }
 
+// h = sum_k Y_k h_k / W_k: mixture enthalpy per unit mass (Sec. A.3.1, the
+// enthalpy variant of the temperature inversion)
+template <class S> S enthalpy_mass(const OMech& m, S T, const S* Y) {
+  S h = 0;
+  for (int k = 0; k < m.N(); ++k) h += Y[k] * (R_GAS * T * h_RT(m.sp[k], T)) / m.sp[k].W;
+  return h;
+}
+
+// c_p = sum_k Y_k cp_k / W_k = dh/dT
+template <class S> S cp_mass(const OMech& m, S T, const S* Y) {
+  S c = 0;
+  for (int k = 0; k < m.N(); ++k) c += Y[k] * (R_GAS * cp_R(m.sp[k], T)) / m.sp[k].W;
+  return c;
+}
+
+// the quantity the inversion matches (e or h) and its temperature derivative (c_v or c_p)
+double mixture_caloric(const OMech& m, double T, const double* Y, bool enthalpy) {
+  return enthalpy ? enthalpy_mass(m, T, Y) : internal_energy(m, T, Y);
+}
+double mixture_heat_capacity(const OMech& m, double T, const double* Y, bool enthalpy) {
+  return enthalpy ? cp_mass(m, T, Y) : cv_mass(m, T, Y);
+}
+
 // Newton iteration for T(e, Y)       (Sec. A.3.1, Eq. delta_temp)
 //   T_{m+1} = T_m - (Y.e(T_m) - e) / c_v(T_m)
 // reading (c7): stop once |dT| <= tol*T_{m+1}, then take one more step;
 // reading (c6): iterates clamped to [100, 5000] K.  Returns iterations used,
 // or -1 if max_iter was reached without meeting the stop rule.
+// The enthalpy variant (enthalpy = true) is the same iteration on h with c_p.
 int temperature_newton(const OMech& m, double e, const double* Y, double T0, double tol,
-                       int max_iter, double* T_out) {
+                       int max_iter, double* T_out, bool enthalpy = false) {
   double T = T0;
   for (int it = 1; it <= max_iter; ++it) {
-    double dT = -(internal_energy(m, T, Y) - e) / cv_mass(m, T, Y);
+    double dT = -(mixture_caloric(m, T, Y, enthalpy) - e) / mixture_heat_capacity(m, T, Y, enthalpy);
     double Tn = T + dT;
     if (Tn < 100.0) Tn = 100.0;
     if (Tn > 5000.0) Tn = 5000.0;
     bool done = std::fabs(Tn - T) <= tol * Tn;
     T = Tn;
     if (done) {
-      double dT2 = -(internal_energy(m, T, Y) - e) / cv_mass(m, T, Y);
+      double dT2 = -(mixture_caloric(m, T, Y, enthalpy) - e) / mixture_heat_capacity(m, T, Y, enthalpy);
       T = T + dT2;
       *T_out = T;
       return it + 1;
@@ -266,13 +290,14 @@ int temperature_newton(const OMech& m, double e, const double* Y, double T0, dou
   return -1;
 }
 
-// Bisection on [lo, hi] for e(T) = e (independent check of the Newton result).
-double temperature_bisect(const OMech& m, double e, const double* Y, double lo, double hi) {
-  double flo = internal_energy(m, lo, Y) - e;
+// Bisection on [lo, hi] for e(T) = e, or h(T) = h (independent check of the Newton result).
+double temperature_bisect(const OMech& m, double e, const double* Y, double lo, double hi,
+                          bool enthalpy = false) {
+  double flo = mixture_caloric(m, lo, Y, enthalpy) - e;
   for (int it = 0; it < 200; ++it) {
     double mid = 0.5 * (lo + hi);
     if (mid <= lo || mid >= hi) break;
-    double fm = internal_energy(m, mid, Y) - e;
+    double fm = mixture_caloric(m, mid, Y, enthalpy) - e;
     if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else { hi = mid; }
   }
   return 0.5 * (lo + hi);
@@ -402,6 +427,97 @@ template <class S> S temperature_rate(const OMech& m, S rho, S T, const S* Y, co
 
 typedef std::complex<double> cplx;
 const double CS_H = 1e-30;   // complex-step size (no subtractive cancellation)
+
+// Chemical Jacobian J_jk = dS_j/dY_k of the source S_j = W_j omega_j (Eq. massfrac_ode,
+// Eq. chem_jacobian) at fixed rho and e: T follows Y through the inversion of
+// Eq. int_energy.  Complex step through that inversion: starting from the real
+// root T of e(T, Y) = e, Newton steps in complex arithmetic carry the derivative
+// dT/dY_k into the imaginary part (one step is exact to O(h^2); two are taken).
+// J is row-major [j][k], N x N.
+void source_jacobian_adiabatic(const OMech& m, double rho, double T, const double* Y, double* J) {
+  const int N = m.N();
+  const double e = internal_energy(m, T, Y);
+  std::vector<cplx> y(N), w(N);
+  for (int c = 0; c < N; ++c) {
+    for (int k = 0; k < N; ++k) y[k] = cplx(Y[k], k == c ? CS_H : 0.0);
+    cplx Tc(T, 0.0);
+    for (int it = 0; it < 2; ++it) Tc -= (internal_energy<cplx>(m, Tc, y.data()) - e) / cv_mass<cplx>(m, Tc, y.data());
+    net_production_rates<cplx>(m, cplx(rho, 0.0), Tc, y.data(), w.data());
+    for (int j = 0; j < N; ++j) J[j * N + c] = m.sp[j].W * w[j].imag() / CS_H;
+  }
+}
+
+// Solve A x = b (A n x n row-major, overwritten; b overwritten by x) by Gaussian
+// elimination with partial pivoting.  Returns false for a zero pivot.
+bool solve_dense(int n, double* A, double* b) {
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i) if (std::fabs(A[i * n + k]) > std::fabs(A[p * n + k])) p = i;
+    if (A[p * n + k] == 0.0) return false;
+    if (p != k) {
+      for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[p * n + j]);
+      std::swap(b[k], b[p]);
+    }
+    for (int i = k + 1; i < n; ++i) {
+      double l = A[i * n + k] / A[k * n + k];
+      for (int j = k + 1; j < n; ++j) A[i * n + j] -= l * A[k * n + j];
+      b[i] -= l * b[k];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int j = i + 1; j < n; ++j) s -= A[i * n + j] * b[j];
+    b[i] = s / A[i * n + i];
+  }
+  return true;
+}
+
+// One Crank-Nicolson step of Eq. massfrac_ode for the adiabatic isochoric reactor
+// (Eqs. crank_nicol_rhs, crank_nicol_newton_system, crank_nicol_newton_update,
+// crank_nicol_jac).  Reading: Eq. massfrac_ode gives dY/dt = S/rho, so the
+// residual is F = Y - Y^m - dt/(2 rho) (S(Y) + S(Y^m)) and the Newton matrix is
+// I - dt/(2 rho) J with J = dS/dY at fixed (rho, e).  Newton starts from Y^m;
+// T follows each iterate through T(e, Y).  Stop rule as for the temperature
+// solve: once max_k |dY_k| <= tol, one more step.  Returns the Newton steps
+// taken, or -1 (no convergence within max_newton, or a singular matrix).
+int cn_step(const OMech& m, double rho, double dt, const double* Ym, double Tm, double tol, int max_newton,
+            double* Y_out, double* T_out) {
+  const int N = m.N();
+  const double e = internal_energy(m, Tm, Ym);
+  const double h = dt / (2.0 * rho);
+  std::vector<double> Sm(N), w(N), Y(Ym, Ym + N), A((size_t)N * N), b(N);
+  net_production_rates(m, rho, Tm, Ym, w.data());
+  for (int k = 0; k < N; ++k) Sm[k] = m.sp[k].W * w[k];
+  double T = Tm;
+  bool flag = false;
+  int it = 0;
+  for (; it < max_newton + 1; ) {
+    ++it;
+    double Tn;
+    if (temperature_newton(m, e, Y.data(), T, 1e-14, 100, &Tn) < 0) return -1;
+    T = Tn;
+    net_production_rates(m, rho, T, Y.data(), w.data());
+    source_jacobian_adiabatic(m, rho, T, Y.data(), A.data());
+    for (int j = 0; j < N; ++j) {
+      b[j] = -(Y[j] - Ym[j] - h * (m.sp[j].W * w[j] + Sm[j]));
+      for (int k = 0; k < N; ++k) A[j * N + k] = (j == k ? 1.0 : 0.0) - h * A[j * N + k];
+    }
+    if (!solve_dense(N, A.data(), b.data())) return -1;
+    double dmax = 0;
+    for (int k = 0; k < N; ++k) { Y[k] += b[k]; dmax = std::max(dmax, std::fabs(b[k])); }
+    if (flag) break;
+    if (dmax <= tol) flag = true;
+    else if (it >= max_newton) { it = -1; break; }
+  }
+  if (it > 0) {
+    double Tn;
+    if (temperature_newton(m, e, Y.data(), T, 1e-14, 100, &Tn) < 0) return -1;
+    T = Tn;
+  }
+  for (int k = 0; k < N; ++k) Y_out[k] = Y[k];
+  *T_out = T;
+  return it;
+}
 
 // ---------------------------------------------------------------------------
 // BF16 MLP for the Newton initial guess (model definition; FP64 arithmetic
@@ -553,6 +669,46 @@ void orc_temperature_bisect(void* h, int64_t n, const double* e, const double* Y
   }
 }
 
+void orc_enthalpy(void* h, int64_t n, const double* T, const double* Y, double* hm, double* cp) {
+  OMech* m = (OMech*)h; int N = m->N();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    hm[i] = enthalpy_mass(*m, T[i], y.data());
+    if (cp) cp[i] = cp_mass(*m, T[i], y.data());
+  }
+}
+
+// T(h, Y) by the enthalpy variant of the Newton inversion; returns the number of
+// points that did not converge.
+int64_t orc_temperature_enthalpy(void* h, int64_t n, const double* hm, const double* Y, const double* guess,
+                                 double T_guess, double tol, int max_iter, double* T, int32_t* iters) {
+  OMech* m = (OMech*)h; int N = m->N();
+  int64_t bad = 0;
+#pragma omp parallel for schedule(static) reduction(+:bad)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    double T0 = guess ? guess[i] : T_guess;
+    int it = temperature_newton(*m, hm[i], y.data(), T0, tol, max_iter, &T[i], true);
+    if (iters) iters[i] = it;
+    if (it < 0) ++bad;
+  }
+  return bad;
+}
+
+void orc_temperature_bisect_enthalpy(void* h, int64_t n, const double* hm, const double* Y, double lo,
+                                     double hi, double* T) {
+  OMech* m = (OMech*)h; int N = m->N();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    T[i] = temperature_bisect(*m, hm[i], y.data(), lo, hi, true);
+  }
+}
+
 // Per-reaction quantities at each point: kf, Kc, Rf, Rr (each [M][n]); any may be null.
 void orc_reaction_data(void* h, int64_t n, const double* rho, const double* T, const double* Y,
                        double* kf, double* Kc, double* Rf, double* Rr) {
@@ -665,6 +821,58 @@ void orc_vjp(void* h, int64_t n, const double* rho, const double* T, const doubl
       else Y_bar[(c - 2) * n + i] = acc;
     }
   }
+}
+
+// Chemical Jacobian dS/dY at fixed (rho, e), [N*N][n]: J[(j*N + k)*n + p] = dS_j/dY_k.
+void orc_jacobian_adiabatic(void* h, int64_t n, const double* rho, const double* T, const double* Y,
+                            double* J) {
+  OMech* m = (OMech*)h; int N = m->N();
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N), A((size_t)N * N);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    source_jacobian_adiabatic(*m, rho[i], T[i], y.data(), A.data());
+    for (int q = 0; q < N * N; ++q) J[(int64_t)q * n + i] = A[q];
+  }
+}
+
+// Source terms S = W omega at fixed (rho, e) as a function of Y alone (for finite
+// differences of the adiabatic Jacobian): T solved from e each call.  [N][n]
+void orc_source_at_energy(void* h, int64_t n, const double* rho, const double* e, const double* Y,
+                          double* S) {
+  OMech* m = (OMech*)h; int N = m->N();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N), w(N);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    double T;
+    temperature_newton(*m, e[i], y.data(), 1200.0, 1e-14, 100, &T);
+    net_production_rates(*m, rho[i], T, y.data(), w.data());
+    for (int k = 0; k < N; ++k) S[k * n + i] = m->sp[k].W * w[k];
+  }
+}
+
+// Dense solve (Gaussian elimination with partial pivoting), one system: A [n*n]
+// row-major, b [n]; x returned in b.  Returns 0, or -1 for a singular matrix.
+int orc_solve_dense(int n, double* A, double* b) { return solve_dense(n, A, b) ? 0 : -1; }
+
+// One Crank-Nicolson step per point; returns the number of points that failed.
+int64_t orc_cn_step(void* h, int64_t n, double dt, const double* rho, const double* Tm, const double* Ym,
+                    double tol, int max_newton, double* Y_out, double* T_out, int32_t* iters) {
+  OMech* m = (OMech*)h; int N = m->N();
+  int64_t bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+:bad)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N), yo(N);
+    for (int k = 0; k < N; ++k) y[k] = Ym[k * n + i];
+    double T;
+    int it = cn_step(*m, rho[i], dt, y.data(), Tm[i], tol, max_newton, yo.data(), &T);
+    for (int k = 0; k < N; ++k) Y_out[k * n + i] = yo[k];
+    T_out[i] = T;
+    if (iters) iters[i] = it;
+    if (it < 0) ++bad;
+  }
+  return bad;
 }
 
 // ---------------------------------------------------------------------------

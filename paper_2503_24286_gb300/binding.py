@@ -34,7 +34,7 @@ EXPORTS = [
     "pyro_nonconverged", "pyro_math_eval", "pyro_last_error", "pyro_version",
     "pyro_net_production_rates_noalloc", "pyro_mech_prepare", "pyro_jvp", "pyro_vjp", "pyro_jacobian",
     "pyro_mlp_n_params", "pyro_mlp_set_params", "pyro_mlp_get_params", "pyro_mlp_train", "pyro_mlp_grad",
-    "pyro_mlp_guess", "pyro_mlp_save", "pyro_mlp_load",
+    "pyro_mlp_guess", "pyro_mlp_save", "pyro_mlp_load", "pyro_enthalpy", "pyro_temperature_enthalpy",
 ]
 
 _lib = None
@@ -65,6 +65,8 @@ def lib() -> ctypes.CDLL:
         L.pyro_density.argtypes = [P, I64, D, D, D, D, P]
         L.pyro_internal_energy.argtypes = [P, I64, D, D, D, D, P]
         L.pyro_temperature.argtypes = [P, I64, D, D, D, ctypes.c_int, D, D, P]
+        L.pyro_enthalpy.argtypes = [P, I64, D, D, D, D, P]
+        L.pyro_temperature_enthalpy.argtypes = [P, I64, D, D, D, D, D, P]
         L.pyro_net_production_rates.argtypes = [P, I64, D, D, ctypes.c_int, D, D, D, P]
         L.pyro_net_production_rates_noalloc.argtypes = [P, I64, D, D, ctypes.c_int, D, D, D, P]
         L.pyro_mech_prepare.argtypes = [P, ctypes.c_char_p]
@@ -179,6 +181,20 @@ class Mechanism:
         args = [T, Y, e, cv]
         _check(lib().pyro_internal_energy(self._h, _n(T), *[_ptr(a)[0] for a in args], _stream(args)))
         return (e, cv) if with_cv else e
+
+    def enthalpy(self, T, Y, with_cp=False):
+        h = _empty_like(T, (_n(T),))
+        cp = _empty_like(T, (_n(T),)) if with_cp else None
+        args = [T, Y, h, cp]
+        _check(lib().pyro_enthalpy(self._h, _n(T), *[_ptr(a)[0] for a in args], _stream(args)))
+        return (h, cp) if with_cp else h
+
+    def temperature_enthalpy(self, h, Y, guess=None, with_iters=False, out=None):
+        T = _empty_like(h, (_n(h),)) if out is None else out
+        it = _empty_like(h, (_n(h),), "int32") if with_iters else None
+        args = [h, Y, guess, T, it]
+        _check(lib().pyro_temperature_enthalpy(self._h, _n(h), *[_ptr(a)[0] for a in args], _stream(args)))
+        return (T, it) if with_iters else T
 
     def temperature(self, e, Y, guess=None, learned=False, with_iters=False, out=None):
         T = _empty_like(e, (_n(e),)) if out is None else out

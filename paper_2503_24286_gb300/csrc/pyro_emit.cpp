@@ -172,18 +172,24 @@ void emit_tsolve(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, 
                  std::map<std::string, double>& st) {
   int N = m.n_species();
   // FP32 collapse (both ranges) and FP64 collapse (one range)
-  s << "// Newton inversion of e = sum_k Y_k e_k(T) (Sec. A.3.1, Eq. delta_temp); returns T,\n"
-       "// writes the iteration count (FP32 + FP64 steps) or -1 if max_iter FP64 steps\n"
-       "// did not meet |dT| <= tol T.\n";
-  s << "__device__ __forceinline__ double pyro_tsolve(const double* __restrict__ Yp, i64 n, double e,\n"
+  s << "// Newton inversion of e = sum_k Y_k e_k(T) (Sec. A.3.1, Eq. delta_temp), or with\n"
+       "// ENTH of h = sum_k Y_k h_k(T) (the enthalpy variant: the linear coefficient of each\n"
+       "// species polynomial gains 1/W_k, c_v becomes c_p); returns T, writes the iteration\n"
+       "// count (FP32 + FP64 steps) or -1 if max_iter FP64 steps did not meet |dT| <= tol T.\n";
+  s << "template <bool ENTH>\n__device__ __forceinline__ double pyro_tsolve(const double* __restrict__ Yp, i64 n, double e,\n"
        "    double T0, int max_iter, float tolf, int* iters) {\n";
   s << "  const double eR = e * " << lit((double)(1.0L / R_GAS)) << ";\n";
   Src dummy;
   s << "  float bl0=0.f,bl1=0.f,bl2=0.f,bl3=0.f,bl4=0.f,bl5=0.f,bh0=0.f,bh1=0.f,bh2=0.f,bh3=0.f,bh4=0.f,bh5=0.f;\n";
   for (int k = 0; k < N; ++k) {
+    const double invW = 1.0 / m.species[k].W;
+    auto cf = [&](int r, int q) {
+      if (q != 1) return litf(C[k].d[r][q]);
+      return "(ENTH ? " + litf(C[k].d[r][1] + invW) + " : " + litf(C[k].d[r][1]) + ")";
+    };
     s << "  { float y = pdm::to_float_trunc(__ldg(Yp + (i64)" << k << " * n));";
-    for (int q = 0; q < 6; ++q) s << " bl" << q << " = fmaf(y, " << litf(C[k].d[0][q]) << ", bl" << q << ");";
-    for (int q = 0; q < 6; ++q) s << " bh" << q << " = fmaf(y, " << litf(C[k].d[1][q]) << ", bh" << q << ");";
+    for (int q = 0; q < 6; ++q) s << " bl" << q << " = fmaf(y, " << cf(0, q) << ", bl" << q << ");";
+    for (int q = 0; q < 6; ++q) s << " bh" << q << " = fmaf(y, " << cf(1, q) << ", bh" << q << ");";
     s << " }\n";
   }
   s << R"(  float Tf = pdm::to_float_trunc(T0);
@@ -211,10 +217,16 @@ void emit_tsolve(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, 
   // collapse macro for a given range flag 'hi'
   s << "  auto collapse = [&](bool hi) {\n    B0 = 0.0; B1 = 0.0; B2 = 0.0; B3 = 0.0; B4 = 0.0; B5 = 0.0;\n";
   for (int k = 0; k < N; ++k) {
+    const double invW = 1.0 / m.species[k].W;
     s << "    { double y = __ldg(Yp + (i64)" << k << " * n);";
     for (int q = 0; q < 6; ++q) {
       double v[2] = {C[k].d[0][q], C[k].d[1][q]};
-      s << " B" << q << " = fma(y, " << sel(v) << ", B" << q << ");";
+      if (q == 1) {
+        double vh[2] = {C[k].d[0][1] + invW, C[k].d[1][1] + invW};
+        s << " B1 = fma(y, (ENTH ? " << sel(vh) << " : " << sel(v) << "), B1);";
+      } else {
+        s << " B" << q << " = fma(y, " << sel(v) << ", B" << q << ");";
+      }
     }
     s << " }\n";
   }
@@ -1049,10 +1061,10 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_mlp(i64 n, co
     if (!valid) continue;
     double T0 = (double)fminf(fmaxf(fmaf(S.T_std, y, S.T_mean), 200.0f), 3500.0f);
     int it;
-    double T = pyro_tsolve(g_Y + p, n, e, T0, max_iter, tolf, &it);
+    double T = pyro_tsolve<false>(g_Y + p, n, e, T0, max_iter, tolf, &it);
     if (it < 0) {
       int it2;
-      T = pyro_tsolve(g_Y + p, n, e, 1200.0, max_iter, tolf, &it2);
+      T = pyro_tsolve<false>(g_Y + p, n, e, 1200.0, max_iter, tolf, &it2);
       it = it2 < 0 ? -1 : it2 + max_iter + 1;
     }
     g_T[p] = T;
@@ -1119,6 +1131,26 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_math(int fn, i64 n, const
        "    if (g_cv) g_cv[p] = " << lit((double)R_GAS)
     << " * fma(T, fma(T, fma(T, fma(T, 5.0 * B5, 4.0 * B4), 3.0 * B3), 2.0 * B2), B1);\n  }\n}\n";
 
+  // ---- enthalpy and c_p (h_k = e_k + R T / W_k) --------------------------------
+  s << "\nextern \"C\" __global__ void __launch_bounds__(BLK) pyro_enthalpy(i64 n, const double* __restrict__ g_T,\n"
+       "    const double* __restrict__ g_Y, double* __restrict__ g_h, double* __restrict__ g_cp) {\n"
+       "  for (i64 p = (i64)blockIdx.x * BLK + threadIdx.x; p < n; p += (i64)gridDim.x * BLK) {\n"
+       "    const double* Yp = g_Y + p;\n    const double T = g_T[p];\n"
+       "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n"
+       "    double B0 = 0.0, B1 = 0.0, B2 = 0.0, B3 = 0.0, B4 = 0.0, B5 = 0.0;\n";
+  for (int k = 0; k < N; ++k) {
+    s << "    { double y = __ldg(Yp + (i64)" << k << " * n);";
+    for (int q = 0; q < 6; ++q) {
+      double v[2] = {C[k].d[0][q], C[k].d[1][q]};
+      if (q == 1) { v[0] += 1.0 / m.species[k].W; v[1] += 1.0 / m.species[k].W; }
+      s << " B" << q << " = fma(y, " << sel(v) << ", B" << q << ");";
+    }
+    s << " }\n";
+  }
+  s << "    g_h[p] = " << lit((double)R_GAS) << " * fma(T, fma(T, fma(T, fma(T, fma(T, B5, B4), B3), B2), B1), B0);\n"
+       "    if (g_cp) g_cp[p] = " << lit((double)R_GAS)
+    << " * fma(T, fma(T, fma(T, fma(T, 5.0 * B5, 4.0 * B4), 3.0 * B3), 2.0 * B2), B1);\n  }\n}\n";
+
   // ---- temperature --------------------------------------------------------------
   s << R"(
 extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature(i64 n, const double* __restrict__ g_e,
@@ -1127,7 +1159,21 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature(i64 n, const 
   const float tolf = (float)tol;
   for (i64 p = (i64)blockIdx.x * BLK + threadIdx.x; p < n; p += (i64)gridDim.x * BLK) {
     int it;
-    double T = pyro_tsolve(g_Y + p, n, g_e[p], g_guess ? g_guess[p] : T_guess, max_iter, tolf, &it);
+    double T = pyro_tsolve<false>(g_Y + p, n, g_e[p], g_guess ? g_guess[p] : T_guess, max_iter, tolf, &it);
+    g_T[p] = T;
+    if (g_iters) g_iters[p] = it;
+    if (it < 0) atomicAdd(g_fail, 1ull);
+  }
+}
+
+// Temperature from the mixture enthalpy (the enthalpy variant of the inversion)
+extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, const double* __restrict__ g_h,
+    const double* __restrict__ g_Y, const double* __restrict__ g_guess, double T_guess, int max_iter, double tol,
+    double* __restrict__ g_T, int* __restrict__ g_iters, unsigned long long* __restrict__ g_fail) {
+  const float tolf = (float)tol;
+  for (i64 p = (i64)blockIdx.x * BLK + threadIdx.x; p < n; p += (i64)gridDim.x * BLK) {
+    int it;
+    double T = pyro_tsolve<true>(g_Y + p, n, g_h[p], g_guess ? g_guess[p] : T_guess, max_iter, tolf, &it);
     g_T[p] = T;
     if (g_iters) g_iters[p] = it;
     if (it < 0) atomicAdd(g_fail, 1ull);
@@ -1155,7 +1201,7 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature(i64 n, const 
        "    const double* Yp = g_Y + p;\n    const double rho = g_rho[p];\n"
        "    double T;\n"
        "    if (energy_mode) {\n      int it;\n"
-       "      T = pyro_tsolve(Yp, n, g_Tin[p], T_guess, max_iter, tolf, &it);\n"
+       "      T = pyro_tsolve<false>(Yp, n, g_Tin[p], T_guess, max_iter, tolf, &it);\n"
        "      if (it < 0) atomicAdd(g_fail, 1ull);\n      if (g_Tout) g_Tout[p] = T;\n"
        "    } else {\n      T = g_Tin[p];\n    }\n"
        "    const double lnT = pdm::log(T, s_log);\n    const double invT = pdm::rcp(T);\n"

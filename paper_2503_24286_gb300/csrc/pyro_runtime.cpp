@@ -223,7 +223,7 @@ struct pyro_mech {
   int num_sms = 0;
   CUmodule module = nullptr;
   CUfunction f_omega = nullptr, f_temperature = nullptr, f_energy = nullptr, f_density = nullptr,
-             f_math = nullptr;
+             f_math = nullptr, f_enthalpy = nullptr, f_temperature_h = nullptr;
   int omega_blocks_per_sm = 1;
   unsigned long long* d_fail = nullptr;
   // derivative kernels: compiled and loaded on first use (or by pyro_mech_prepare)
@@ -580,7 +580,8 @@ int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) 
   if (r != CUDA_SUCCESS) { delete h; return fail(PYRO_ECUDA, "cuModuleLoadData: " + cu_err(r)); }
   struct { const char* name; CUfunction* f; } fns[] = {
       {"pyro_omega", &h->f_omega}, {"pyro_temperature", &h->f_temperature}, {"pyro_energy", &h->f_energy},
-      {"pyro_density", &h->f_density}, {"pyro_math", &h->f_math}};
+      {"pyro_density", &h->f_density}, {"pyro_math", &h->f_math}, {"pyro_enthalpy", &h->f_enthalpy},
+      {"pyro_temperature_h", &h->f_temperature_h}};
   for (auto& q : fns) {
     r = d.ModuleGetFunction(q.f, h->module, q.name);
     if (r != CUDA_SUCCESS) { pyro_mech_free(h); return fail(PYRO_ECUDA, std::string("missing kernel ") + q.name); }
@@ -685,6 +686,42 @@ int pyro_internal_energy(const pyro_mech* hc, int64_t n, const double* T, const 
                      void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3]};
                      return launch(h, h->f_energy, nc, 8, 0, st, params);
                    });
+}
+
+int pyro_enthalpy(const pyro_mech* hc, int64_t n, const double* T, const double* Y, double* hm, double* cp,
+                  void* stream) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n < 0 || (n > 0 && (!T || !Y || !hm))) return fail(PYRO_EINVAL, "pyro_enthalpy: bad arguments");
+  if (n == 0) return PYRO_OK;
+  if (int rc = check_device(h)) return rc;
+  const int64_t NS = h->m.n_species();
+  return with_args(h, n, {{T, 1, 8, true, false}, {Y, NS, 8, true, false}, {hm, 1, 8, false, true}, {cp, 1, 8, false, true}},
+                   stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
+                     long long nn = nc;
+                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3]};
+                     return launch(h, h->f_enthalpy, nc, 8, 0, st, params);
+                   });
+}
+
+int pyro_temperature_enthalpy(const pyro_mech* hc, int64_t n, const double* hm, const double* Y,
+                              const double* T_guess, double* T_out, int32_t* iters, void* stream) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n < 0 || (n > 0 && (!hm || !Y || !T_out)))
+    return fail(PYRO_EINVAL, "pyro_temperature_enthalpy: bad arguments");
+  if (n == 0) return PYRO_OK;
+  if (int rc = check_device(h)) return rc;
+  const int64_t NS = h->m.n_species();
+  int rc = with_args(h, n, {{hm, 1, 8, true, false}, {Y, NS, 8, true, false}, {T_guess, 1, 8, true, false},
+                            {T_out, 1, 8, false, true}, {iters, 1, 4, false, true}},
+                     stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
+                       long long nn = nc;
+                       double Tg = 1200.0, tol = 1e-10;
+                       int max_iter = 50;
+                       void* params[] = {&nn, &d[0], &d[1], &d[2], &Tg, &max_iter, &tol, &d[3], &d[4], &h->d_fail};
+                       return launch(h, h->f_temperature_h, nc, 8, 0, st, params);
+                     });
+  if (rc) return rc;
+  return maybe_checked(h, stream);
 }
 
 int pyro_temperature(const pyro_mech* hc, int64_t n, const double* e, const double* Y, const double* T_guess,
