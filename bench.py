@@ -320,6 +320,54 @@ def large_mechanism_rates(synth, dev, stream, args, rank):
     return res
 
 
+def crank_nicolson_rates(synth, dev, stream, args, rank):
+    """One Crank-Nicolson step (Sec. A.3.2) of 2^18 states of the 53-species
+    mechanism at T ~ U[2000, 2800] K with dt = 3e-41 s (the synthetic kinetics'
+    stiff time scale), and the chemical Jacobian dS/dY at fixed (rho, e) on the
+    same states."""
+    import torch
+    from paper_2503_24286_gb300 import binding as B
+    d = tempfile.mkdtemp()
+    path = os.path.join(d, "mech.txt")
+    cfg = synth.CONFIGS[5]
+    synth.write_mechanism(synth.config_mechanism(5), path)
+    m = B.Mechanism(path)
+    m.prepare("jacobian_adiabatic,cn")
+    n = args.cn_points
+    T, p, Y = synth.generate_states_torch(53, n, cfg["T"], cfg["p_atm"], synth.STATE_SEED_BASE + 5 + 7919 * rank, dev)
+    rho = m.density(p, T, Y)
+    del p
+    dt = cfg["dt"]
+    res = {"workload": "53 species / 325 reactions, %d states, T ~ U[2000, 2800] K, p ~ U[0.5, 20] atm, "
+                       "Dirichlet Y; one Crank-Nicolson step, dt = %g s, Newton tol 1e-12 on max|dY|; "
+                       "Newton matrix by FP32 LU + 2 FP64 refinement steps" % (n, dt)}
+    To = torch.empty_like(T)
+    Yo = torch.empty_like(Y)
+    _, _, it = m.cn_step(dt, rho, T, Y, T_out=To, Y_out=Yo, with_iters=True)
+    torch.cuda.synchronize(dev)
+    assert m.nonconverged() == 0 and (it > 0).all().item()
+    res["newton_iters_mean"] = float(it.double().mean().item())
+    res["newton_iters_max"] = int(it.max().item())
+    steps = max(2, min(args.steps, 3))
+    J = torch.empty((53 * 53, n), dtype=torch.float64, device=dev)
+    calls = {"cn_step": lambda: m.cn_step(dt, rho, T, Y, T_out=To, Y_out=Yo),
+             "jacobian_adiabatic": lambda: m.jacobian_adiabatic(rho, T, Y, out=J)}
+    for name, f in calls.items():
+        f()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            f()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, dev)
+        res[name + "_ms"] = ms
+        res[name + "_per_s"] = n / (ms * 1e-3)
+    del J
+    return res
+
+
 def run_ours(args):
     import torch
     from paper_2503_24286_gb300 import binding as B
@@ -418,6 +466,10 @@ def run_ours(args):
         warp53 = {"ms": ms_w, "states_per_s": n / (ms_w * 1e-3)}
         large = large_mechanism_rates(synth, dev, stream, args, rank)
 
+    cn = None
+    if not args.no_cn:
+        cn = crank_nicolson_rates(synth, dev, stream, args, rank)
+
     # --- roofline of the timed kernel ---------------------------------------------------
     flops_fwd = mech.stat("omega_fp64_flops_per_point")
     flops_ts = 2 * mech.stat("tsolve_collapse_fp64_ops") + 3 * 2 * mech.stat("tsolve_iter_fp64_ops_mixed")
@@ -453,6 +505,7 @@ def run_ours(args):
                 "learned_guess": learned,
                 "warp_per_state_53sp": warp53,
                 "large_mechanism": large,
+                "crank_nicolson": cn,
                 "kernel_source_hash": src_hash,
                 "kernel": "pyro_omega (fused Newton T(e,Y) + omega), %d threads/block, %d blocks/SM"
                           % (int(mech.stat("block")), int(mech.stat("omega_blocks_per_sm")))}
@@ -475,6 +528,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--large-points", type=int, default=2 ** 21)
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--cn-points", type=int, default=2 ** 18)
+    ap.add_argument("--no-cn", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -141,7 +141,8 @@ int pyro_net_production_rates(const pyro_mech* mech, int64_t n, const double* rh
                               double* T_out, double* omega_out, void* stream);
 
 /* Compile and load derivative kernels ahead of their first use.  kernels:
- * NULL or "all", or a comma list of "jvp", "vjp", "jacobian".  The groups are
+ * NULL or "all" (jvp, vjp, jacobian), or a comma list of "jvp", "vjp",
+ * "jacobian", "jacobian_adiabatic", "cn".  The groups are
  * compiled in parallel host threads with NVRTC (cached on disk); without this
  * call each group is compiled on the first call that needs it. */
 int pyro_mech_prepare(const pyro_mech* mech, const char* kernels);
@@ -172,6 +173,38 @@ int pyro_vjp(const pyro_mech* mech, int64_t n, const double* rho, const double* 
  * use, grown as needed). */
 int pyro_jacobian(const pyro_mech* mech, int64_t n, const double* rho, const double* T, const double* Y,
                   double* J, void* stream);
+
+/* Chemical Jacobian of the source term at fixed density and internal energy
+ * (Sec. A.3.2 Eq. chem_jacobian, with S_j = W_j omega_j of Eq. massfrac_ode):
+ *   J_jk = dS_j/dY_k |_(rho, e) = W_j (d omega_j/dY_k + d omega_j/dT dT/dY_k),
+ *   dT/dY_k = -e_k(T)/c_v  (Eq. int_energy, Eq. cv: T follows Y at fixed e).
+ * T must be the temperature of (e, Y) (e.g. from pyro_temperature).
+ * rho, T: [n]; Y: [N][n]; J: [N*N][n] out, entry (j, k) at J[(j*N + k)*n + p].
+ * Columns sum to zero (mass conservation).  Shares the per-handle scratch of
+ * pyro_jacobian.  Same mechanism restriction as pyro_jacobian. */
+int pyro_jacobian_adiabatic(const pyro_mech* mech, int64_t n, const double* rho, const double* T,
+                            const double* Y, double* J, void* stream);
+
+/* One Crank-Nicolson step of the adiabatic isochoric reactor (Sec. A.3.2,
+ * Eqs. crank_nicol_rhs, crank_nicol_newton_system, crank_nicol_newton_update,
+ * crank_nicol_jac), reading Eq. massfrac_ode as dY/dt = S/rho at fixed (rho, e):
+ *   F(Y) = Y - Y^m - dt/(2 rho) (S(Y) + S(Y^m)) = 0,
+ * solved per state by Newton from Y^m with the matrix I - dt/(2 rho) J, J from
+ * pyro_jacobian_adiabatic at each iterate and T re-solved from (e, Y) at each
+ * iterate (e = e(T^m, Y^m)).  Stop once max_k |dY_k| <= tol, after one further
+ * Newton step; at most max_newton steps.  The linear systems are solved by LU
+ * with partial pivoting in FP32 on row-scaled matrices plus two steps of
+ * iterative refinement with FP64 residuals.
+ * rho, T: [n] state at t^m; Y: [N][n]; T_out: [n] and Y_out: [N][n] at
+ * t^m + dt (may alias T and Y); iters_out: nullable int32 [n], Newton steps
+ * taken or -1 where the step failed (no convergence, singular matrix or a
+ * failed temperature solve; counted by pyro_nonconverged).
+ * Work arrays (about 8 (N^2 + 2N + 2) bytes per state, in chunks of at most
+ * 2 GiB) are allocated on first use and kept by the handle.  Returns
+ * PYRO_EINVAL for dt < 0, tol <= 0 or max_newton outside [1, 1000]. */
+int pyro_cn_step(const pyro_mech* mech, int64_t n, double dt, const double* rho, const double* T,
+                 const double* Y, double tol, int max_newton, double* T_out, double* Y_out,
+                 int32_t* iters_out, void* stream);
 
 /* ---- Learned initial guess for the Newton temperature solve ----------------
  * Not in the paper (its Newton starts from a fixed guess, Sec. 4.3 listing of

@@ -35,6 +35,7 @@ EXPORTS = [
     "pyro_net_production_rates_noalloc", "pyro_mech_prepare", "pyro_jvp", "pyro_vjp", "pyro_jacobian",
     "pyro_mlp_n_params", "pyro_mlp_set_params", "pyro_mlp_get_params", "pyro_mlp_train", "pyro_mlp_grad",
     "pyro_mlp_guess", "pyro_mlp_save", "pyro_mlp_load", "pyro_enthalpy", "pyro_temperature_enthalpy",
+    "pyro_jacobian_adiabatic", "pyro_cn_step",
 ]
 
 _lib = None
@@ -66,6 +67,8 @@ def lib() -> ctypes.CDLL:
         L.pyro_internal_energy.argtypes = [P, I64, D, D, D, D, P]
         L.pyro_temperature.argtypes = [P, I64, D, D, D, ctypes.c_int, D, D, P]
         L.pyro_enthalpy.argtypes = [P, I64, D, D, D, D, P]
+        L.pyro_jacobian_adiabatic.argtypes = [P, I64, D, D, D, D, P]
+        L.pyro_cn_step.argtypes = [P, I64, ctypes.c_double, D, D, D, ctypes.c_double, ctypes.c_int, D, D, D, P]
         L.pyro_temperature_enthalpy.argtypes = [P, I64, D, D, D, D, D, P]
         L.pyro_net_production_rates.argtypes = [P, I64, D, D, ctypes.c_int, D, D, D, P]
         L.pyro_net_production_rates_noalloc.argtypes = [P, I64, D, D, ctypes.c_int, D, D, D, P]
@@ -261,6 +264,27 @@ class Mechanism:
         args = [rho, T, Y, J]
         _check(lib().pyro_jacobian(self._h, _n(rho), *[_ptr(a)[0] for a in args], _stream(args)))
         return J
+
+    def jacobian_adiabatic(self, rho, T, Y, out=None):
+        """J [N*N, n]: dS_j/dY_k (row j, column k) of S = W omega at fixed (rho, e)."""
+        N = self.n_species
+        J = _empty_like(rho, (N * N, _n(rho))) if out is None else out
+        args = [rho, T, Y, J]
+        _check(lib().pyro_jacobian_adiabatic(self._h, _n(rho), *[_ptr(a)[0] for a in args], _stream(args)))
+        return J
+
+    def cn_step(self, dt, rho, T, Y, tol=1e-12, max_newton=20, T_out=None, Y_out=None, with_iters=False):
+        """One Crank-Nicolson step of dY/dt = S/rho at fixed (rho, e): (T_next [n], Y_next [N, n]
+        [, Newton steps [n], -1 where the step failed])."""
+        n = _n(T)
+        To = _empty_like(T, (n,)) if T_out is None else T_out
+        Yo = _empty_like(T, (self.n_species, n)) if Y_out is None else Y_out
+        it = _empty_like(T, (n,), "int32") if with_iters else None
+        arrays = [rho, T, Y, To, Yo, it]
+        ptr = [_ptr(a)[0] for a in arrays]
+        _check(lib().pyro_cn_step(self._h, n, float(dt), ptr[0], ptr[1], ptr[2], float(tol), int(max_newton),
+                                  ptr[3], ptr[4], ptr[5], _stream(arrays)))
+        return (To, Yo, it) if with_iters else (To, Yo)
 
     # --- learned initial guess ---------------------------------------------------
     def mlp_n_params(self) -> int:

@@ -751,7 +751,17 @@ struct JacSlots {
   std::vector<std::map<int, int>> Q;          // per reaction: species -> slot
 };
 
-void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, int blk, int* nslots) {
+// Which outputs the Jacobian kernel assembles from the per-reaction partials:
+//  TY    d(Tdot, omega)/d(T, Y) at fixed rho, [(N+1)^2][n]
+//  ADIA  dS_j/dY_k at fixed (rho, e), S = W omega (Eq. chem_jacobian), [N^2][n]
+//  CN    the Crank-Nicolson Newton system (Eqs. crank_nicol_newton_update,
+//        crank_nicol_jac) at the current iterate: matrix I - (dt/2rho) dS/dY|_(rho,e)
+//        in groups of CN_G states ([n/CN_G][N^2][CN_G], the layout the batched solve
+//        reads) and right-hand side -F = c + (dt/2rho) S - Y, c = Y^m + (dt/2rho) S^m.
+enum class JacMode { TY, ADIA, CN };
+
+void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, int blk, int* nslots,
+                          JacMode mode = JacMode::TY) {
   int N = m.n_species(), M = m.n_reactions(), NP = N + 1;
   JacSlots sl;
   sl.R.resize(M); sl.Rt.resize(M); sl.RM.assign(M, -1); sl.Q.resize(M);
@@ -767,20 +777,53 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
   }
   *nslots = sl.n;
   auto slot = [&](int q) { return "W[" + std::to_string(q) + " * BLKD]"; };
-  s << "\n// Dense Jacobian d(Tdot, omega)/d(T, Y) at fixed rho, [(N+1)^2][n]; row 0 = Tdot of the adiabatic\n"
-       "// isochoric reactor, rows 1..N = omega; column 0 = T, columns 1..N = Y.  Phase 1 writes the\n"
-       "// per-reaction partials to the block's scratch, phase 2 assembles the rows.\n";
-  s << "extern \"C\" __global__ void __launch_bounds__(" << blk << ") pyro_jacobian(i64 n, const double* __restrict__ g_rho,\n"
-       "    const double* __restrict__ g_T, const double* __restrict__ g_Y, double* __restrict__ g_J,\n"
-       "    double* __restrict__ g_scratch) {\n"
-       "  __shared__ double s_exp[512];\n  __shared__ double s_log[256];\n  extern __shared__ double s_dyn[];\n"
-       "  double* sL = s_dyn; double* sA = sL + NSP * BLKD; double* sE = sA + NSP * BLKD; double* sLp = sE + NSP * BLKD;\n"
-       "  pyro_load_tables(s_exp, s_log);\n  __syncthreads();\n  const int t = threadIdx.x;\n"
-       "  double* W = g_scratch + (i64)blockIdx.x * " << sl.n << " * BLKD + t;\n"
-       "  for (i64 p = (i64)blockIdx.x * BLKD + t; p < n; p += (i64)gridDim.x * BLKD) {\n"
-       "    const double* Yp = g_Y + p;\n    double* Jp = g_J + p;\n"
-       "    const double rho = g_rho[p], T = g_T[p];\n"
-       "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
+  const char* prologue =
+      "  __shared__ double s_exp[512];\n  __shared__ double s_log[256];\n  extern __shared__ double s_dyn[];\n"
+      "  double* sL = s_dyn; double* sA = sL + NSP * BLKD; double* sE = sA + NSP * BLKD; double* sLp = sE + NSP * BLKD;\n"
+      "  pyro_load_tables(s_exp, s_log);\n  __syncthreads();\n  const int t = threadIdx.x;\n";
+  if (mode == JacMode::TY) {
+    s << "\n// Dense Jacobian d(Tdot, omega)/d(T, Y) at fixed rho, [(N+1)^2][n]; row 0 = Tdot of the adiabatic\n"
+         "// isochoric reactor, rows 1..N = omega; column 0 = T, columns 1..N = Y.  Phase 1 writes the\n"
+         "// per-reaction partials to the block's scratch, phase 2 assembles the rows.\n";
+    s << "extern \"C\" __global__ void __launch_bounds__(" << blk << ") pyro_jacobian(i64 n, const double* __restrict__ g_rho,\n"
+         "    const double* __restrict__ g_T, const double* __restrict__ g_Y, double* __restrict__ g_J,\n"
+         "    double* __restrict__ g_scratch) {\n" << prologue <<
+         "  double* W = g_scratch + (i64)blockIdx.x * " << sl.n << " * BLKD + t;\n"
+         "  for (i64 p = (i64)blockIdx.x * BLKD + t; p < n; p += (i64)gridDim.x * BLKD) {\n"
+         "    const double* Yp = g_Y + p;\n    double* Jp = g_J + p;\n"
+         "    const double rho = g_rho[p], T = g_T[p];\n";
+  } else if (mode == JacMode::ADIA) {
+    s << "\n// Chemical Jacobian dS_j/dY_k of S = W omega at fixed (rho, e) (Eq. chem_jacobian), [N^2][n],\n"
+         "// row j, column k: W_j (d omega_j/dY_k + d omega_j/dT dT/dY_k), dT/dY_k = -e_k/c_v.\n";
+    s << "extern \"C\" __global__ void __launch_bounds__(" << blk << ") pyro_jacobian_adiabatic(i64 n,\n"
+         "    const double* __restrict__ g_rho, const double* __restrict__ g_T, const double* __restrict__ g_Y,\n"
+         "    double* __restrict__ g_J, double* __restrict__ g_scratch) {\n" << prologue <<
+         "  double* W = g_scratch + (i64)blockIdx.x * " << sl.n << " * BLKD + t;\n"
+         "  for (i64 p = (i64)blockIdx.x * BLKD + t; p < n; p += (i64)gridDim.x * BLKD) {\n"
+         "    const double* Yp = g_Y + p;\n    double* Jp = g_J + p;\n"
+         "    const double rho = g_rho[p], T = g_T[p];\n";
+  } else {
+    s << "\n// Crank-Nicolson Newton system at the current iterate Y (state arrays [N][n], n = stride;\n"
+         "// cnt states).  state: 0 first iteration (forms c from S^m = S(Y^m)), 1 iterating,\n"
+         "// 2 converged (one more step pending), 3 done, 4 failed; states >= 3 are skipped.\n";
+    s << "extern \"C\" __global__ void __launch_bounds__(" << blk << ") pyro_cn_assemble(i64 cnt, i64 n,\n"
+         "    const double* __restrict__ g_rho, const double* __restrict__ g_e, const double* __restrict__ g_Y,\n"
+         "    double* __restrict__ g_c, double* __restrict__ g_T, int* __restrict__ g_state, double dt,\n"
+         "    int max_iter, double tol, double* __restrict__ g_A, double* __restrict__ g_b,\n"
+         "    double* __restrict__ g_scratch, unsigned long long* __restrict__ g_fail) {\n" << prologue <<
+         "  double* W = g_scratch + (i64)blockIdx.x * " << sl.n << " * BLKD + t;\n"
+         "  const float tolf = (float)tol;\n"
+         "  for (i64 p = (i64)blockIdx.x * BLKD + t; p < cnt; p += (i64)gridDim.x * BLKD) {\n"
+         "    const int stp = g_state[p];\n    if (stp >= 3) continue;\n"
+         "    const double* Yp = g_Y + p;\n"
+         "    double* Jp = g_A + (p / CN_G) * (i64)(NSP * NSP * CN_G) + (p % CN_G);\n"
+         "    const double rho = g_rho[p];\n"
+         "    int tit;\n"
+         "    const double T = pyro_tsolve<false>(Yp, n, g_e[p], g_T[p], max_iter, tolf, &tit);\n"
+         "    if (tit < 0) { g_state[p] = 4; atomicAdd(g_fail, 1ull); continue; }\n"
+         "    g_T[p] = T;\n";
+  }
+  s << "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
        "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
   emit_species_deriv(s, m, C, DMode::JAC);
   // ---- phase 1
@@ -815,6 +858,92 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
       s << "      " << slot(sl.Q[j][i]) << " = kk * sE" << sidx(i) << " * (" << diff << ");\n";
     }
     s << "    }\n";
+  }
+  if (mode != JacMode::TY) {
+    // ---- phase 2 at fixed (rho, e): sL becomes s_i = rho/W_i, sA becomes
+    // dT/dY_i|_e = -e_i/c_v (Eq. int_energy: e = sum_i Y_i e_i(T), c_v = de/dT).
+    s << "    asm volatile(\"\" ::: \"memory\");\n";
+    s << "    const double RT = " << lit((double)R_GAS) << " * T;\n    double cv = 0.0;\n";
+    for (int i = 0; i < N; ++i) {
+      const SpeciesCoef& c = C[i];
+      double h4[2] = {c.h[0][4], c.h[1][4]}, h3[2] = {c.h[0][3], c.h[1][3]}, h2[2] = {c.h[0][2], c.h[1][2]};
+      double h1[2] = {c.h[0][1], c.h[1][1]}, h0[2] = {c.h[0][0], c.h[1][0]}, h5[2] = {c.h[0][5], c.h[1][5]};
+      double p4[2] = {c.cp[0][4], c.cp[1][4]}, p3[2] = {c.cp[0][3], c.cp[1][3]}, p2[2] = {c.cp[0][2], c.cp[1][2]};
+      double p1[2] = {c.cp[0][1], c.cp[1][1]}, p0[2] = {c.cp[0][0], c.cp[1][0]};
+      s << "    { const double y = __ldg(Yp + (i64)" << i << " * n);\n";
+      s << "      double hr = fma(T, " << sel(h4) << ", " << sel(h3) << "); hr = fma(T, hr, " << sel(h2)
+        << "); hr = fma(T, hr, " << sel(h1) << "); hr = fma(T, hr, " << sel(h0) << "); hr = fma(" << sel(h5)
+        << ", invT, hr);\n";
+      s << "      double cp = fma(T, " << sel(p4) << ", " << sel(p3) << "); cp = fma(T, cp, " << sel(p2)
+        << "); cp = fma(T, cp, " << sel(p1) << "); cp = fma(T, cp, " << sel(p0) << ");\n";
+      s << "      sA" << sidx(i) << " = fma(RT, hr, -RT) * " << lit(1.0 / m.species[i].W) << ";\n";
+      s << "      cv = fma(y * " << lit((double)R_GAS / m.species[i].W) << ", cp - 1.0, cv);\n";
+      s << "      sL" << sidx(i) << " = rho * " << lit(1.0 / m.species[i].W) << "; }\n";
+    }
+    s << "    const double mrcv = -pdm::rcp(cv);\n";
+    s << "    #pragma unroll 1\n    for (int i = 0; i < NSP; ++i) sA[i * BLKD + t] *= mrcv;\n";
+    if (mode == JacMode::CN) {
+      s << "    const double hh = 0.5 * dt * pdm::rcp(rho);\n";
+      s << "    const i64 nr = CN_G;\n";
+    } else {
+      s << "    const i64 nr = opq(n);\n";
+    }
+    std::vector<std::vector<std::pair<int, int>>> rows(N);
+    for (int j = 0; j < M; ++j)
+      for (auto& q : net_nu(m.reactions[j])) if (q.second) rows[q.first].push_back({j, q.second});
+    for (int k = 0; k < N; ++k) {
+      s << "    { // row of species " << k << "\n      double w = 0.0, jt = 0.0, u = 0.0;\n";
+      std::map<int, std::string> acc, cr;
+      for (auto& jn : rows[k]) {
+        int j = jn.first;
+        std::string nu = lit((double)jn.second);
+        s << "      w = fma(" << nu << ", " << slot(sl.R[j]) << ", w); jt = fma(" << nu << ", " << slot(sl.Rt[j]) << ", jt);";
+        if (sl.RM[j] >= 0) s << " u = fma(" << nu << ", " << slot(sl.RM[j]) << ", u);";
+        s << "\n";
+        for (auto& qi : sl.Q[j]) {
+          std::string name = "q" + std::to_string(qi.first);
+          if (!acc.count(qi.first)) { acc[qi.first] = name; s << "      double " << name << " = 0.0;\n"; }
+          s << "      " << name << " = fma(" << nu << ", " << slot(qi.second) << ", " << name << ");\n";
+        }
+        if (sl.RM[j] >= 0) {
+          for (auto& e : m.reactions[j].efficiencies) {
+            if (e.second == 1.0) continue;
+            std::string name = "c" + std::to_string(e.first);
+            if (!cr.count(e.first)) { cr[e.first] = name; s << "      double " << name << " = 0.0;\n"; }
+            s << "      " << name << " = fma(" << nu << " * " << lit(e.second - 1.0) << ", " << slot(sl.RM[j]) << ", " << name << ");\n";
+          }
+        }
+      }
+      // row factor: W_k (Jacobian of S = W omega), or -dt/(2 rho) W_k (Newton matrix)
+      if (mode == JacMode::CN) s << "      const double F = -hh * " << lit(m.species[k].W) << ";\n";
+      else s << "      const double F = " << lit(m.species[k].W) << ";\n";
+      s << "      const double fu = F * u, fj = F * jt;\n";
+      s << "      double* Jr = Jp + (i64)" << k * N << " * nr;\n";
+      s << "      #pragma unroll 1\n      for (int i = 0; i < NSP; ++i) Jr[(i64)i * nr] = fma(sL[i * BLKD + t], fu, fj * sA[i * BLKD + t]);\n";
+      for (int i = 0; i < N; ++i) {
+        std::string si = "sL" + sidx(i), ti = "sA" + sidx(i);
+        std::string dst = "Jr[(i64)" + std::to_string(i) + " * nr]";
+        bool hs = acc.count(i), hc = cr.count(i), diag = mode == JacMode::CN && i == k;
+        if (hs || hc) {
+          std::string tv = hc ? "fma(" + si + ", " + cr[i] + ", " + (hs ? acc[i] : std::string("0.0")) + ")" : acc[i];
+          std::string base = diag ? "fma(F, " + tv + ", 1.0)" : "F * " + tv;
+          s << "      " << dst << " = fma(" << si << ", fu, fma(fj, " << ti << ", " << base << "));\n";
+        } else if (diag) {
+          s << "      " << dst << " = fma(" << si << ", fu, fma(fj, " << ti << ", 1.0));\n";
+        }
+      }
+      if (mode == JacMode::CN) {
+        // right-hand side -F_k = c_k + (dt/2rho) W_k omega_k - Y_k (Eq. crank_nicol_rhs)
+        s << "      { const double y = __ldg(Yp + (i64)" << k << " * n);\n"
+             "        const double sk = (hh * " << lit(m.species[k].W) << ") * w;\n"
+             "        double ck;\n"
+             "        if (stp == 0) { ck = y + sk; g_c[(i64)" << k << " * cnt + p] = ck; } else { ck = g_c[(i64)" << k << " * cnt + p]; }\n"
+             "        g_b[(i64)" << k << " * cnt + p] = (ck + sk) - y; }\n";
+      }
+      s << "    }\n";
+    }
+    s << "  }\n}\n";
+    return;
   }
   // ---- phase 2: rows.  sL becomes s_i = rho/W_i, sA the Tdot column accumulators.
   // The barrier keeps the compiler from forwarding phase-1 values through registers.
@@ -896,6 +1025,193 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
   s << "    #pragma unroll 1\n    for (int i = 0; i < NSP; ++i) Jp[(i64)(1 + i) * n] = "
        "fma(-fma(sL[i * BLKD + t], U, sA[i * BLKD + t]), rcv, -tcv * sE[i * BLKD + t]);\n";
   s << "  }\n}\n";
+}
+
+// ---------------------------------------------------------------------------
+// Crank-Nicolson step (Sec. A.3.2, Eqs. crank_nicol_rhs to crank_nicol_jac):
+// preparation, batched dense solve of the Newton system, completion.  The
+// Newton system itself is assembled by the Jacobian kernel in mode CN.
+// ---------------------------------------------------------------------------
+void emit_cn_kernels(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C) {
+  int N = m.n_species();
+  // preparation: e = e(T^m, Y^m) (Eq. int_energy), iterate Y <- Y^m, T <- T^m
+  s << "\nextern \"C\" __global__ void __launch_bounds__(BLKD) pyro_cn_prep(i64 cnt, i64 n,\n"
+       "    const double* __restrict__ g_Tin, const double* __restrict__ g_Yin, double* __restrict__ g_Tout,\n"
+       "    double* __restrict__ g_Yout, double* __restrict__ g_e, int* __restrict__ g_state, int* __restrict__ g_it) {\n"
+       "  for (i64 p = (i64)blockIdx.x * BLKD + threadIdx.x; p < cnt; p += (i64)gridDim.x * BLKD) {\n"
+       "    const double* Yp = g_Yin + p;\n    const double T = g_Tin[p];\n"
+       "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n"
+       "    double B0 = 0.0, B1 = 0.0, B2 = 0.0, B3 = 0.0, B4 = 0.0, B5 = 0.0;\n";
+  for (int k = 0; k < N; ++k) {
+    s << "    { double y = __ldg(Yp + (i64)" << k << " * n);";
+    for (int q = 0; q < 6; ++q) {
+      double v[2] = {C[k].d[0][q], C[k].d[1][q]};
+      s << " B" << q << " = fma(y, " << sel(v) << ", B" << q << ");";
+    }
+    s << " }\n";
+  }
+  s << "    g_e[p] = " << lit((double)R_GAS) << " * fma(T, fma(T, fma(T, fma(T, fma(T, B5, B4), B3), B2), B1), B0);\n"
+       "    if (g_Yout != g_Yin) {\n"
+       "      #pragma unroll 1\n      for (int k = 0; k < NSP; ++k) g_Yout[(i64)k * n + p] = Yp[(i64)k * n];\n    }\n"
+       "    g_Tout[p] = T;\n    g_state[p] = 0;\n    g_it[p] = 0;\n  }\n}\n";
+
+  // batched solve: one warp per state
+  s << R"(
+// Newton update of one Crank-Nicolson iteration, one warp per state: solve
+// (I - dt/(2 rho) J) dY = -F by LU with partial pivoting in FP32 (rows scaled by
+// powers of two so that every entry is at most 1 in magnitude) and `refine`
+// steps of iterative refinement whose residuals b - A x are formed in FP64 from
+// the FP64 matrix; then Y += dY and the state's Newton bookkeeping: stop once
+// max_k |dY_k| <= tol, after one further step (the rule of the temperature solve).
+#define CN_LDA (NSP | 1)
+extern "C" __global__ void __launch_bounds__(CN_G * 32) pyro_cn_solve(i64 cnt, i64 n,
+    const double* __restrict__ g_A, const double* __restrict__ g_b, double* __restrict__ g_Y,
+    int* __restrict__ g_state, int* __restrict__ g_it, double tol, int max_newton, int refine,
+    unsigned long long* __restrict__ g_fail) {
+  extern __shared__ double s_cn[];
+  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const unsigned FULL = 0xffffffffu;
+  double* sd = s_cn + wi * NSP;                       // row scales (powers of two)
+  double* sx = s_cn + (CN_G + wi) * NSP;              // solution (FP64)
+  double* sr = s_cn + (2 * CN_G + wi) * NSP;          // right-hand side / residual (FP64)
+  float* fb = (float*)(s_cn + 3 * CN_G * NSP);
+  float* sM = fb + wi * (NSP * CN_LDA);                                // scaled LU factors
+  float* sv = fb + CN_G * NSP * CN_LDA + wi * NSP;                      // FP32 solve vector
+  float* sq = fb + CN_G * NSP * CN_LDA + CN_G * NSP + wi * NSP;         // reciprocal pivots
+  int* spiv = (int*)(fb + CN_G * NSP * CN_LDA + 2 * CN_G * NSP) + wi * NSP;   // pivot rows
+  for (i64 p = ((i64)blockIdx.x * CN_G + wi); p < cnt; p += (i64)gridDim.x * CN_G) {
+    const int st = g_state[p];
+    if (st >= 3) continue;
+    const double* Ag = g_A + (p / CN_G) * (i64)(NSP * NSP * CN_G) + (p % CN_G);
+    // row scales: 2^-e with 2^(e-1) <= max_j |A_ij| < 2^e
+    for (int i = 0; i < NSP; ++i) {
+      double mx = 0.0;
+      for (int j = l; j < NSP; j += 32) mx = fmax(mx, fabs(__ldg(Ag + (i64)(i * NSP + j) * CN_G)));
+      for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
+      if (l == 0) { int e; frexp(mx, &e); sd[i] = mx > 0.0 ? ldexp(1.0, -e) : 1.0; }
+    }
+    __syncwarp();
+    for (int i = 0; i < NSP; ++i) {
+      const double di = sd[i];
+      for (int j = l; j < NSP; j += 32) sM[i * CN_LDA + j] = (float)(__ldg(Ag + (i64)(i * NSP + j) * CN_G) * di);
+    }
+    for (int k = l; k < NSP; k += 32) { sr[k] = g_b[(i64)k * cnt + p]; sx[k] = 0.0; }
+    __syncwarp();
+    // LU factorisation with partial pivoting (row exchanges applied to the whole rows)
+    bool sing = false;
+    for (int k = 0; k < NSP; ++k) {
+      float bv = -1.0f;
+      int bi = k;
+      for (int i = k + l; i < NSP; i += 32) {
+        const float v = fabsf(sM[i * CN_LDA + k]);
+        if (v > bv) { bv = v; bi = i; }
+      }
+      for (int o = 16; o; o >>= 1) {
+        const float ov = __shfl_xor_sync(FULL, bv, o);
+        const int oi = __shfl_xor_sync(FULL, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if (!(bv > 0.0f) || bv > 3.0e38f) { sing = true; break; }
+      if (bi != k)
+        for (int j = l; j < NSP; j += 32) {
+          const float a = sM[k * CN_LDA + j];
+          sM[k * CN_LDA + j] = sM[bi * CN_LDA + j];
+          sM[bi * CN_LDA + j] = a;
+        }
+      if (l == 0) spiv[k] = bi;
+      __syncwarp();
+      const float inv = __frcp_rn(sM[k * CN_LDA + k]);
+      if (l == 0) sq[k] = inv;
+      for (int i = k + 1 + l; i < NSP; i += 32) sM[i * CN_LDA + k] *= inv;
+      __syncwarp();
+      for (int j = k + 1 + l; j < NSP; j += 32) {
+        const float u = sM[k * CN_LDA + j];
+        for (int i = k + 1; i < NSP; ++i) sM[i * CN_LDA + j] = fmaf(-sM[i * CN_LDA + k], u, sM[i * CN_LDA + j]);
+      }
+      __syncwarp();
+    }
+    double dmax = 0.0;
+    if (!sing) {
+      for (int pass = 0; pass <= refine; ++pass) {
+        if (pass > 0) {   // residual r = b - A x in FP64
+          for (int i = l; i < NSP; i += 32) {
+            double acc = g_b[(i64)i * cnt + p];
+            const double* Ai = Ag + (i64)(i * NSP) * CN_G;
+            for (int j = 0; j < NSP; ++j) acc = fma(-__ldg(Ai + (i64)j * CN_G), sx[j], acc);
+            sr[i] = acc;
+          }
+          __syncwarp();
+        }
+        for (int k = l; k < NSP; k += 32) sv[k] = (float)(sr[k] * sd[k]);
+        __syncwarp();
+        if (l == 0)
+          for (int k = 0; k < NSP; ++k) {
+            const int q = spiv[k];
+            if (q != k) { const float a = sv[k]; sv[k] = sv[q]; sv[q] = a; }
+          }
+        __syncwarp();
+        for (int k = 0; k < NSP - 1; ++k) {        // unit lower triangle
+          const float vk = sv[k];
+          for (int i = k + 1 + l; i < NSP; i += 32) sv[i] = fmaf(-sM[i * CN_LDA + k], vk, sv[i]);
+          __syncwarp();
+        }
+        for (int k = NSP - 1; k >= 0; --k) {       // upper triangle
+          const float vk = sv[k] * sq[k];
+          __syncwarp();
+          if (l == 0) sv[k] = vk;
+          for (int i = l; i < k; i += 32) sv[i] = fmaf(-sM[i * CN_LDA + k], vk, sv[i]);
+          __syncwarp();
+        }
+        for (int k = l; k < NSP; k += 32) sx[k] += (double)sv[k];
+        __syncwarp();
+      }
+      for (int k = l; k < NSP; k += 32) {
+        const double dx = sx[k];
+        g_Y[(i64)k * n + p] += dx;
+        const double a = fabs(dx);
+        dmax = (a > dmax || a != a) ? a : dmax;
+      }
+      for (int o = 16; o; o >>= 1) {
+        const double od = __shfl_xor_sync(FULL, dmax, o);
+        dmax = (od > dmax || od != od) ? od : dmax;
+      }
+    }
+    if (l == 0) {
+      const int it = g_it[p] + 1;
+      g_it[p] = it;
+      int ns;
+      if (sing || !(dmax == dmax)) ns = 4;
+      else if (st == 2) ns = 3;
+      else if (dmax <= tol) ns = 2;
+      else if (it >= max_newton) ns = 4;
+      else ns = 1;
+      g_state[p] = ns;
+      if (ns == 4) atomicAdd(g_fail, 1ull);
+    }
+    __syncwarp();
+  }
+}
+
+// completion: T from (e, Y^{m+1}) and the Newton step counts (-1: failed)
+extern "C" __global__ void __launch_bounds__(BLKD) pyro_cn_finish(i64 cnt, i64 n, const double* __restrict__ g_e,
+    const double* __restrict__ g_Y, double* __restrict__ g_T, const int* __restrict__ g_state,
+    const int* __restrict__ g_it, int* __restrict__ g_iters, int max_iter, double tol,
+    unsigned long long* __restrict__ g_fail) {
+  const float tolf = (float)tol;
+  for (i64 p = (i64)blockIdx.x * BLKD + threadIdx.x; p < cnt; p += (i64)gridDim.x * BLKD) {
+    int st = g_state[p];
+    if (st == 3) {
+      int tit;
+      const double T = pyro_tsolve<false>(g_Y + p, n, g_e[p], g_T[p], max_iter, tolf, &tit);
+      if (tit < 0) { st = 4; atomicAdd(g_fail, 1ull); } else { g_T[p] = T; }
+    } else if (st != 4) {
+      st = 4;
+      atomicAdd(g_fail, 1ull);
+    }
+    if (g_iters) g_iters[p] = st == 3 ? g_it[p] : -1;
+  }
+}
+)";
 }
 
 // ---------------------------------------------------------------------------
@@ -1238,6 +1554,25 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, cons
     Src d; d << pre.o.str(); emit_jacobian_kernel(d, m, C, opt.deriv_block, &nslots); out.group_sources["jac"] = d.o.str();
   }
   out.jac_slots = nslots;
+  {
+    int ns2 = 0;
+    Src d; d << pre.o.str();
+    emit_jacobian_kernel(d, m, C, opt.deriv_block, &ns2, JacMode::ADIA);
+    out.group_sources["jad"] = d.o.str();
+  }
+  {
+    // Crank-Nicolson: temperature solve + Newton-system assembly + batched solve
+    int ns2 = 0;
+    Src d; d << pre.o.str();
+    d << "#define CN_G " << kCnGroup << "\n#define opt_mixed " << (opt.mixed_newton ? 1 : 0) << "\n";
+    std::map<std::string, double> dummy;
+    emit_tsolve(d, m, C, opt, dummy);
+    emit_jacobian_kernel(d, m, C, opt.deriv_block, &ns2, JacMode::CN);
+    emit_cn_kernels(d, m, C);
+    out.group_sources["cn"] = d.o.str();
+    const int lda = N | 1;
+    out.smem_dyn_bytes_cn_solve = kCnGroup * (3 * N * 8 + N * lda * 4 + 3 * N * 4);
+  }
   out.smem_dyn_bytes_deriv = opt.dgstore ? 0 : 4 * N * opt.deriv_block * (int)sizeof(double);
   out.stats["jacobian_scratch_doubles_per_point"] = nslots;
   out.stats["deriv_block"] = opt.deriv_block;

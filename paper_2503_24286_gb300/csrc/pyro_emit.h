@@ -25,13 +25,18 @@ struct EmitOptions {
 
 struct EmitResult {
   std::string source;                     // CUDA C of the forward kernels
-  std::map<std::string, std::string> group_sources;   // "fwd", "jvp", "vjp", "jac"
+  std::map<std::string, std::string> group_sources;   // "fwd", "jvp", "vjp", "jac", "jad", "cn"
 
   std::map<std::string, double> stats;    // static FP64-pipe op counts per point etc.
   int smem_dyn_bytes_omega = 0;           // dynamic shared memory of the omega kernel
   int smem_dyn_bytes_deriv = 0;           // dynamic shared memory of the derivative kernels
   int jac_slots = 0;                      // scratch doubles per point of the Jacobian kernel
+  int smem_dyn_bytes_cn_solve = 0;        // dynamic shared memory of the Crank-Nicolson solve kernel
 };
+
+// States per group of the Crank-Nicolson Newton-matrix layout [n/G][N^2][G]
+// (also the warps per block of the batched solve).
+constexpr int kCnGroup = 4;
 
 EmitResult emit_module(const Mechanism& m, const EmitOptions& opt);
 

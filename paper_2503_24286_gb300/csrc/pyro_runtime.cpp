@@ -234,11 +234,15 @@ struct pyro_mech {
     bool failed = false;
     std::string err;
     double* store = nullptr;   // per-block species arrays of this group (large mechanisms)
+    std::map<std::string, CUfunction> fn;   // further kernels of the group
+    int solve_blocks_per_sm = 0;            // Crank-Nicolson batched solve
   };
   std::map<std::string, Group> groups;
   std::mutex group_mu;
   double* d_jac_scratch = nullptr;
   size_t jac_scratch_bytes = 0;
+  void* d_cn = nullptr;            // Crank-Nicolson per-chunk arrays (grows on demand)
+  size_t cn_bytes = 0;
   double* d_store = nullptr;       // per-block species arrays when they do not fit in shared memory
   size_t store_bytes = 0;
   // learned initial guess
@@ -453,7 +457,8 @@ int ensure_store(pyro_mech* h, size_t bytes) {
 }
 
 const char* group_kernel(const std::string& g) {
-  return g == "jvp" ? "pyro_jvp" : g == "vjp" ? "pyro_vjp" : "pyro_jacobian";
+  return g == "jvp" ? "pyro_jvp" : g == "vjp" ? "pyro_vjp" : g == "jad" ? "pyro_jacobian_adiabatic"
+       : g == "cn" ? "pyro_cn_assemble" : "pyro_jacobian";
 }
 
 // Compile (in parallel threads, cached on disk) and load the named derivative
@@ -508,7 +513,40 @@ int ensure_groups(pyro_mech* h, const std::vector<std::string>& names) {
       cudaError_t e = cudaMalloc(&G.store, bytes);
       if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("species-array store allocation: ") + cudaGetErrorString(e));
     }
+    if (todo[i] == "cn") {
+      for (const char* nm : {"pyro_cn_prep", "pyro_cn_solve", "pyro_cn_finish"}) {
+        CUfunction f = nullptr;
+        r = d.ModuleGetFunction(&f, G.module, nm);
+        if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, std::string("missing kernel ") + nm);
+        G.fn[nm] = f;
+      }
+      const int ssm = h->emitted.smem_dyn_bytes_cn_solve;
+      r = d.FuncSetAttribute(G.fn["pyro_cn_solve"], CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, ssm);
+      if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "shared memory request (Crank-Nicolson solve): " + cu_err(r));
+      int sb = 0;
+      r = d.Occupancy(&sb, G.fn["pyro_cn_solve"], 32 * pyro::kCnGroup, ssm);
+      if (r != CUDA_SUCCESS || sb < 1) return fail(PYRO_ECUDA, "pyro_cn_solve does not fit on an SM");
+      G.solve_blocks_per_sm = sb;
+      h->emitted.stats["cn_solve_blocks_per_sm"] = sb;
+    }
     h->emitted.stats[todo[i] + "_cubin_bytes"] = (double)cubins[i].size();
+  }
+  return PYRO_OK;
+}
+
+// grow the per-block scratch of the Jacobian-type kernels (per-reaction partials)
+int ensure_jac_scratch(pyro_mech* h, const pyro_mech::Group& G, int64_t n) {
+  std::lock_guard<std::mutex> lock(h->mu);
+  int64_t need = (n + h->opt.deriv_block - 1) / h->opt.deriv_block;
+  int64_t grid = std::min<int64_t>(need, (int64_t)h->num_sms * G.blocks_per_sm);
+  size_t bytes = (size_t)grid * h->emitted.jac_slots * h->opt.deriv_block * sizeof(double);
+  if (bytes > h->jac_scratch_bytes) {
+    if (h->d_jac_scratch) cudaFree(h->d_jac_scratch);
+    h->d_jac_scratch = nullptr;
+    h->jac_scratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&h->d_jac_scratch, bytes);
+    if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("Jacobian scratch allocation: ") + cudaGetErrorString(e));
+    h->jac_scratch_bytes = bytes;
   }
   return PYRO_OK;
 }
@@ -623,6 +661,7 @@ void pyro_mech_free(pyro_mech* h) {
   if (h->module && driver().ModuleUnload) driver().ModuleUnload(h->module);
   if (h->d_fail) cudaFree(h->d_fail);
   if (h->d_jac_scratch) cudaFree(h->d_jac_scratch);
+  if (h->d_cn) cudaFree(h->d_cn);
   if (h->d_store) cudaFree(h->d_store);
   if (h->mlp) pyro::mlp_free(h->mlp);
   if (h->warp) pyro::warp_free(h->warp);
@@ -799,6 +838,8 @@ int pyro_mech_prepare(const pyro_mech* hc, const char* kernels) {
     while (std::getline(ss, item, ',')) {
       if (item == "jvp" || item == "vjp") names.push_back(item);
       else if (item == "jacobian" || item == "jac") names.push_back("jac");
+      else if (item == "jacobian_adiabatic" || item == "jad") names.push_back("jad");
+      else if (item == "cn" || item == "crank_nicolson") names.push_back("cn");
       else if (!item.empty()) return fail(PYRO_EINVAL, "unknown kernel group '" + item + "'");
     }
   }
@@ -854,21 +895,7 @@ int pyro_jacobian(const pyro_mech* hc, int64_t n, const double* rho, const doubl
   const pyro_mech::Group& G = h->groups["jac"];
   int NP = h->m.n_species() + 1;
   const int64_t NS = h->m.n_species();
-  // per-block scratch for the per-reaction partials (grows on demand)
-  {
-    std::lock_guard<std::mutex> lock(h->mu);
-    int64_t need = (n + h->opt.deriv_block - 1) / h->opt.deriv_block;
-    int64_t grid = std::min<int64_t>(need, (int64_t)h->num_sms * G.blocks_per_sm);
-    size_t bytes = (size_t)grid * h->emitted.jac_slots * h->opt.deriv_block * sizeof(double);
-    if (bytes > h->jac_scratch_bytes) {
-      if (h->d_jac_scratch) cudaFree(h->d_jac_scratch);
-      h->d_jac_scratch = nullptr;
-      h->jac_scratch_bytes = 0;
-      cudaError_t e = cudaMalloc(&h->d_jac_scratch, bytes);
-      if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("Jacobian scratch allocation: ") + cudaGetErrorString(e));
-      h->jac_scratch_bytes = bytes;
-    }
-  }
+  if (int rc = ensure_jac_scratch(h, G, n)) return rc;
   return with_args(h, n, {{rho, 1, 8, true, false}, {T, 1, 8, true, false}, {Y, NS, 8, true, false}, {J, (int64_t)NP * NP, 8, false, true}},
                    stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
                      long long nn = nc;
@@ -877,6 +904,135 @@ int pyro_jacobian(const pyro_mech* hc, int64_t n, const double* rho, const doubl
                    });
 }
 
+
+int pyro_jacobian_adiabatic(const pyro_mech* hc, int64_t n, const double* rho, const double* T, const double* Y,
+                            double* J, void* stream) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n < 0 || (n > 0 && (!rho || !T || !Y || !J)))
+    return fail(PYRO_EINVAL, "pyro_jacobian_adiabatic: bad arguments");
+  if (n == 0) return PYRO_OK;
+  if (int rc = check_device(h)) return rc;
+  if (h->emitted.stats["deriv_store_global"] > 0)
+    return fail(PYRO_EINVAL, "the dense Jacobian needs the per-state species arrays in shared memory "
+                             "(4 N deriv_block 8 B <= 160 KB); use pyro_jvp / pyro_vjp for this mechanism");
+  if (int rc = ensure_groups(h, {"jad"})) return rc;
+  const pyro_mech::Group& G = h->groups["jad"];
+  const int64_t NS = h->m.n_species();
+  if (int rc = ensure_jac_scratch(h, G, n)) return rc;
+  return with_args(h, n, {{rho, 1, 8, true, false}, {T, 1, 8, true, false}, {Y, NS, 8, true, false}, {J, NS * NS, 8, false, true}},
+                   stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
+                     long long nn = nc;
+                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &h->d_jac_scratch};
+                     return launch_deriv(h, G, nc, st, params);
+                   });
+}
+
+namespace {
+// States per chunk of the Crank-Nicolson work arrays (Newton matrix N^2 doubles
+// per state): about 2 GiB, a multiple of the matrix group size.
+int64_t cn_chunk(const pyro_mech* h, int64_t n) {
+  const int64_t N = h->m.n_species();
+  const int64_t Gs = pyro::kCnGroup;
+  const size_t per_state = (size_t)(N * N + 2 * N + 2) * sizeof(double);
+  int64_t m = std::max<int64_t>(4096, (int64_t)(((size_t)2 << 30) / per_state));
+  m = std::min<int64_t>(m, (n + Gs - 1) / Gs * Gs);
+  return (m + Gs - 1) / Gs * Gs;
+}
+
+// Allocate (grow) the Crank-Nicolson work arrays and the Jacobian scratch for
+// calls of up to n states.
+int cn_reserve(pyro_mech* h, int64_t n) {
+  const int64_t N = h->m.n_species();
+  const int64_t m = cn_chunk(h, n);
+  if (int rc = ensure_jac_scratch(h, h->groups["cn"], m)) return rc;
+  std::lock_guard<std::mutex> lock(h->mu);
+  const size_t bytes = (size_t)m * (size_t)(N * N + 2 * N + 2) * sizeof(double);
+  if (bytes > h->cn_bytes) {
+    if (h->d_cn) cudaFree(h->d_cn);
+    h->d_cn = nullptr;
+    h->cn_bytes = 0;
+    cudaError_t e = cudaMalloc(&h->d_cn, bytes);
+    if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("Crank-Nicolson scratch allocation: ") + cudaGetErrorString(e));
+    h->cn_bytes = bytes;
+  }
+  return PYRO_OK;
+}
+
+// Crank-Nicolson step over `cnt` states of arrays with row stride `ld` (pointers
+// already offset to the first state), in chunks of cn_chunk states; the work
+// arrays must have been reserved (cn_reserve) for at least cnt states.
+int cn_run(pyro_mech* h, int64_t cnt, int64_t ld, double dt, const double* rho, const double* Tin,
+           const double* Yin, double tol, int max_newton, int refine, double* Tout, double* Yout, int32_t* iters,
+           void* stream) {
+  const pyro_mech::Group& G = h->groups["cn"];
+  const int64_t N = h->m.n_species();
+  const int64_t Gs = pyro::kCnGroup;
+  const int64_t m = cn_chunk(h, cnt);
+  double* dA = (double*)h->d_cn;                 // [m/G][N^2][G]
+  double* dc = dA + (size_t)m * N * N;           // [N][m]
+  double* db = dc + (size_t)m * N;               // [N][m]
+  double* de = db + (size_t)m * N;               // [m]
+  int* dstate = (int*)(de + m);                  // [m]
+  int* dit = dstate + m;                         // [m]
+  Driver& d = driver();
+  const int bd = h->opt.deriv_block;
+  double Tg_tol = 1e-10;
+  int t_iter = 50;
+  for (int64_t p0 = 0; p0 < cnt; p0 += m) {
+    long long nc = std::min<int64_t>(m, cnt - p0), nld = ld;
+    const double* rho_c = rho + p0;
+    const double* Tin_c = Tin + p0;
+    const double* Yin_c = Yin + p0;
+    double* Tout_c = Tout + p0;
+    double* Yout_c = Yout + p0;
+    int32_t* it_c = iters ? iters + p0 : nullptr;
+    unsigned gs = (unsigned)std::min<int64_t>((nc + bd - 1) / bd, (int64_t)h->num_sms * 8);
+    void* pp[] = {&nc, &nld, &Tin_c, &Yin_c, &Tout_c, &Yout_c, &de, &dstate, &dit};
+    CUresult r = d.LaunchKernel(G.fn.at("pyro_cn_prep"), gs, 1, 1, bd, 1, 1, 0, as_stream(stream), pp, nullptr);
+    if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
+    unsigned gsolve = (unsigned)std::min<int64_t>((nc + Gs - 1) / Gs, (int64_t)h->num_sms * G.solve_blocks_per_sm);
+    for (int it = 0; it <= max_newton; ++it) {
+      void* pa[] = {&nc, &nld, &rho_c, &de, &Yout_c, &dc, &Tout_c, &dstate, &dt, &t_iter, &Tg_tol, &dA, &db,
+                    &h->d_jac_scratch, &h->d_fail};
+      if (int rc = launch_deriv(h, G, nc, stream, pa)) return rc;
+      void* ps[] = {&nc, &nld, &dA, &db, &Yout_c, &dstate, &dit, &tol, &max_newton, &refine, &h->d_fail};
+      r = d.LaunchKernel(G.fn.at("pyro_cn_solve"), gsolve, 1, 1, 32 * pyro::kCnGroup, 1, 1,
+                         h->emitted.smem_dyn_bytes_cn_solve, as_stream(stream), ps, nullptr);
+      if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
+    }
+    void* pf[] = {&nc, &nld, &de, &Yout_c, &Tout_c, &dstate, &dit, &it_c, &t_iter, &Tg_tol, &h->d_fail};
+    r = d.LaunchKernel(G.fn.at("pyro_cn_finish"), gs, 1, 1, bd, 1, 1, 0, as_stream(stream), pf, nullptr);
+    if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
+  }
+  return PYRO_OK;
+}
+}  // namespace
+
+int pyro_cn_step(const pyro_mech* hc, int64_t n, double dt, const double* rho, const double* T, const double* Y,
+                 double tol, int max_newton, double* T_out, double* Y_out, int32_t* iters_out, void* stream) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n < 0 || (n > 0 && (!rho || !T || !Y || !T_out || !Y_out)))
+    return fail(PYRO_EINVAL, "pyro_cn_step: bad arguments");
+  if (!(dt >= 0.0) || !(tol > 0.0) || max_newton < 1 || max_newton > 1000)
+    return fail(PYRO_EINVAL, "pyro_cn_step: need dt >= 0, tol > 0 and 1 <= max_newton <= 1000");
+  if (n == 0) return PYRO_OK;
+  if (int rc = check_device(h)) return rc;
+  if (h->emitted.stats["deriv_store_global"] > 0)
+    return fail(PYRO_EINVAL, "the Crank-Nicolson step needs the dense Jacobian, which needs the per-state species "
+                             "arrays in shared memory (4 N deriv_block 8 B <= 160 KB)");
+  if (int rc = ensure_groups(h, {"cn"})) return rc;
+  const int64_t NS = h->m.n_species();
+  const int refine = 2;
+  if (int rc = cn_reserve(h, n)) return rc;
+  int rc = with_args(h, n, {{rho, 1, 8, true, false}, {T, 1, 8, true, false}, {Y, NS, 8, true, false},
+                            {T_out, 1, 8, false, true}, {Y_out, NS, 8, false, true}, {iters_out, 1, 4, false, true}},
+                     stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
+                       return cn_run(h, nc, nc, dt, (const double*)d[0], (const double*)d[1], (const double*)d[2],
+                                     tol, max_newton, refine, (double*)d[3], (double*)d[4], (int32_t*)d[5], st);
+                     });
+  if (rc) return rc;
+  return maybe_checked(h, stream);
+}
 
 // ---- learned initial guess ---------------------------------------------------
 namespace {

@@ -67,6 +67,23 @@ def test_derivative_kernels_compile_without_gpu(mech_files):
         m.prepare("hessian")
 
 
+def test_adiabatic_jacobian_and_crank_nicolson_kernels_compile_without_gpu(mech_files):
+    m = B.Mechanism(mech_files[0][0], "device=0")
+    m.prepare("jacobian_adiabatic,cn")
+    assert m.stat("jad_cubin_bytes") > 1000 and m.stat("cn_cubin_bytes") > 1000
+    L = B.lib()
+    D = ctypes.POINTER(ctypes.c_double)
+    x = (ctypes.c_double * 40)()
+    px = ctypes.cast(x, D)
+    # argument checks come before any device work: bad dt / tol / max_newton, null arrays
+    assert L.pyro_cn_step(m.handle, 4, -1.0, px, px, px, 1e-12, 20, px, px, None, None) == B.PYRO_EINVAL
+    assert L.pyro_cn_step(m.handle, 4, 1e-9, px, px, px, 0.0, 20, px, px, None, None) == B.PYRO_EINVAL
+    assert L.pyro_cn_step(m.handle, 4, 1e-9, px, px, px, 1e-12, 0, px, px, None, None) == B.PYRO_EINVAL
+    assert L.pyro_cn_step(m.handle, 4, 1e-9, None, px, px, 1e-12, 20, px, px, None, None) == B.PYRO_EINVAL
+    assert L.pyro_cn_step(m.handle, 0, 1e-9, None, None, None, 1e-12, 20, None, None, None, None) == B.PYRO_OK
+    assert L.pyro_jacobian_adiabatic(m.handle, 4, None, px, px, px, None) == B.PYRO_EINVAL
+
+
 def test_unbalanced_mechanism_is_rejected(tmp_path):
     mech = handmech.abcd_mechanism()
     mech.reactions[0].products = [(2, 1), (3, 2)]      # H + O2 -> OH + 2 O : O not balanced
