@@ -340,7 +340,7 @@ def crank_nicolson_rates(synth, dev, stream, args, rank):
     dt = cfg["dt"]
     res = {"workload": "53 species / 325 reactions, %d states, T ~ U[2000, 2800] K, p ~ U[0.5, 20] atm, "
                        "Dirichlet Y; one Crank-Nicolson step, dt = %g s, Newton tol 1e-12 on max|dY|; "
-                       "Newton matrix by FP32 LU + 2 FP64 refinement steps" % (n, dt)}
+                       "Newton matrix by FP32 LU + 1 FP64 refinement step" % (n, dt)}
     To = torch.empty_like(T)
     Yo = torch.empty_like(Y)
     _, _, it = m.cn_step(dt, rho, T, Y, T_out=To, Y_out=Yo, with_iters=True)

@@ -193,14 +193,14 @@ int pyro_jacobian_adiabatic(const pyro_mech* mech, int64_t n, const double* rho,
  * pyro_jacobian_adiabatic at each iterate and T re-solved from (e, Y) at each
  * iterate (e = e(T^m, Y^m)).  Stop once max_k |dY_k| <= tol, after one further
  * Newton step; at most max_newton steps.  The linear systems are solved by LU
- * with partial pivoting in FP32 on row-scaled matrices plus two steps of
- * iterative refinement with FP64 residuals.
+ * with partial pivoting in FP32 on row-scaled matrices plus one step of
+ * iterative refinement with an FP64 residual.
  * rho, T: [n] state at t^m; Y: [N][n]; T_out: [n] and Y_out: [N][n] at
  * t^m + dt (may alias T and Y); iters_out: nullable int32 [n], Newton steps
  * taken or -1 where the step failed (no convergence, singular matrix or a
  * failed temperature solve; counted by pyro_nonconverged).
- * Work arrays (about 8 (N^2 + 2N + 2) bytes per state, in chunks of at most
- * 2 GiB) are allocated on first use and kept by the handle.  Returns
+ * Work arrays (about 8 (N^2 + 2N + 3) bytes per state, in chunks of at most
+ * 8 GiB) are allocated on first use and kept by the handle.  Returns
  * PYRO_EINVAL for dt < 0, tol <= 0 or max_newton outside [1, 1000]. */
 int pyro_cn_step(const pyro_mech* mech, int64_t n, double dt, const double* rho, const double* T,
                  const double* Y, double tol, int max_newton, double* T_out, double* Y_out,

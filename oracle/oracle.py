@@ -71,6 +71,14 @@ def lib():
         L.orc_temperature_bisect_enthalpy.argtypes = [P, I64, D, D, ctypes.c_double, ctypes.c_double, D]
         L.orc_jacobian_adiabatic.argtypes = [P, I64, D, D, D, D]
         L.orc_source_at_energy.argtypes = [P, I64, D, D, D, D]
+        L.orc_has_transport.restype = ctypes.c_int
+        L.orc_has_transport.argtypes = [P]
+        L.orc_species_transport.argtypes = [P, ctypes.c_int, ctypes.c_double, D]
+        L.orc_binary_diffusivity.restype = ctypes.c_double
+        L.orc_binary_diffusivity.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        L.orc_wilke_phi.argtypes = [P, ctypes.c_double, D]
+        L.orc_transport.argtypes = [P, I64, D, D, D, D, D]
+        L.orc_transport_ld.argtypes = [P, I64, D, D, D, D, D]
         L.orc_solve_dense.restype = ctypes.c_int
         L.orc_solve_dense.argtypes = [ctypes.c_int, D, D]
         L.orc_cn_step.restype = I64
@@ -249,6 +257,35 @@ class Oracle:
         bad = lib().orc_cn_step(self._h, n, float(dt), _d(rho), _d(T), _d(Y), float(tol), int(max_newton),
                                 _d(Yo), _d(To), it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
         return Yo, To, it, int(bad)
+
+    # --- mixture-averaged transport (Sec. A.2) ---------------------------------
+    @property
+    def has_transport(self) -> bool:
+        return bool(lib().orc_has_transport(self._h))
+
+    def species_transport(self, k: int, T: float):
+        """(mu_k, kappa_k) of species k at T."""
+        out = np.zeros(2)
+        lib().orc_species_transport(self._h, int(k), float(T), _d(out))
+        return out[0], out[1]
+
+    def binary_diffusivity(self, k: int, j: int, T: float) -> float:
+        return lib().orc_binary_diffusivity(self._h, int(k), int(j), float(T))
+
+    def wilke_phi(self, T: float) -> np.ndarray:
+        """[N, N] Wilke's Phi_kj at T."""
+        Phi = np.zeros((self.N, self.N))
+        lib().orc_wilke_phi(self._h, float(T), _d(Phi))
+        return Phi
+
+    def transport(self, T, Y, long_double=False):
+        """(mu [n], kappa [n], D_km [N, n]) of the mixture-averaged model."""
+        T, Y = _c(T), _c(Y)
+        n = T.size
+        mu, kappa, Dm = np.zeros(n), np.zeros(n), np.zeros((self.N, n))
+        f = lib().orc_transport_ld if long_double else lib().orc_transport
+        f(self._h, n, _d(T), _d(Y), _d(mu), _d(kappa), _d(Dm))
+        return mu, kappa, Dm
 
     def jvp(self, rho, T, Y, drho, dT, dY):
         args = [_c(a) for a in (rho, T, Y, drho, dT, dY)]

@@ -68,6 +68,9 @@ struct OMech {
   std::vector<double> el_weight;
   std::vector<OSpecies> sp;
   std::vector<OReaction> rx;
+  // transport fits (Sec. A.2), coefficients of (log T)^m, m = 0..4; empty if absent
+  std::vector<std::vector<double>> visc, cond;              // [N][5]
+  std::vector<std::vector<std::vector<double>>> bdiff;      // [N][N][5], symmetric
   int N() const { return (int)sp.size(); }
   int M() const { return (int)rx.size(); }
 };
@@ -164,6 +167,30 @@ bool parse_mech(const char* path, OMech& m) {
       } else { g_err = "unknown reaction token " + tok; return false; }
     }
     if (tok != "end") { g_err = "unterminated reaction"; return false; }
+  }
+  // optional transport section: per-species viscosity and conductivity fits,
+  // then the binary diffusivity fit of every pair k < j
+  if (next(is)) {
+    int nt = 0; is >> key >> nt;
+    if (key != "transport" || nt != ns) { g_err = "bad transport header"; return false; }
+    m.visc.assign(ns, std::vector<double>(5, 0.0));
+    m.cond.assign(ns, std::vector<double>(5, 0.0));
+    m.bdiff.assign(ns, std::vector<std::vector<double>>(ns, std::vector<double>(5, 0.0)));
+    for (int q = 0; q < ns; ++q) {
+      if (!next(is)) { g_err = "short transport section"; return false; }
+      int k; is >> key >> k;
+      if (key != "tspecies" || k < 0 || k >= ns) { g_err = "bad tspecies line"; return false; }
+      for (int i = 0; i < 5; ++i) is >> m.visc[k][i];
+      for (int i = 0; i < 5; ++i) is >> m.cond[k][i];
+      if (!is) { g_err = "short tspecies line"; return false; }
+    }
+    for (int q = 0; q < ns * (ns - 1) / 2; ++q) {
+      if (!next(is)) { g_err = "short transport section"; return false; }
+      int k, j; is >> key >> k >> j;
+      if (key != "tbinary" || k < 0 || j < 0 || k >= ns || j >= ns || k == j) { g_err = "bad tbinary line"; return false; }
+      for (int i = 0; i < 5; ++i) { is >> m.bdiff[k][j][i]; m.bdiff[j][k][i] = m.bdiff[k][j][i]; }
+      if (!is) { g_err = "short tbinary line"; return false; }
+    }
   }
   return true;
 }
@@ -520,6 +547,91 @@ int cn_step(const OMech& m, double rho, double dt, const double* Ym, double Tm, 
 }
 
 // ---------------------------------------------------------------------------
+// Mixture-averaged transport (Sec. A.2: Eq. mixavg_flux, Eq. diff_mix_rule,
+// Eq. mixavg_viscosity, Eq. mixavg_conductivity, Eq. species_cond).
+// Reading (t1): "log" in the fits is the natural logarithm.  Reading (t2): the
+// binary diffusivity fits carry no pressure factor, as printed.
+// ---------------------------------------------------------------------------
+
+template <class S> S poly_logT(const std::vector<double>& c, S T) {
+  S lt = std::log(T), v = 0;
+  for (int m = 0; m <= 4; ++m) v += c[m] * std::pow(lt, (double)m);
+  return v;
+}
+
+// mu_i = sqrt(T) [sum_m b_im (log T)^m]^2
+template <class S> S species_viscosity(const OMech& m, int k, S T) {
+  S b = poly_logT(m.visc[k], T);
+  return std::sqrt(T) * b * b;
+}
+// kappa_i = sqrt(T) sum_m c_im (log T)^m      (Eq. species_cond)
+template <class S> S species_conductivity(const OMech& m, int k, S T) {
+  return std::sqrt(T) * poly_logT(m.cond[k], T);
+}
+// D_ij = sqrt(T) sum_m a_ijm (log T)^m
+template <class S> S binary_diffusivity(const OMech& m, int k, int j, S T) {
+  return std::sqrt(T) * poly_logT(m.bdiff[k][j], T);
+}
+
+// mole fractions X_k = W Y_k / W_k with W = (sum_k Y_k/W_k)^-1 (Eq. eos)
+template <class S> S mole_fractions(const OMech& m, const S* Y, S* X) {
+  S inv = 0;
+  for (int k = 0; k < m.N(); ++k) inv += Y[k] / m.sp[k].W;
+  S W = 1.0 / inv;
+  for (int k = 0; k < m.N(); ++k) X[k] = W * Y[k] / m.sp[k].W;
+  return W;
+}
+
+// Wilke's Phi_kj = [1 + sqrt((mu_k/mu_j) sqrt(W_j/W_k))]^2 / sqrt(8 (1 + W_k/W_j))
+template <class S> S wilke_phi(const OMech& m, int k, int j, S mu_k, S mu_j) {
+  double Wk = m.sp[k].W, Wj = m.sp[j].W;
+  S t = 1.0 + std::sqrt((mu_k / mu_j) * std::sqrt(Wj / Wk));
+  return t * t / std::sqrt(8.0 * (1.0 + Wk / Wj));
+}
+
+// mu = sum_k X_k mu_k / sum_j Phi_kj X_j      (Eq. mixavg_viscosity)
+template <class S> S mixture_viscosity(const OMech& m, S T, const S* Y) {
+  int N = m.N();
+  std::vector<S> X(N), mu(N);
+  mole_fractions(m, Y, X.data());
+  for (int k = 0; k < N; ++k) mu[k] = species_viscosity(m, k, T);
+  S out = 0;
+  for (int k = 0; k < N; ++k) {
+    S den = 0;
+    for (int j = 0; j < N; ++j) den += wilke_phi(m, k, j, mu[k], mu[j]) * X[j];
+    out += X[k] * mu[k] / den;
+  }
+  return out;
+}
+
+// kappa = (1/2) [sum_k X_k kappa_k + (sum_k X_k/kappa_k)^-1]      (Eq. mixavg_conductivity)
+template <class S> S mixture_conductivity(const OMech& m, S T, const S* Y) {
+  int N = m.N();
+  std::vector<S> X(N);
+  mole_fractions(m, Y, X.data());
+  S a = 0, h = 0;
+  for (int k = 0; k < N; ++k) {
+    S kk = species_conductivity(m, k, T);
+    a += X[k] * kk;
+    h += X[k] / kk;
+  }
+  return 0.5 * (a + 1.0 / h);
+}
+
+// D_km = (W - X_k W_k)/W (sum_{j != k} X_j/D_kj)^-1      (Eq. diff_mix_rule)
+template <class S> void mixture_diffusivities(const OMech& m, S T, const S* Y, S* Dm) {
+  int N = m.N();
+  std::vector<S> X(N);
+  S W = mole_fractions(m, Y, X.data());
+  for (int k = 0; k < N; ++k) {
+    S sum = 0;
+    for (int j = 0; j < N; ++j)
+      if (j != k) sum += X[j] / binary_diffusivity(m, k, j, T);
+    Dm[k] = (W - X[k] * m.sp[k].W) / W / sum;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // BF16 MLP for the Newton initial guess (model definition; FP64 arithmetic
 // with bf16 rounding at the same points as the GPU network).
 // ---------------------------------------------------------------------------
@@ -855,6 +967,60 @@ void orc_source_at_energy(void* h, int64_t n, const double* rho, const double* e
 // Dense solve (Gaussian elimination with partial pivoting), one system: A [n*n]
 // row-major, b [n]; x returned in b.  Returns 0, or -1 for a singular matrix.
 int orc_solve_dense(int n, double* A, double* b) { return solve_dense(n, A, b) ? 0 : -1; }
+
+int orc_has_transport(void* h) { return ((OMech*)h)->visc.empty() ? 0 : 1; }
+
+// species fits at T: out = (mu_k, kappa_k)
+void orc_species_transport(void* h, int k, double T, double* out) {
+  const OMech& m = *(OMech*)h;
+  out[0] = species_viscosity(m, k, T);
+  out[1] = species_conductivity(m, k, T);
+}
+
+double orc_binary_diffusivity(void* h, int k, int j, double T) {
+  return binary_diffusivity(*(OMech*)h, k, j, T);
+}
+
+// Phi [N*N] (row k, column j) at T
+void orc_wilke_phi(void* h, double T, double* Phi) {
+  const OMech& m = *(OMech*)h;
+  int N = m.N();
+  for (int k = 0; k < N; ++k)
+    for (int j = 0; j < N; ++j)
+      Phi[k * N + j] = wilke_phi(m, k, j, species_viscosity(m, k, T), species_viscosity(m, j, T));
+}
+
+// mu [n], kappa [n], Dm [N][n] (each nullable)
+void orc_transport(void* h, int64_t n, const double* T, const double* Y, double* mu, double* kappa, double* Dm) {
+  const OMech& m = *(OMech*)h;
+  const int N = m.N();
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N), d(N);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    if (mu) mu[i] = mixture_viscosity(m, T[i], y.data());
+    if (kappa) kappa[i] = mixture_conductivity(m, T[i], y.data());
+    if (Dm) {
+      mixture_diffusivities(m, T[i], y.data(), d.data());
+      for (int k = 0; k < N; ++k) Dm[k * n + i] = d[k];
+    }
+  }
+}
+
+// the same in long double (rounding envelope of the double oracle)
+void orc_transport_ld(void* h, int64_t n, const double* T, const double* Y, double* mu, double* kappa, double* Dm) {
+  const OMech& m = *(OMech*)h;
+  const int N = m.N();
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<long double> y(N), d(N);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    long double t = T[i];
+    mu[i] = (double)mixture_viscosity<long double>(m, t, y.data());
+    kappa[i] = (double)mixture_conductivity<long double>(m, t, y.data());
+    mixture_diffusivities<long double>(m, t, y.data(), d.data());
+    for (int k = 0; k < N; ++k) Dm[k * n + i] = (double)d[k];
+  }
+}
 
 // One Crank-Nicolson step per point; returns the number of points that failed.
 int64_t orc_cn_step(void* h, int64_t n, double dt, const double* rho, const double* Tm, const double* Ym,

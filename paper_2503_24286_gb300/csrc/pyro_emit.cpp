@@ -804,19 +804,25 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
          "    const double rho = g_rho[p], T = g_T[p];\n";
   } else {
     s << "\n// Crank-Nicolson Newton system at the current iterate Y (state arrays [N][n], n = stride;\n"
-         "// cnt states).  state: 0 first iteration (forms c from S^m = S(Y^m)), 1 iterating,\n"
-         "// 2 converged (one more step pending), 3 done, 4 failed; states >= 3 are skipped.\n";
+         "// cnt states) for the *g_count active states listed in g_list; the system of the i-th\n"
+         "// listed state goes to slot i.  state: 0 first iteration (forms c from S^m = S(Y^m)),\n"
+         "// 1 iterating, 2 converged (one more step pending), 3 done, 4 failed.  Clears the\n"
+         "// counter of the list the following solve builds.\n";
     s << "extern \"C\" __global__ void __launch_bounds__(" << blk << ") pyro_cn_assemble(i64 cnt, i64 n,\n"
          "    const double* __restrict__ g_rho, const double* __restrict__ g_e, const double* __restrict__ g_Y,\n"
          "    double* __restrict__ g_c, double* __restrict__ g_T, int* __restrict__ g_state, double dt,\n"
          "    int max_iter, double tol, double* __restrict__ g_A, double* __restrict__ g_b,\n"
-         "    double* __restrict__ g_scratch, unsigned long long* __restrict__ g_fail) {\n" << prologue <<
+         "    double* __restrict__ g_scratch, unsigned long long* __restrict__ g_fail,\n"
+         "    const int* __restrict__ g_list, const int* __restrict__ g_count, int* __restrict__ g_count_next) {\n" << prologue <<
          "  double* W = g_scratch + (i64)blockIdx.x * " << sl.n << " * BLKD + t;\n"
          "  const float tolf = (float)tol;\n"
-         "  for (i64 p = (i64)blockIdx.x * BLKD + t; p < cnt; p += (i64)gridDim.x * BLKD) {\n"
-         "    const int stp = g_state[p];\n    if (stp >= 3) continue;\n"
+         "  const i64 na = *g_count;\n"
+         "  if (blockIdx.x == 0 && t == 0) *g_count_next = 0;\n"
+         "  for (i64 q = (i64)blockIdx.x * BLKD + t; q < na; q += (i64)gridDim.x * BLKD) {\n"
+         "    const i64 p = g_list[q];\n"
+         "    const int stp = g_state[p];\n"
          "    const double* Yp = g_Y + p;\n"
-         "    double* Jp = g_A + (p / CN_G) * (i64)(NSP * NSP * CN_G) + (p % CN_G);\n"
+         "    double* Jp = g_A + (q / CN_G) * (i64)(NSP * NSP * CN_G) + (q % CN_G);\n"
          "    const double rho = g_rho[p];\n"
          "    int tit;\n"
          "    const double T = pyro_tsolve<false>(Yp, n, g_e[p], g_T[p], max_iter, tolf, &tit);\n"
@@ -938,7 +944,7 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
              "        const double sk = (hh * " << lit(m.species[k].W) << ") * w;\n"
              "        double ck;\n"
              "        if (stp == 0) { ck = y + sk; g_c[(i64)" << k << " * cnt + p] = ck; } else { ck = g_c[(i64)" << k << " * cnt + p]; }\n"
-             "        g_b[(i64)" << k << " * cnt + p] = (ck + sk) - y; }\n";
+             "        g_b[(i64)" << k << " * cnt + q] = (ck + sk) - y; }\n";
       }
       s << "    }\n";
     }
@@ -1037,7 +1043,8 @@ void emit_cn_kernels(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
   // preparation: e = e(T^m, Y^m) (Eq. int_energy), iterate Y <- Y^m, T <- T^m
   s << "\nextern \"C\" __global__ void __launch_bounds__(BLKD) pyro_cn_prep(i64 cnt, i64 n,\n"
        "    const double* __restrict__ g_Tin, const double* __restrict__ g_Yin, double* __restrict__ g_Tout,\n"
-       "    double* __restrict__ g_Yout, double* __restrict__ g_e, int* __restrict__ g_state, int* __restrict__ g_it) {\n"
+       "    double* __restrict__ g_Yout, double* __restrict__ g_e, int* __restrict__ g_state, int* __restrict__ g_it,\n"
+       "    int* __restrict__ g_list, int* __restrict__ g_count) {\n"
        "  for (i64 p = (i64)blockIdx.x * BLKD + threadIdx.x; p < cnt; p += (i64)gridDim.x * BLKD) {\n"
        "    const double* Yp = g_Yin + p;\n    const double T = g_Tin[p];\n"
        "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n"
@@ -1053,49 +1060,92 @@ void emit_cn_kernels(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
   s << "    g_e[p] = " << lit((double)R_GAS) << " * fma(T, fma(T, fma(T, fma(T, fma(T, B5, B4), B3), B2), B1), B0);\n"
        "    if (g_Yout != g_Yin) {\n"
        "      #pragma unroll 1\n      for (int k = 0; k < NSP; ++k) g_Yout[(i64)k * n + p] = Yp[(i64)k * n];\n    }\n"
-       "    g_Tout[p] = T;\n    g_state[p] = 0;\n    g_it[p] = 0;\n  }\n}\n";
+       "    g_Tout[p] = T;\n    g_state[p] = 0;\n    g_it[p] = 0;\n    g_list[p] = (int)p;\n  }\n"
+       "  if (blockIdx.x == 0 && threadIdx.x == 0) *g_count = (int)cnt;\n}\n";
 
   // batched solve: one warp per state
   s << R"(
 // Newton update of one Crank-Nicolson iteration, one warp per state: solve
-// (I - dt/(2 rho) J) dY = -F by LU with partial pivoting in FP32 (rows scaled by
-// powers of two so that every entry is at most 1 in magnitude) and `refine`
+// (I - dt/(2 rho) J) dY = -F by LU with partial pivoting in FP32 and `refine`
 // steps of iterative refinement whose residuals b - A x are formed in FP64 from
-// the FP64 matrix; then Y += dY and the state's Newton bookkeeping: stop once
-// max_k |dY_k| <= tol, after one further step (the rule of the temperature solve).
-#define CN_LDA (NSP | 1)
+// the FP64 matrix; then Y += dY and the state's Newton bookkeeping (stop once
+// max_k |dY_k| <= tol, after one further step: the rule of the temperature solve).
+// Each row is scaled by a power of two that brings its largest entry into
+// [0.5, 1) before it is rounded to FP32; row maxima, scaling and rounding (to
+// nearest even) work on the bit patterns in integer arithmetic.  The trailing
+// update of the factorisation spreads the submatrix over the lanes as a 16 x 2
+// tile (rows l/2 mod 16, columns l mod 2), so with the leading dimension
+// CN_LDA = 2 * odd the tile's shared-memory accesses are conflict-free.
+#define CN_NJ ((NSP + 31) / 32)
+#define CN_LDA (((NSP + 1) / 2) % 2 == 1 ? 2 * ((NSP + 1) / 2) : 2 * ((NSP + 1) / 2) + 2)
+
+// |v| 2^-e rounded to FP32 (round to nearest even), with v's bits; 0 below FP32's normal range
+__device__ __forceinline__ float pyro_scaled_f32(long long bits, int e) {
+  const unsigned long long a = (unsigned long long)bits & 0x7fffffffffffffffull;
+  const int ex = (int)(a >> 52);
+  if (ex == 2047) return __int_as_float(0x7fc00000);   // Inf or NaN: NaN (the pivot search rejects it)
+  int fe = ex - 1023 - e + 127;
+  if (ex == 0 || fe <= 0) return 0.0f;
+  unsigned long long mant = a & 0xfffffffffffffull;
+  unsigned int m23 = (unsigned int)(mant >> 29);
+  const unsigned int rem = (unsigned int)(mant & 0x1fffffffu);
+  if (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) {
+    ++m23;
+    if (m23 == 0x800000u) { m23 = 0; ++fe; }
+  }
+  const unsigned int fb = ((unsigned int)(bits >> 32) & 0x80000000u) | ((unsigned int)min(fe, 255) << 23) |
+                          (fe >= 255 ? 0u : m23);
+  return __uint_as_float(fb);
+}
+
 extern "C" __global__ void __launch_bounds__(CN_G * 32) pyro_cn_solve(i64 cnt, i64 n,
     const double* __restrict__ g_A, const double* __restrict__ g_b, double* __restrict__ g_Y,
     int* __restrict__ g_state, int* __restrict__ g_it, double tol, int max_newton, int refine,
-    unsigned long long* __restrict__ g_fail) {
+    unsigned long long* __restrict__ g_fail, const int* __restrict__ g_list, const int* __restrict__ g_count,
+    int* __restrict__ g_list_next, int* __restrict__ g_count_next) {
   extern __shared__ double s_cn[];
   const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
-  double* sd = s_cn + wi * NSP;                       // row scales (powers of two)
-  double* sx = s_cn + (CN_G + wi) * NSP;              // solution (FP64)
-  double* sr = s_cn + (2 * CN_G + wi) * NSP;          // right-hand side / residual (FP64)
-  float* fb = (float*)(s_cn + 3 * CN_G * NSP);
+  double* sx = s_cn + wi * NSP;                       // solution (FP64)
+  double* sr = s_cn + (CN_G + wi) * NSP;              // right-hand side / residual (FP64)
+  float* fb = (float*)(s_cn + 2 * CN_G * NSP);
   float* sM = fb + wi * (NSP * CN_LDA);                                // scaled LU factors
   float* sv = fb + CN_G * NSP * CN_LDA + wi * NSP;                      // FP32 solve vector
   float* sq = fb + CN_G * NSP * CN_LDA + CN_G * NSP + wi * NSP;         // reciprocal pivots
   int* spiv = (int*)(fb + CN_G * NSP * CN_LDA + 2 * CN_G * NSP) + wi * NSP;   // pivot rows
-  for (i64 p = ((i64)blockIdx.x * CN_G + wi); p < cnt; p += (i64)gridDim.x * CN_G) {
+  int* se = spiv + CN_G * NSP;                                          // row scale exponents
+  const int tr = l >> 1, tc = l & 1;                  // lane's place in the 16 x 2 update tile
+  const i64 na = *g_count;
+  for (i64 q = ((i64)blockIdx.x * CN_G + wi); q < na; q += (i64)gridDim.x * CN_G) {
+    const i64 p = g_list[q];
     const int st = g_state[p];
     if (st >= 3) continue;
-    const double* Ag = g_A + (p / CN_G) * (i64)(NSP * NSP * CN_G) + (p % CN_G);
-    // row scales: 2^-e with 2^(e-1) <= max_j |A_ij| < 2^e
+    const double* Ag = g_A + (q / CN_G) * (i64)(NSP * NSP * CN_G) + (q % CN_G);
+    // scaled FP32 copy of the matrix, one row at a time
+    #pragma unroll 2
     for (int i = 0; i < NSP; ++i) {
-      double mx = 0.0;
-      for (int j = l; j < NSP; j += 32) mx = fmax(mx, fabs(__ldg(Ag + (i64)(i * NSP + j) * CN_G)));
-      for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
-      if (l == 0) { int e; frexp(mx, &e); sd[i] = mx > 0.0 ? ldexp(1.0, -e) : 1.0; }
+      long long v[CN_NJ];
+      unsigned long long mx = 0;
+      #pragma unroll
+      for (int t = 0; t < CN_NJ; ++t) {
+        const int j = l + 32 * t;
+        v[t] = j < NSP ? __double_as_longlong(__ldg(Ag + (i64)(i * NSP + j) * CN_G)) : 0ll;
+        const unsigned long long a = (unsigned long long)v[t] & 0x7fffffffffffffffull;
+        mx = a > mx ? a : mx;
+      }
+      for (int o = 16; o; o >>= 1) {
+        const unsigned long long om = __shfl_xor_sync(FULL, mx, o);
+        mx = om > mx ? om : mx;
+      }
+      const int e = mx ? (int)(mx >> 52) - 1022 : 0;   // 2^(e-1) <= max |A_ij| < 2^e
+      #pragma unroll
+      for (int t = 0; t < CN_NJ; ++t) {
+        const int j = l + 32 * t;
+        if (j < NSP) sM[i * CN_LDA + j] = pyro_scaled_f32(v[t], e);
+      }
+      if (l == 0) se[i] = e;
     }
-    __syncwarp();
-    for (int i = 0; i < NSP; ++i) {
-      const double di = sd[i];
-      for (int j = l; j < NSP; j += 32) sM[i * CN_LDA + j] = (float)(__ldg(Ag + (i64)(i * NSP + j) * CN_G) * di);
-    }
-    for (int k = l; k < NSP; k += 32) { sr[k] = g_b[(i64)k * cnt + p]; sx[k] = 0.0; }
+    for (int k = l; k < NSP; k += 32) { sr[k] = g_b[(i64)k * cnt + q]; sx[k] = 0.0; }
     __syncwarp();
     // LU factorisation with partial pivoting (row exchanges applied to the whole rows)
     bool sing = false;
@@ -1124,30 +1174,50 @@ extern "C" __global__ void __launch_bounds__(CN_G * 32) pyro_cn_solve(i64 cnt, i
       if (l == 0) sq[k] = inv;
       for (int i = k + 1 + l; i < NSP; i += 32) sM[i * CN_LDA + k] *= inv;
       __syncwarp();
-      for (int j = k + 1 + l; j < NSP; j += 32) {
-        const float u = sM[k * CN_LDA + j];
-        for (int i = k + 1; i < NSP; ++i) sM[i * CN_LDA + j] = fmaf(-sM[i * CN_LDA + k], u, sM[i * CN_LDA + j]);
+      // trailing update A[i][j] -= A[i][k] A[k][j], i, j > k, on the 16 x 2 tile
+      const int m = NSP - 1 - k;
+      float li[(NSP + 15) / 16];
+      #pragma unroll
+      for (int u = 0; u < (NSP + 15) / 16; ++u) {
+        const int i = k + 1 + tr + 16 * u;
+        li[u] = i < NSP ? sM[i * CN_LDA + k] : 0.0f;
+      }
+      for (int jj = tc; jj < m; jj += 2) {
+        const int j = k + 1 + jj;
+        const float uj = sM[k * CN_LDA + j];
+        #pragma unroll
+        for (int u = 0; u < (NSP + 15) / 16; ++u) {
+          if (16 * u < m) {                          // uniform across the warp
+            const int i = k + 1 + tr + 16 * u;
+            if (i < NSP) sM[i * CN_LDA + j] = fmaf(-li[u], uj, sM[i * CN_LDA + j]);
+          }
+        }
       }
       __syncwarp();
     }
     double dmax = 0.0;
     if (!sing) {
       for (int pass = 0; pass <= refine; ++pass) {
-        if (pass > 0) {   // residual r = b - A x in FP64
+        if (pass > 0) {   // residual r = b - A x in FP64, one row per lane
           for (int i = l; i < NSP; i += 32) {
-            double acc = g_b[(i64)i * cnt + p];
             const double* Ai = Ag + (i64)(i * NSP) * CN_G;
-            for (int j = 0; j < NSP; ++j) acc = fma(-__ldg(Ai + (i64)j * CN_G), sx[j], acc);
-            sr[i] = acc;
+            double acc0 = g_b[(i64)i * cnt + q], acc1 = 0.0;
+            int j = 0;
+            for (; j + 1 < NSP; j += 2) {
+              acc0 = fma(-__ldg(Ai + (i64)j * CN_G), sx[j], acc0);
+              acc1 = fma(-__ldg(Ai + (i64)(j + 1) * CN_G), sx[j + 1], acc1);
+            }
+            if (j < NSP) acc0 = fma(-__ldg(Ai + (i64)j * CN_G), sx[j], acc0);
+            sr[i] = acc0 + acc1;
           }
           __syncwarp();
         }
-        for (int k = l; k < NSP; k += 32) sv[k] = (float)(sr[k] * sd[k]);
+        for (int k = l; k < NSP; k += 32) sv[k] = __double2float_rn(ldexp(sr[k], -se[k]));   // row scaling
         __syncwarp();
         if (l == 0)
           for (int k = 0; k < NSP; ++k) {
-            const int q = spiv[k];
-            if (q != k) { const float a = sv[k]; sv[k] = sv[q]; sv[q] = a; }
+            const int pk = spiv[k];
+            if (pk != k) { const float a = sv[k]; sv[k] = sv[pk]; sv[pk] = a; }
           }
         __syncwarp();
         for (int k = 0; k < NSP - 1; ++k) {        // unit lower triangle
@@ -1187,6 +1257,7 @@ extern "C" __global__ void __launch_bounds__(CN_G * 32) pyro_cn_solve(i64 cnt, i
       else ns = 1;
       g_state[p] = ns;
       if (ns == 4) atomicAdd(g_fail, 1ull);
+      if (ns < 3) g_list_next[atomicAdd(g_count_next, 1)] = (int)p;
     }
     __syncwarp();
   }
@@ -1570,8 +1641,8 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, cons
     emit_jacobian_kernel(d, m, C, opt.deriv_block, &ns2, JacMode::CN);
     emit_cn_kernels(d, m, C);
     out.group_sources["cn"] = d.o.str();
-    const int lda = N | 1;
-    out.smem_dyn_bytes_cn_solve = kCnGroup * (3 * N * 8 + N * lda * 4 + 3 * N * 4);
+    const int half = (N + 1) / 2, lda = half % 2 == 1 ? 2 * half : 2 * half + 2;   // CN_LDA
+    out.smem_dyn_bytes_cn_solve = kCnGroup * (2 * N * 8 + N * lda * 4 + 4 * N * 4);
   }
   out.smem_dyn_bytes_deriv = opt.dgstore ? 0 : 4 * N * opt.deriv_block * (int)sizeof(double);
   out.stats["jacobian_scratch_doubles_per_point"] = nslots;

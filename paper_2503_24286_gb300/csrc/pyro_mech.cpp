@@ -164,6 +164,46 @@ bool parse_mechanism_file(const std::string& path, Mechanism& m, std::string& er
     if (!has_arr) return fail("reaction without 'arr'");
     if (r.reactants.empty() || r.products.empty()) return fail("reaction without reactants or products");
   }
+  // optional transport section
+  if (li < L.size()) {
+    int nt = 0;
+    if (!expect("transport", nt) || nt != ns) return fail("expected 'transport <n_species>' or end of file");
+    TransportFits& tf = m.transport;
+    tf.visc.assign((size_t)ns * 5, 0.0);
+    tf.cond.assign((size_t)ns * 5, 0.0);
+    tf.diff.assign((size_t)ns * ns * 5, 0.0);
+    std::vector<bool> sp(ns, false);
+    for (int q = 0; q < ns; ++q, ++li) {
+      if (li >= L.size()) return fail("missing tspecies line");
+      std::string key; int k;
+      if (!L[li].word(key) || key != "tspecies" || !L[li].integer(k) || k < 0 || k >= ns || sp[k])
+        return fail("bad tspecies line");
+      sp[k] = true;
+      bool ok = true;
+      for (int i = 0; i < 5 && ok; ++i) ok = L[li].real(tf.visc[(size_t)k * 5 + i]);
+      for (int i = 0; i < 5 && ok; ++i) ok = L[li].real(tf.cond[(size_t)k * 5 + i]);
+      if (!ok || !L[li].done()) return fail("bad tspecies coefficients");
+    }
+    std::vector<bool> pr((size_t)ns * ns, false);
+    const long long npairs = (long long)ns * (ns - 1) / 2;
+    for (long long q = 0; q < npairs; ++q, ++li) {
+      if (li >= L.size()) return fail("missing tbinary line");
+      std::string key; int k, j;
+      if (!L[li].word(key) || key != "tbinary" || !L[li].integer(k) || !L[li].integer(j) || k < 0 || j <= k ||
+          j >= ns || pr[(size_t)k * ns + j])
+        return fail("bad tbinary line");
+      pr[(size_t)k * ns + j] = true;
+      bool ok = true;
+      for (int i = 0; i < 5 && ok; ++i) {
+        double a;
+        ok = L[li].real(a);
+        tf.diff[((size_t)k * ns + j) * 5 + i] = tf.diff[((size_t)j * ns + k) * 5 + i] = a;
+      }
+      if (!ok || !L[li].done()) return fail("bad tbinary coefficients");
+    }
+    if (li < L.size()) return fail("unexpected content after the transport section");
+    m.has_transport = true;
+  }
   return true;
 }
 

@@ -37,12 +37,22 @@ struct Reaction {
   double troe[4] = {0, 0, 0, 0};
 };
 
+// Mixture-averaged transport data (Sec. A.2): per-species fits of viscosity
+// mu_k = sqrt(T) (sum_m b_km ln^m T)^2 and conductivity kappa_k = sqrt(T) sum_m c_km ln^m T,
+// and symmetric binary-diffusivity fits D_kj = sqrt(T) sum_m a_kjm ln^m T, m = 0..4.
+struct TransportFits {
+  std::vector<double> visc, cond;   // [N][5]
+  std::vector<double> diff;         // [N][N][5], symmetric, diagonal unused
+};
+
 struct Mechanism {
   std::string name;
   std::vector<std::string> element_names;
   std::vector<double> element_weights;
   std::vector<Species> species;
   std::vector<Reaction> reactions;
+  bool has_transport = false;
+  TransportFits transport;
   int n_species() const { return (int)species.size(); }
   int n_reactions() const { return (int)reactions.size(); }
 };

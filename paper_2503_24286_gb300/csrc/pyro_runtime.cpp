@@ -929,12 +929,14 @@ int pyro_jacobian_adiabatic(const pyro_mech* hc, int64_t n, const double* rho, c
 
 namespace {
 // States per chunk of the Crank-Nicolson work arrays (Newton matrix N^2 doubles
-// per state): about 2 GiB, a multiple of the matrix group size.
+// per state): at most 8 GiB, a multiple of the matrix group size.  Chunks run one
+// after another and each ends in a tail of slowly converging states that keeps
+// only a few warps busy, so fewer, larger chunks are faster.
 int64_t cn_chunk(const pyro_mech* h, int64_t n) {
   const int64_t N = h->m.n_species();
   const int64_t Gs = pyro::kCnGroup;
-  const size_t per_state = (size_t)(N * N + 2 * N + 2) * sizeof(double);
-  int64_t m = std::max<int64_t>(4096, (int64_t)(((size_t)2 << 30) / per_state));
+  const size_t per_state = (size_t)(N * N + 2 * N + 3) * sizeof(double);
+  int64_t m = std::max<int64_t>(4096, (int64_t)(((size_t)8 << 30) / per_state));
   m = std::min<int64_t>(m, (n + Gs - 1) / Gs * Gs);
   return (m + Gs - 1) / Gs * Gs;
 }
@@ -946,7 +948,7 @@ int cn_reserve(pyro_mech* h, int64_t n) {
   const int64_t m = cn_chunk(h, n);
   if (int rc = ensure_jac_scratch(h, h->groups["cn"], m)) return rc;
   std::lock_guard<std::mutex> lock(h->mu);
-  const size_t bytes = (size_t)m * (size_t)(N * N + 2 * N + 2) * sizeof(double);
+  const size_t bytes = (size_t)m * (size_t)(N * N + 2 * N + 3) * sizeof(double) + 4 * sizeof(int);
   if (bytes > h->cn_bytes) {
     if (h->d_cn) cudaFree(h->d_cn);
     h->d_cn = nullptr;
@@ -974,6 +976,8 @@ int cn_run(pyro_mech* h, int64_t cnt, int64_t ld, double dt, const double* rho, 
   double* de = db + (size_t)m * N;               // [m]
   int* dstate = (int*)(de + m);                  // [m]
   int* dit = dstate + m;                         // [m]
+  int* dlist[2] = {dit + m, dit + 2 * m};        // active-state lists [m], built alternately
+  int* dcount[2] = {dit + 3 * m, dit + 3 * m + 1};
   Driver& d = driver();
   const int bd = h->opt.deriv_block;
   double Tg_tol = 1e-10;
@@ -987,15 +991,20 @@ int cn_run(pyro_mech* h, int64_t cnt, int64_t ld, double dt, const double* rho, 
     double* Yout_c = Yout + p0;
     int32_t* it_c = iters ? iters + p0 : nullptr;
     unsigned gs = (unsigned)std::min<int64_t>((nc + bd - 1) / bd, (int64_t)h->num_sms * 8);
-    void* pp[] = {&nc, &nld, &Tin_c, &Yin_c, &Tout_c, &Yout_c, &de, &dstate, &dit};
+    void* pp[] = {&nc, &nld, &Tin_c, &Yin_c, &Tout_c, &Yout_c, &de, &dstate, &dit, &dlist[0], &dcount[0]};
     CUresult r = d.LaunchKernel(G.fn.at("pyro_cn_prep"), gs, 1, 1, bd, 1, 1, 0, as_stream(stream), pp, nullptr);
     if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
     unsigned gsolve = (unsigned)std::min<int64_t>((nc + Gs - 1) / Gs, (int64_t)h->num_sms * G.solve_blocks_per_sm);
     for (int it = 0; it <= max_newton; ++it) {
+      int* li = dlist[it & 1];
+      int* lo = dlist[(it + 1) & 1];
+      int* ci = dcount[it & 1];
+      int* co = dcount[(it + 1) & 1];
       void* pa[] = {&nc, &nld, &rho_c, &de, &Yout_c, &dc, &Tout_c, &dstate, &dt, &t_iter, &Tg_tol, &dA, &db,
-                    &h->d_jac_scratch, &h->d_fail};
+                    &h->d_jac_scratch, &h->d_fail, &li, &ci, &co};
       if (int rc = launch_deriv(h, G, nc, stream, pa)) return rc;
-      void* ps[] = {&nc, &nld, &dA, &db, &Yout_c, &dstate, &dit, &tol, &max_newton, &refine, &h->d_fail};
+      void* ps[] = {&nc, &nld, &dA, &db, &Yout_c, &dstate, &dit, &tol, &max_newton, &refine, &h->d_fail,
+                    &li, &ci, &lo, &co};
       r = d.LaunchKernel(G.fn.at("pyro_cn_solve"), gsolve, 1, 1, 32 * pyro::kCnGroup, 1, 1,
                          h->emitted.smem_dyn_bytes_cn_solve, as_stream(stream), ps, nullptr);
       if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
@@ -1022,7 +1031,7 @@ int pyro_cn_step(const pyro_mech* hc, int64_t n, double dt, const double* rho, c
                              "arrays in shared memory (4 N deriv_block 8 B <= 160 KB)");
   if (int rc = ensure_groups(h, {"cn"})) return rc;
   const int64_t NS = h->m.n_species();
-  const int refine = 2;
+  const int refine = 1;
   if (int rc = cn_reserve(h, n)) return rc;
   int rc = with_args(h, n, {{rho, 1, 8, true, false}, {T, 1, 8, true, false}, {Y, NS, 8, true, false},
                             {T_out, 1, 8, false, true}, {Y_out, NS, 8, false, true}, {iters_out, 1, 4, false, true}},

@@ -18,7 +18,15 @@ synthetic workloads:
 * element-balanced reversible reactions with 1-3 species a side (coefficients
   1 or 2, order <= 3), optional third-body efficiencies U[0.5, 12] on up to 8
   species, Troe falloff, and duplicate pairs;
-* states: T ~ U, p ~ U (atm), Y ~ Dirichlet(0.5).
+* states: T ~ U, p ~ U (atm), Y ~ Dirichlet(0.5);
+* transport fits of the form the paper's mixture-averaged model takes (Sec. A.2):
+  species viscosity sqrt(T) (sum_m b_m ln^m T)^2, conductivity
+  sqrt(T) sum_m c_m ln^m T and binary diffusivity sqrt(T) sum_m a_m ln^m T,
+  m = 0..4, least-squares fitted on [250, 3600] K to Chapman-Enskog-type model
+  curves (Lennard-Jones parameters drawn per species, Neufeld-Janzen-Aziz
+  collision integrals, Eucken-type conductivity, diffusivity at 1 atm).  The
+  model curves are only the fitting targets; the library and the oracle
+  evaluate the fits and the mixture rules.
 
 The text format written by :func:`write_mechanism` is the interchange format
 of the library (``pyro_mech_load``) and the oracle; see ``MECH_FORMAT``.
@@ -64,6 +72,9 @@ reactions <M>
 reaction <kind> rev <0|1> dup <0|1> reac <n> <k> <nu> ... prod <n> <k> <nu> ...
          arr <A> <b> <theta>
          [eff <n> <k> <eps> ...] [low <A0> <b0> <theta0>] [troe <a> <T3> <T1> [<T2>]] end
+[transport <N>                                           (optional section)
+ tspecies <k> <b0..b4> <c0..c4>                          (N lines: viscosity, conductivity)
+ tbinary <k> <j> <a0..a4>                                (k < j, N(N-1)/2 lines: diffusivity)]
 kind in {arrhenius, threebody, falloff}; theta = Ea/R in K; SI kmol units.
 All reals are written with 17 significant digits (exact round trip).
 """
@@ -98,11 +109,20 @@ class Reaction:
 
 
 @dataclass
+class Transport:
+    """Polynomial transport fits (Sec. A.2), coefficients of ln^m T, m = 0..4."""
+    visc: np.ndarray       # [N, 5]: mu_k = sqrt(T) (sum_m b_km ln^m T)^2        [Pa s]
+    cond: np.ndarray       # [N, 5]: kappa_k = sqrt(T) sum_m c_km ln^m T          [W/(m K)]
+    diff: np.ndarray       # [N, N, 5] symmetric: D_kj = sqrt(T) sum_m a_kjm ln^m T  [m^2/s]
+
+
+@dataclass
 class Mechanism:
     name: str
     elements: List[Tuple[str, float]]
     species: List[Species]
     reactions: List[Reaction]
+    transport: Optional[Transport] = None
 
     @property
     def n_species(self) -> int:
@@ -149,15 +169,21 @@ MECH_SEED_BASE = 2503
 STATE_SEED_BASE = 24286
 
 
+TRANSPORT_SEED_OFFSET = 1000
+
+
 def config_mechanism(index: int) -> Mechanism:
-    """The synthetic mechanism of workload ``index`` (seed 2503 + mechanism index)."""
+    """The synthetic mechanism of workload ``index`` (seed 2503 + mechanism index),
+    with transport fits drawn from a separate stream (seed 3503 + mechanism index)."""
     cfg = CONFIGS[index]
     m = CONFIGS[cfg["mech"]]
-    return generate_mechanism(
+    mech = generate_mechanism(
         name=m["name"], elements=m["elements"], n_species=m["n_species"],
         n_reactions=m["n_reactions"], n_threebody=m["n_threebody"],
         n_falloff=m["n_falloff"], n_dup_pairs=m["n_dup_pairs"], inert=m["inert"],
         seed=MECH_SEED_BASE + cfg["mech"])
+    mech.transport = generate_transport(mech, MECH_SEED_BASE + TRANSPORT_SEED_OFFSET + cfg["mech"])
+    return mech
 
 
 # ----------------------------------------------------------------------------
@@ -469,6 +495,92 @@ def generate_mechanism(name: str, elements: List[str], n_species: int, n_reactio
 
 
 # ----------------------------------------------------------------------------
+# Transport fits
+# ----------------------------------------------------------------------------
+
+R_UNIV = 8314.462618          # J/(kmol K), for the Eucken-type model only
+TR_FIT_T = (250.0, 3600.0)
+
+
+def _omega22(ts: np.ndarray) -> np.ndarray:
+    """Reduced collision integral Omega(2,2)* of the Lennard-Jones potential
+    (Neufeld, Janzen and Aziz, J. Chem. Phys. 57, 1100 (1972))."""
+    return 1.16145 * ts ** -0.14874 + 0.52487 * np.exp(-0.77320 * ts) + 2.16178 * np.exp(-2.43787 * ts)
+
+
+def _omega11(ts: np.ndarray) -> np.ndarray:
+    """Reduced collision integral Omega(1,1)* (same reference)."""
+    return (1.06036 * ts ** -0.15610 + 0.19300 * np.exp(-0.47635 * ts) + 1.03587 * np.exp(-1.52996 * ts)
+            + 1.76474 * np.exp(-3.89411 * ts))
+
+
+@dataclass
+class TransportModel:
+    """Per-species model parameters the fits are drawn from (not in the file)."""
+    W: np.ndarray          # kg/kmol
+    sigma: np.ndarray      # Lennard-Jones diameter [Angstrom]
+    eps: np.ndarray        # well depth / k_B [K]
+    cint: np.ndarray       # internal-mode weight of the conductivity model
+    theta: np.ndarray      # internal-mode temperature of the conductivity model [K]
+
+    def viscosity(self, T: np.ndarray) -> np.ndarray:
+        """[N, nT] Chapman-Enskog viscosity [Pa s]."""
+        T = np.asarray(T, dtype=float)
+        ts = T[None, :] / self.eps[:, None]
+        return 2.6693e-6 * np.sqrt(self.W[:, None] * T[None, :]) / (self.sigma[:, None] ** 2 * _omega22(ts))
+
+    def conductivity(self, T: np.ndarray) -> np.ndarray:
+        """[N, nT] Eucken-type conductivity [W/(m K)]: (mu/W) R (15/4 + internal part)."""
+        T = np.asarray(T, dtype=float)
+        f = 3.75 + self.cint[:, None] * (1.0 - np.exp(-T[None, :] / self.theta[:, None]))
+        return self.viscosity(T) / self.W[:, None] * R_UNIV * f
+
+    def diffusivity(self, T: np.ndarray) -> np.ndarray:
+        """[N, N, nT] Chapman-Enskog binary diffusivity at 1 atm [m^2/s]."""
+        T = np.asarray(T, dtype=float)
+        sig = 0.5 * (self.sigma[:, None] + self.sigma[None, :])
+        eps = np.sqrt(self.eps[:, None] * self.eps[None, :])
+        wr = 1.0 / self.W[:, None] + 1.0 / self.W[None, :]
+        ts = T[None, None, :] / eps[:, :, None]
+        return 1.8583e-7 * np.sqrt(T[None, None, :] ** 3 * wr[:, :, None]) / (sig[:, :, None] ** 2 * _omega11(ts))
+
+
+def transport_model(mech: Mechanism, seed: int) -> TransportModel:
+    """Seeded Lennard-Jones and conductivity-model parameters of every species."""
+    rng = np.random.default_rng(seed)
+    ew = dict(mech.elements)
+    W = np.array([sum(c * ew[e] for e, c in s.composition.items()) for s in mech.species])
+    atoms = np.array([sum(s.composition.values()) for s in mech.species], dtype=float)
+    sigma = 2.6 + 0.45 * np.sqrt(atoms) + rng.uniform(-0.2, 0.2, size=atoms.size)
+    eps = (90.0 + 55.0 * atoms ** 0.7) * rng.uniform(0.7, 1.3, size=atoms.size)
+    cint = np.where(atoms > 1, rng.uniform(0.5, 4.0, size=atoms.size), 0.0)
+    theta = rng.uniform(300.0, 2000.0, size=atoms.size)
+    return TransportModel(W, sigma, eps, cint, theta)
+
+
+def _fit_lnT(T: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Least-squares coefficients of sum_m c_m ln^m T (m = 0..4), rows of y fitted independently."""
+    V = np.vander(np.log(T), 5, increasing=True)
+    c, *_ = np.linalg.lstsq(V, y.T, rcond=None)
+    return np.ascontiguousarray(c.T)
+
+
+def generate_transport(mech: Mechanism, seed: int) -> Transport:
+    """Transport fits of every species and species pair (Sec. A.2 forms)."""
+    mdl = transport_model(mech, seed)
+    T = np.exp(np.linspace(math.log(TR_FIT_T[0]), math.log(TR_FIT_T[1]), 48))
+    sq = np.sqrt(T)[None, :]
+    visc = _fit_lnT(T, np.sqrt(mdl.viscosity(T) / sq))
+    cond = _fit_lnT(T, mdl.conductivity(T) / sq)
+    N = mech.n_species
+    D = mdl.diffusivity(T) / sq[None]
+    diff = _fit_lnT(T, D.reshape(N * N, -1)).reshape(N, N, 5)
+    diff = 0.5 * (diff + diff.transpose(1, 0, 2))          # exactly symmetric
+    diff[np.arange(N), np.arange(N)] = 0.0                  # self-diffusion is not used (j != k)
+    return Transport(visc, cond, diff)
+
+
+# ----------------------------------------------------------------------------
 # File format
 # ----------------------------------------------------------------------------
 
@@ -510,6 +622,15 @@ def write_mechanism(mech: Mechanism, path: str) -> None:
             parts += ["troe"] + [_f(x) for x in r.troe]
         parts.append("end")
         lines.append(" ".join(parts))
+    tr = mech.transport
+    if tr is not None:
+        lines.append("transport %d" % mech.n_species)
+        for k in range(mech.n_species):
+            lines.append("tspecies %d %s %s" % (k, " ".join(_f(x) for x in tr.visc[k]),
+                                                " ".join(_f(x) for x in tr.cond[k])))
+        for k in range(mech.n_species):
+            for j in range(k + 1, mech.n_species):
+                lines.append("tbinary %d %d %s" % (k, j, " ".join(_f(x) for x in tr.diff[k, j])))
     with open(path, "w") as f:
         f.write("\n".join(lines) + "\n")
 
@@ -579,7 +700,22 @@ def read_mechanism(path: str) -> Mechanism:
             else:
                 raise ValueError("unknown reaction key " + key)
         reactions.append(Reaction(kind, reac, prod, A, b, th, rev, dup, eff, low, troe))
-    return Mechanism(name, elements, species, reactions)
+    transport = None
+    t = next(it, None)
+    if t is not None and t[0] == "transport":
+        visc, cond = np.zeros((ns, 5)), np.zeros((ns, 5))
+        diff = np.zeros((ns, ns, 5))
+        for _ in range(ns):
+            t = next(it)
+            k = int(t[1])
+            visc[k] = [float(x) for x in t[2:7]]
+            cond[k] = [float(x) for x in t[7:12]]
+        for _ in range(ns * (ns - 1) // 2):
+            t = next(it)
+            k, j = int(t[1]), int(t[2])
+            diff[k, j] = diff[j, k] = [float(x) for x in t[3:8]]
+        transport = Transport(visc, cond, diff)
+    return Mechanism(name, elements, species, reactions, transport)
 
 
 # ----------------------------------------------------------------------------
