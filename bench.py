@@ -368,6 +368,41 @@ def crank_nicolson_rates(synth, dev, stream, args, rank):
     return res
 
 
+def transport_rates(mech, synth, dev, stream, args, rank):
+    """Mixture-averaged mu, kappa and D_km (Sec. A.2) on 2^20 resident states of the
+    53-species mechanism (T ~ U[300, 2800] K, Dirichlet Y)."""
+    import torch
+    mech.prepare("transport")
+    n = args.transport_points
+    cfg = synth.CONFIGS[1]
+    T, p, Y = synth.generate_states_torch(53, n, cfg["T"], cfg["p_atm"], synth.STATE_SEED_BASE + 1 + 17 + 7919 * rank, dev)
+    del p
+    mu = torch.empty(n, dtype=torch.float64, device=dev)
+    ka = torch.empty(n, dtype=torch.float64, device=dev)
+    Dm = torch.empty((53, n), dtype=torch.float64, device=dev)
+    from paper_2503_24286_gb300 import binding as B
+
+    def call():
+        B._check(B.lib().pyro_transport(mech.handle, n, *[B._ptr(a)[0] for a in (T, Y, mu, ka, Dm)],
+                                        B._stream([T])))
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize(dev)
+    steps = max(2, min(args.steps, 5))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, dev)
+    ops = mech.stat("transport_fp64_ops_per_point")
+    return {"workload": "53 species, %d states, T ~ U[300, 2800] K, Dirichlet Y; mu (Wilke), kappa, D_km" % n,
+            "ms": ms, "states_per_s": n / (ms * 1e-3),
+            "fp64_ops_per_state_static": ops,
+            "fp64_pipe_frac": ops * n / (ms * 1e-3) / (FP64_PEAK_GFLOPS * 1e9 / 2)}
+
+
 def run_ours(args):
     import torch
     from paper_2503_24286_gb300 import binding as B
@@ -466,6 +501,9 @@ def run_ours(args):
         warp53 = {"ms": ms_w, "states_per_s": n / (ms_w * 1e-3)}
         large = large_mechanism_rates(synth, dev, stream, args, rank)
 
+    transport = None
+    if not args.no_transport:
+        transport = transport_rates(mech, synth, dev, stream, args, rank)
     cn = None
     if not args.no_cn:
         cn = crank_nicolson_rates(synth, dev, stream, args, rank)
@@ -506,6 +544,7 @@ def run_ours(args):
                 "warp_per_state_53sp": warp53,
                 "large_mechanism": large,
                 "crank_nicolson": cn,
+                "transport": transport,
                 "kernel_source_hash": src_hash,
                 "kernel": "pyro_omega (fused Newton T(e,Y) + omega), %d threads/block, %d blocks/SM"
                           % (int(mech.stat("block")), int(mech.stat("omega_blocks_per_sm")))}
@@ -530,6 +569,8 @@ def main():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--cn-points", type=int, default=2 ** 18)
     ap.add_argument("--no-cn", action="store_true")
+    ap.add_argument("--transport-points", type=int, default=2 ** 20)
+    ap.add_argument("--no-transport", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -142,7 +142,7 @@ int pyro_net_production_rates(const pyro_mech* mech, int64_t n, const double* rh
 
 /* Compile and load derivative kernels ahead of their first use.  kernels:
  * NULL or "all" (jvp, vjp, jacobian), or a comma list of "jvp", "vjp",
- * "jacobian", "jacobian_adiabatic", "cn".  The groups are
+ * "jacobian", "jacobian_adiabatic", "cn", "transport".  The groups are
  * compiled in parallel host threads with NVRTC (cached on disk); without this
  * call each group is compiled on the first call that needs it. */
 int pyro_mech_prepare(const pyro_mech* mech, const char* kernels);
@@ -205,6 +205,22 @@ int pyro_jacobian_adiabatic(const pyro_mech* mech, int64_t n, const double* rho,
 int pyro_cn_step(const pyro_mech* mech, int64_t n, double dt, const double* rho, const double* T,
                  const double* Y, double tol, int max_newton, double* T_out, double* Y_out,
                  int32_t* iters_out, void* stream);
+
+/* Mixture-averaged transport properties (Sec. A.2) from the mechanism's transport
+ * section (PYRO_EMECH if it has none):
+ *   mu_k = sqrt(T) (sum_m b_km ln^m T)^2, kappa_k = sqrt(T) sum_m c_km ln^m T,
+ *   D_kj = sqrt(T) sum_m a_kjm ln^m T  (m = 0..4; fits as printed, no pressure factor);
+ *   mu = sum_k X_k mu_k / sum_j Phi_kj X_j with Wilke's
+ *     Phi_kj = [1 + sqrt((mu_k/mu_j) sqrt(W_j/W_k))]^2 / sqrt(8 (1 + W_k/W_j))
+ *     (Eq. mixavg_viscosity);
+ *   kappa = (sum_k X_k kappa_k + (sum_k X_k/kappa_k)^-1) / 2 (Eq. mixavg_conductivity);
+ *   D_km = (W - X_k W_k)/W (sum_{j != k} X_j/D_kj)^-1 (Eq. diff_mix_rule);
+ *   X_k = W Y_k / W_k the mole fractions.
+ * T: [n] K; Y: [N][n]; mu [n] Pa s, kappa [n] W/(m K), D_mix [N][n] m^2/s out, each
+ * nullable (at least one given).  D_mix of a species is undefined (0/0) where it
+ * is the only species present. */
+int pyro_transport(const pyro_mech* mech, int64_t n, const double* T, const double* Y, double* mu,
+                   double* kappa, double* D_mix, void* stream);
 
 /* ---- Learned initial guess for the Newton temperature solve ----------------
  * Not in the paper (its Newton starts from a fixed guess, Sec. 4.3 listing of

@@ -35,7 +35,7 @@ EXPORTS = [
     "pyro_net_production_rates_noalloc", "pyro_mech_prepare", "pyro_jvp", "pyro_vjp", "pyro_jacobian",
     "pyro_mlp_n_params", "pyro_mlp_set_params", "pyro_mlp_get_params", "pyro_mlp_train", "pyro_mlp_grad",
     "pyro_mlp_guess", "pyro_mlp_save", "pyro_mlp_load", "pyro_enthalpy", "pyro_temperature_enthalpy",
-    "pyro_jacobian_adiabatic", "pyro_cn_step",
+    "pyro_jacobian_adiabatic", "pyro_cn_step", "pyro_transport",
 ]
 
 _lib = None
@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
         L.pyro_temperature.argtypes = [P, I64, D, D, D, ctypes.c_int, D, D, P]
         L.pyro_enthalpy.argtypes = [P, I64, D, D, D, D, P]
         L.pyro_jacobian_adiabatic.argtypes = [P, I64, D, D, D, D, P]
+        L.pyro_transport.argtypes = [P, I64, D, D, D, D, D, P]
         L.pyro_cn_step.argtypes = [P, I64, ctypes.c_double, D, D, D, ctypes.c_double, ctypes.c_int, D, D, D, P]
         L.pyro_temperature_enthalpy.argtypes = [P, I64, D, D, D, D, D, P]
         L.pyro_net_production_rates.argtypes = [P, I64, D, D, ctypes.c_int, D, D, D, P]
@@ -264,6 +265,16 @@ class Mechanism:
         args = [rho, T, Y, J]
         _check(lib().pyro_jacobian(self._h, _n(rho), *[_ptr(a)[0] for a in args], _stream(args)))
         return J
+
+    def transport(self, T, Y, mu=True, kappa=True, diffusivities=True):
+        """Mixture-averaged (mu [n], kappa [n], D_mix [N, n]); outputs not requested are None."""
+        n = _n(T)
+        m_ = _empty_like(T, (n,)) if mu else None
+        k_ = _empty_like(T, (n,)) if kappa else None
+        d_ = _empty_like(T, (self.n_species, n)) if diffusivities else None
+        arrays = [T, Y, m_, k_, d_]
+        _check(lib().pyro_transport(self._h, n, *[_ptr(a)[0] for a in arrays], _stream(arrays)))
+        return m_, k_, d_
 
     def jacobian_adiabatic(self, rho, T, Y, out=None):
         """J [N*N, n]: dS_j/dY_k (row j, column k) of S = W omega at fixed (rho, e)."""

@@ -30,6 +30,7 @@
 //    Newton slope until |dT| <= tol T, plus one further step.
 #include "pyro_emit.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <set>
@@ -1034,6 +1035,120 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
 }
 
 // ---------------------------------------------------------------------------
+// Mixture-averaged transport (Sec. A.2): mu (Eq. mixavg_viscosity, Wilke's
+// Phi), kappa (Eq. mixavg_conductivity, Eq. species_cond) and the mixture
+// diffusivities D_km (Eq. diff_mix_rule), one thread per state.
+//
+// Arithmetic (exact up to rounding):
+//  * mu_k = sqrt(T) P_k^2 with P_k = |sum_m b_km ln^m T|, so sqrt(mu_k/mu_j) =
+//    P_k/P_j and Wilke's Phi_kj = c_kj (1 + P_k w_kj / P_j)^2 with the constants
+//    c_kj = 1/sqrt(8 (1 + W_k/W_j)), w_kj = (W_j/W_k)^(1/4).  Expanding the square,
+//      sum_j Phi_kj X_j = sum_j c_kj X_j + 2 P_k sum_j c_kj w_kj (X_j/P_j)
+//                         + P_k^2 sum_j c_kj w_kj^2 (X_j/P_j^2),
+//    three products with constant matrices and no per-pair square root or division.
+//  * the common sqrt(T) of the species fits is factored out of every sum.
+//  * D_km = (1 - Y_k) sqrt(T) / sum_{j != k} X_j / p_kj (W - X_k W_k = W (1 - Y_k)),
+//    with one reciprocal per unordered pair {k, j} feeding both sums.
+// ---------------------------------------------------------------------------
+void emit_transport_kernel(Src& s, const Mechanism& m, int blk, bool gstore) {
+  const int N = m.n_species();
+  const TransportFits& tf = m.transport;
+  auto W = [&](int k) { return (long double)m.species[k].W; };
+  // constant tables (global memory, read with uniform addresses)
+  s << "\n__device__ const double pyro_tr_wilke[" << 3 * N * N << "] = {";
+  for (int t = 0; t < 3; ++t)
+    for (int k = 0; k < N; ++k)
+      for (int j = 0; j < N; ++j) {
+        long double c = 1.0L / sqrtl(8.0L * (1.0L + W(k) / W(j)));
+        long double w = powl(W(j) / W(k), 0.25L);
+        long double v = t == 0 ? c : t == 1 ? c * w : c * w * w;
+        s << ((t | k | j) ? "," : "") << lit((double)v);
+      }
+  s << "};\n";
+  const int npair = N * (N - 1) / 2;
+  s << "__device__ const double pyro_tr_pair[" << std::max(1, 5 * npair) << "] = {";
+  int q = 0;
+  for (int k = 0; k < N; ++k)
+    for (int j = k + 1; j < N; ++j)
+      for (int i = 0; i < 5; ++i) s << (q++ ? "," : "") << lit(tf.diff[((size_t)k * N + j) * 5 + i]);
+  if (q == 0) s << "0.0";
+  s << "};\n";
+  s << "\n// mu, kappa, D_km of the mixture-averaged model (each output nullable)\n";
+  s << "extern \"C\" __global__ void __launch_bounds__(" << blk << ") pyro_transport(i64 n, const double* __restrict__ g_T,\n"
+       "    const double* __restrict__ g_Y, double* __restrict__ g_mu, double* __restrict__ g_kappa,\n"
+       "    double* __restrict__ g_Dm, double* __restrict__ g_store) {\n"
+       "  __shared__ double s_exp[512];\n  __shared__ double s_log[256];\n  extern __shared__ double s_dyn[];\n"
+       "  double* sX = " << (gstore ? "g_store + (i64)blockIdx.x * 4 * NSP * BLKD" : "s_dyn") << ";\n"
+       "  double* sP = sX + NSP * BLKD; double* sV = sP + NSP * BLKD; double* sW = sV + NSP * BLKD;\n"
+       "  pyro_load_tables(s_exp, s_log);\n  __syncthreads();\n  const int t = threadIdx.x;\n"
+       "  for (i64 p = (i64)blockIdx.x * BLKD + t; p < n; p += (i64)gridDim.x * BLKD) {\n"
+       "    const double* Yp = g_Y + p;\n"
+       "    const double T = g_T[p];\n    const double L = pdm::log(T, s_log);\n    const double sqT = sqrt(T);\n"
+       "    double ys = 0.0;\n";
+  for (int k = 0; k < N; ++k) s << "    ys = fma(__ldg(Yp + (i64)" << k << " * n), " << lit(1.0 / m.species[k].W) << ", ys);\n";
+  s << "    const double rys = pdm::rcp(ys);\n    double ka = 0.0, kh = 0.0;\n";
+  for (int k = 0; k < N; ++k) {
+    const double* b = &tf.visc[(size_t)k * 5];
+    const double* c = &tf.cond[(size_t)k * 5];
+    s << "    { const double x = __ldg(Yp + (i64)" << k << " * n) * (" << lit(1.0 / m.species[k].W) << " * rys);\n"
+      << "      double P = fma(L, " << lit(b[4]) << ", " << lit(b[3]) << "); P = fma(L, P, " << lit(b[2])
+      << "); P = fma(L, P, " << lit(b[1]) << "); P = fabs(fma(L, P, " << lit(b[0]) << "));\n"
+      << "      double K = fma(L, " << lit(c[4]) << ", " << lit(c[3]) << "); K = fma(L, K, " << lit(c[2])
+      << "); K = fma(L, K, " << lit(c[1]) << "); K = fma(L, K, " << lit(c[0]) << ");\n"
+      << "      const double qv = pdm::rcp(P) * x;\n"
+      << "      sX" << sidx(k) << " = x; sP" << sidx(k) << " = P; sV" << sidx(k) << " = qv; sW" << sidx(k)
+      << " = qv * pdm::rcp(P);\n"
+      << "      ka = fma(x, K, ka); kh = fma(x, pdm::rcp(K), kh); }\n";
+  }
+  s << "    if (g_kappa) g_kappa[p] = 0.5 * sqT * (ka + pdm::rcp(kh));\n";
+  s << R"(    if (g_mu) {
+      double mu = 0.0;
+      #pragma unroll 1
+      for (int k = 0; k < NSP; ++k) {
+        const double* c0 = pyro_tr_wilke + k * NSP;
+        const double* c1 = c0 + NSP * NSP;
+        const double* c2 = c1 + NSP * NSP;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        #pragma unroll 4
+        for (int j = 0; j < NSP; ++j) {
+          a0 = fma(__ldg(c0 + j), sX[j * BLKD + t], a0);
+          a1 = fma(__ldg(c1 + j), sV[j * BLKD + t], a1);
+          a2 = fma(__ldg(c2 + j), sW[j * BLKD + t], a2);
+        }
+        const double Pk = sP[k * BLKD + t];
+        const double den = fma(Pk, fma(Pk, a2, 2.0 * a1), a0);
+        mu = fma(sX[k * BLKD + t] * (Pk * Pk), pdm::rcp(den), mu);
+      }
+      g_mu[p] = sqT * mu;
+    }
+    if (g_Dm) {
+      #pragma unroll 1
+      for (int k = 0; k < NSP; ++k) sV[k * BLKD + t] = 0.0;
+      const double* a = pyro_tr_pair;
+      #pragma unroll 1
+      for (int k = 0; k < NSP - 1; ++k) {
+        const double xk = sX[k * BLKD + t];
+        double sk = sV[k * BLKD + t];
+        #pragma unroll 2
+        for (int j = k + 1; j < NSP; ++j, a += 5) {
+          double pk = fma(L, __ldg(a + 4), __ldg(a + 3));
+          pk = fma(L, pk, __ldg(a + 2)); pk = fma(L, pk, __ldg(a + 1)); pk = fma(L, pk, __ldg(a));
+          const double r = pdm::rcp(pk);
+          sk = fma(sX[j * BLKD + t], r, sk);
+          sV[j * BLKD + t] = fma(xk, r, sV[j * BLKD + t]);
+        }
+        sV[k * BLKD + t] = sk;
+      }
+      #pragma unroll 1
+      for (int k = 0; k < NSP; ++k)
+        g_Dm[(i64)k * n + p] = (1.0 - __ldg(Yp + (i64)k * n)) * sqT * pdm::rcp(sV[k * BLKD + t]);
+    }
+  }
+}
+)";
+}
+
+// ---------------------------------------------------------------------------
 // Crank-Nicolson step (Sec. A.3.2, Eqs. crank_nicol_rhs to crank_nicol_jac):
 // preparation, batched dense solve of the Newton system, completion.  The
 // Newton system itself is assembled by the Jacobian kernel in mode CN.
@@ -1631,6 +1746,15 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, cons
     emit_jacobian_kernel(d, m, C, opt.deriv_block, &ns2, JacMode::ADIA);
     out.group_sources["jad"] = d.o.str();
   }
+  if (m.has_transport) {
+    Src d; d << pre.o.str();
+    emit_transport_kernel(d, m, opt.deriv_block, opt.dgstore);
+    out.group_sources["tr"] = d.o.str();
+    const int npair = N * (N - 1) / 2;
+    // FP64-pipe operations per state (rcp = 4, log = 7, sqrt counted as 1)
+    out.stats["transport_fp64_ops_per_point"] = 7 + 1 + N + 4 + N * 23.0 + 4 + 3.0 * N * N + 8.0 * N + 10.0 * npair + 6.0 * N;
+  }
+  out.stats["has_transport"] = m.has_transport ? 1 : 0;
   {
     // Crank-Nicolson: temperature solve + Newton-system assembly + batched solve
     int ns2 = 0;

@@ -458,7 +458,7 @@ int ensure_store(pyro_mech* h, size_t bytes) {
 
 const char* group_kernel(const std::string& g) {
   return g == "jvp" ? "pyro_jvp" : g == "vjp" ? "pyro_vjp" : g == "jad" ? "pyro_jacobian_adiabatic"
-       : g == "cn" ? "pyro_cn_assemble" : "pyro_jacobian";
+       : g == "cn" ? "pyro_cn_assemble" : g == "tr" ? "pyro_transport" : "pyro_jacobian";
 }
 
 // Compile (in parallel threads, cached on disk) and load the named derivative
@@ -840,6 +840,10 @@ int pyro_mech_prepare(const pyro_mech* hc, const char* kernels) {
       else if (item == "jacobian" || item == "jac") names.push_back("jac");
       else if (item == "jacobian_adiabatic" || item == "jad") names.push_back("jad");
       else if (item == "cn" || item == "crank_nicolson") names.push_back("cn");
+      else if (item == "transport" || item == "tr") {
+        if (h->emitted.stats["has_transport"] <= 0) return fail(PYRO_EMECH, "the mechanism has no transport section");
+        names.push_back("tr");
+      }
       else if (!item.empty()) return fail(PYRO_EINVAL, "unknown kernel group '" + item + "'");
     }
   }
@@ -904,6 +908,26 @@ int pyro_jacobian(const pyro_mech* hc, int64_t n, const double* rho, const doubl
                    });
 }
 
+
+int pyro_transport(const pyro_mech* hc, int64_t n, const double* T, const double* Y, double* mu, double* kappa,
+                   double* D_mix, void* stream) {
+  pyro_mech* h = const_cast<pyro_mech*>(hc);
+  if (!h || n < 0 || (n > 0 && (!T || !Y || (!mu && !kappa && !D_mix))))
+    return fail(PYRO_EINVAL, "pyro_transport: bad arguments");
+  if (h->emitted.stats["has_transport"] <= 0) return fail(PYRO_EMECH, "the mechanism has no transport section");
+  if (n == 0) return PYRO_OK;
+  if (int rc = check_device(h)) return rc;
+  if (int rc = ensure_groups(h, {"tr"})) return rc;
+  pyro_mech::Group& G = h->groups["tr"];
+  const int64_t NS = h->m.n_species();
+  return with_args(h, n, {{T, 1, 8, true, false}, {Y, NS, 8, true, false}, {mu, 1, 8, false, true},
+                          {kappa, 1, 8, false, true}, {D_mix, NS, 8, false, true}},
+                   stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
+                     long long nn = nc;
+                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &d[4], &G.store};
+                     return launch_deriv(h, G, nc, st, params);
+                   });
+}
 
 int pyro_jacobian_adiabatic(const pyro_mech* hc, int64_t n, const double* rho, const double* T, const double* Y,
                             double* J, void* stream) {

@@ -84,6 +84,24 @@ def test_adiabatic_jacobian_and_crank_nicolson_kernels_compile_without_gpu(mech_
     assert L.pyro_jacobian_adiabatic(m.handle, 4, None, px, px, px, None) == B.PYRO_EINVAL
 
 
+def test_transport_kernels_compile_without_gpu(mech_files, tmp_path):
+    m = B.Mechanism(mech_files[0][0], "device=0")
+    assert m.stat("has_transport") == 1
+    m.prepare("transport")
+    assert m.stat("tr_cubin_bytes") > 1000 and m.stat("transport_fp64_ops_per_point") > 0
+    L = B.lib()
+    D = ctypes.POINTER(ctypes.c_double)
+    x = ctypes.cast((ctypes.c_double * 40)(), D)
+    assert L.pyro_transport(m.handle, 4, x, x, None, None, None, None) == B.PYRO_EINVAL   # no output
+    assert L.pyro_transport(m.handle, 4, None, x, x, None, None, None) == B.PYRO_EINVAL
+    # a mechanism file without a transport section: no transport kernels, PYRO_EMECH
+    mb = B.Mechanism(handmech.write(handmech.abcd_mechanism(), str(tmp_path), "abcd.txt"), "device=0")
+    assert mb.stat("has_transport") == 0
+    assert L.pyro_transport(mb.handle, 4, x, x, x, None, None, None) == B.PYRO_EMECH
+    with pytest.raises(B.PyroError):
+        mb.prepare("transport")
+
+
 def test_unbalanced_mechanism_is_rejected(tmp_path):
     mech = handmech.abcd_mechanism()
     mech.reactions[0].products = [(2, 1), (3, 2)]      # H + O2 -> OH + 2 O : O not balanced
