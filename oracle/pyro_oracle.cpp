@@ -18,6 +18,7 @@
 //
 // Units: SI with kmol.  R = 8314.462618 J/(kmol K), p0 = 1 atm = 101325 Pa.
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdint>
@@ -49,7 +50,7 @@ struct OSpecies {
   double lo[7] = {0}, hi[7] = {0};
 };
 
-enum { K_ARRHENIUS = 0, K_THREEBODY = 1, K_FALLOFF = 2 };
+enum { K_ARRHENIUS = 0, K_THREEBODY = 1, K_FALLOFF = 2, K_PLOG = 3 };
 
 struct OReaction {
   int kind = K_ARRHENIUS;
@@ -61,6 +62,9 @@ struct OReaction {
   double A0 = 0, b0 = 0, theta0 = 0;
   int n_troe = 0;
   double troe[4] = {0, 0, 0, 0};
+  int n_sri = 0;                                 // SRI falloff data (a, b, c[, d, e])
+  double sri[5] = {0, 0, 0, 1, 0};
+  std::vector<std::vector<double>> plog;         // PLOG nodes (p [Pa], A, b, theta), increasing p
 };
 
 struct OMech {
@@ -136,6 +140,7 @@ bool parse_mech(const char* path, OMech& m) {
     if (kind == "arrhenius") r.kind = K_ARRHENIUS;
     else if (kind == "threebody") r.kind = K_THREEBODY;
     else if (kind == "falloff") r.kind = K_FALLOFF;
+    else if (kind == "plog") r.kind = K_PLOG;
     else { g_err = "unknown reaction kind " + kind; return false; }
     std::string tok;
     while (is >> tok && tok != "end") {
@@ -152,9 +157,10 @@ bool parse_mech(const char* path, OMech& m) {
         int n; is >> n;
         for (int q = 0; q < n; ++q) { int k; double e; is >> k >> e; r.eff.push_back({k, e}); }
       } else if (tok == "low") { r.has_low = true; is >> r.A0 >> r.b0 >> r.theta0; }
-      else if (tok == "troe") {
-        // 3 or 4 numbers follow; peek until a keyword
-        r.n_troe = 0;
+      else if (tok == "troe" || tok == "sri") {
+        // 3 to 5 numbers follow; peek until a keyword
+        int cnt = 0;
+        double vals[5] = {0, 0, 0, 1, 0};
         std::streampos pos;
         while (true) {
           pos = is.tellg();
@@ -162,7 +168,16 @@ bool parse_mech(const char* path, OMech& m) {
           char* endp = nullptr;
           double v = std::strtod(t2.c_str(), &endp);
           if (endp == t2.c_str() || *endp != '\0') { is.seekg(pos); break; }
-          if (r.n_troe < 4) r.troe[r.n_troe++] = v;
+          if (cnt < 5) vals[cnt++] = v;
+        }
+        if (tok == "troe") { r.n_troe = std::min(cnt, 4); for (int i = 0; i < 4; ++i) r.troe[i] = vals[i]; }
+        else { r.n_sri = cnt; for (int i = 0; i < 5; ++i) r.sri[i] = vals[i]; }
+      } else if (tok == "plog") {
+        int n; is >> n;
+        for (int q = 0; q < n; ++q) {
+          std::vector<double> node(4);
+          for (int i = 0; i < 4; ++i) is >> node[i];
+          r.plog.push_back(node);
         }
       } else { g_err = "unknown reaction token " + tok; return false; }
     }
@@ -354,6 +369,13 @@ template <class S> S third_body(const OReaction& r, const S* C, int N) {
 // Troe falloff blending (cited in Sec. A.1 for concentration-dependent rate
 // coefficients; standard form, reading (c8)).  Lindemann when no Troe data.
 template <class S> S falloff_factor(const OReaction& r, S T, S Pr) {
+  if (r.n_sri >= 3) {
+    // SRI form (reading (p1)): F = d [a exp(-b/T) + exp(-T/c)]^X T^e,  X = 1/(1 + (log10 Pr)^2)
+    S lPr = std::log10(Pr);
+    S X = 1.0 / (1.0 + lPr * lPr);
+    S base = r.sri[0] * std::exp(-r.sri[1] / T) + std::exp(-T / r.sri[2]);
+    return r.sri[3] * std::pow(base, X) * std::pow(T, r.sri[4]);
+  }
   if (r.n_troe < 3) return S(1.0);
   double a = r.troe[0], T3 = r.troe[1], T1 = r.troe[2];
   S Fcent = (1.0 - a) * std::exp(-T / T3) + a * std::exp(-T / T1);
@@ -369,9 +391,30 @@ template <class S> S falloff_factor(const OReaction& r, S T, S Pr) {
 }
 
 // forward rate coefficient k_f,j (includes [M] for third-body reactions, reading (c14))
+// PLOG rate coefficient (reading (p2)): with the mixture pressure p = R T sum_k C_k
+// (Eq. eos), k = k_1(T) for p <= p_1, k = k_n(T) for p >= p_n, and in between
+// ln k interpolated linearly in ln p between the bracketing nodes
+// p_i <= p < p_{i+1}: ln k = ln k_i + (ln k_{i+1} - ln k_i)(ln p - ln p_i)/(ln p_{i+1} - ln p_i).
+template <class S> S plog_rate(const OReaction& r, S T, const S* C, int N) {
+  S ctot = 0;
+  for (int k = 0; k < N; ++k) ctot += C[k];
+  S p = R_GAS * T * ctot;
+  const auto& nd = r.plog;
+  const int n = (int)nd.size();
+  if (re(p) <= nd[0][0]) return arrhenius(nd[0][1], nd[0][2], nd[0][3], T);
+  if (re(p) >= nd[n - 1][0]) return arrhenius(nd[n - 1][1], nd[n - 1][2], nd[n - 1][3], T);
+  int i = 0;
+  while (!(re(p) < nd[i + 1][0])) ++i;
+  S lk0 = std::log(arrhenius(nd[i][1], nd[i][2], nd[i][3], T));
+  S lk1 = std::log(arrhenius(nd[i + 1][1], nd[i + 1][2], nd[i + 1][3], T));
+  S w = (std::log(p) - std::log(nd[i][0])) / (std::log(nd[i + 1][0]) - std::log(nd[i][0]));
+  return std::exp(lk0 + (lk1 - lk0) * w);
+}
+
 template <class S> S forward_rate_coefficient(const OMech& m, const OReaction& r, S T, const S* C) {
   int N = m.N();
   if (r.kind == K_ARRHENIUS) return arrhenius(r.A, r.b, r.theta, T);
+  if (r.kind == K_PLOG) return plog_rate(r, T, C, N);
   if (r.kind == K_THREEBODY) return arrhenius(r.A, r.b, r.theta, T) * third_body(r, C, N);
   // falloff: k = k_inf * Pr/(1+Pr) * F,  Pr = k0 [M] / k_inf
   S kinf = arrhenius(r.A, r.b, r.theta, T);

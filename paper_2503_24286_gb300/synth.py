@@ -71,11 +71,14 @@ thermo <k> <T_low> <T_mid> <T_high> <a1..a7 low> <a1..a7 high>   (N lines)
 reactions <M>
 reaction <kind> rev <0|1> dup <0|1> reac <n> <k> <nu> ... prod <n> <k> <nu> ...
          arr <A> <b> <theta>
-         [eff <n> <k> <eps> ...] [low <A0> <b0> <theta0>] [troe <a> <T3> <T1> [<T2>]] end
+         [eff <n> <k> <eps> ...] [low <A0> <b0> <theta0>] [troe <a> <T3> <T1> [<T2>]]
+         [sri <a> <b> <c> [<d> <e>]] [plog <n> <p> <A> <b> <theta> ...] end
 [transport <N>                                           (optional section)
  tspecies <k> <b0..b4> <c0..c4>                          (N lines: viscosity, conductivity)
  tbinary <k> <j> <a0..a4>                                (k < j, N(N-1)/2 lines: diffusivity)]
-kind in {arrhenius, threebody, falloff}; theta = Ea/R in K; SI kmol units.
+kind in {arrhenius, threebody, falloff, plog}; theta = Ea/R in K; SI kmol units.
+A falloff reaction carries troe or sri data (neither: Lindemann); a plog
+reaction lists its pressure nodes (Pa, increasing) and its arr data is unused.
 All reals are written with 17 significant digits (exact round trip).
 """
 
@@ -106,6 +109,8 @@ class Reaction:
     efficiencies: Dict[int, float] = field(default_factory=dict)
     low: Optional[Tuple[float, float, float]] = None       # k0 (A0, b0, theta0)
     troe: Optional[Tuple[float, ...]] = None               # (a, T3, T1[, T2])
+    sri: Optional[Tuple[float, ...]] = None                # falloff SRI (a, b, c[, d, e])
+    plog: Optional[List[Tuple[float, float, float, float]]] = None   # kind plog: (p [Pa], A, b, theta)
 
 
 @dataclass
@@ -163,7 +168,13 @@ CONFIGS = {
     # the same for the 10-species mechanism (fastest scales ~1e-31 s at 1500-2500 K)
     6: dict(name="h2air-10sp-crank-nicolson", mech=0, n_points=4096, T=(1500.0, 2500.0),
             p_atm=(1.0, 1.0), dt=1.0e-31),
+    # other pressure-dependent forms: the 53-species mechanism with 10 of its Troe
+    # falloff reactions given SRI data instead and 20 plain reactions turned into
+    # PLOG reactions (3-5 pressure nodes between 0.1 and 100 atm)
+    7: dict(name="gri-53sp-pdep", mech=7, base=1, n_sri=10, n_plog=20, n_points=2 ** 22,
+            T=(300.0, 2800.0), p_atm=(0.5, 20.0)),
 }
+PDEP_SEED_OFFSET = 2000
 
 MECH_SEED_BASE = 2503
 STATE_SEED_BASE = 24286
@@ -177,6 +188,9 @@ def config_mechanism(index: int) -> Mechanism:
     with transport fits drawn from a separate stream (seed 3503 + mechanism index)."""
     cfg = CONFIGS[index]
     m = CONFIGS[cfg["mech"]]
+    if "base" in m:
+        return pressure_dependent_variant(config_mechanism(m["base"]), m["n_sri"], m["n_plog"],
+                                          MECH_SEED_BASE + PDEP_SEED_OFFSET + cfg["mech"], m["name"])
     mech = generate_mechanism(
         name=m["name"], elements=m["elements"], n_species=m["n_species"],
         n_reactions=m["n_reactions"], n_threebody=m["n_threebody"],
@@ -494,6 +508,35 @@ def generate_mechanism(name: str, elements: List[str], n_species: int, n_reactio
     return Mechanism(name, elems, species, reactions)
 
 
+def pressure_dependent_variant(base: Mechanism, n_sri: int, n_plog: int, seed: int, name: str) -> Mechanism:
+    """A copy of ``base`` with the first ``n_sri`` Troe falloff reactions given SRI
+    data (a ~ U[0.1, 2], b ~ U[100, 1000] K, c ~ U[100, 3000] K; d ~ U[0.5, 2],
+    e ~ U[-0.5, 0.5] on every other one) and the first ``n_plog`` plain
+    non-duplicate reactions turned into PLOG reactions with 3-5 pressure nodes
+    log-uniform in [0.1, 100] atm, each node's Arrhenius data the reaction's own
+    with A x 10^U[-1, 1], b + U[-0.3, 0.3], theta + U[-1000, 1000] K (>= 0)."""
+    import copy
+    rng = np.random.default_rng(seed)
+    mech = copy.deepcopy(base)
+    mech.name = name
+    falloff = [r for r in mech.reactions if r.kind == "falloff" and r.troe is not None]
+    for q, r in enumerate(falloff[:n_sri]):
+        a, b, c = float(rng.uniform(0.1, 2.0)), float(rng.uniform(100.0, 1000.0)), float(rng.uniform(100.0, 3000.0))
+        r.troe = None
+        r.sri = (a, b, c, float(rng.uniform(0.5, 2.0)), float(rng.uniform(-0.5, 0.5))) if q % 2 == 0 else (a, b, c)
+    plain = [r for r in mech.reactions if r.kind == "arrhenius" and not r.duplicate]
+    for r in plain[:n_plog]:
+        nn = int(rng.integers(3, 6))
+        lp = np.sort(rng.uniform(np.log(0.1), np.log(100.0), size=nn))
+        nodes = []
+        for q in range(nn):
+            nodes.append((float(np.exp(lp[q]) * ONE_ATM), float(r.A * 10.0 ** rng.uniform(-1.0, 1.0)),
+                          float(r.b + rng.uniform(-0.3, 0.3)), float(max(0.0, r.theta + rng.uniform(-1000.0, 1000.0)))))
+        r.kind = "plog"
+        r.plog = nodes
+    return mech
+
+
 # ----------------------------------------------------------------------------
 # Transport fits
 # ----------------------------------------------------------------------------
@@ -620,6 +663,12 @@ def write_mechanism(mech: Mechanism, path: str) -> None:
             parts += ["low"] + [_f(x) for x in r.low]
         if r.troe is not None:
             parts += ["troe"] + [_f(x) for x in r.troe]
+        if r.sri is not None:
+            parts += ["sri"] + [_f(x) for x in r.sri]
+        if r.plog is not None:
+            parts += ["plog", str(len(r.plog))]
+            for node in r.plog:
+                parts += [_f(x) for x in node]
         parts.append("end")
         lines.append(" ".join(parts))
     tr = mech.transport
@@ -670,7 +719,7 @@ def read_mechanism(path: str) -> Mechanism:
         rev = dup = False
         reac, prod = [], []
         A = b = th = 0.0
-        eff, low, troe = {}, None, None
+        eff, low, troe, sri, plog = {}, None, None, None, None
         while t[i] != "end":
             key = t[i]
             if key == "rev":
@@ -692,14 +741,22 @@ def read_mechanism(path: str) -> Mechanism:
                 i += 2 + 2 * n
             elif key == "low":
                 low = (float(t[i + 1]), float(t[i + 2]), float(t[i + 3])); i += 4
-            elif key == "troe":
+            elif key in ("troe", "sri"):
                 j = i + 1; vals = []
-                while t[j] not in ("end", "eff", "low"):
+                while t[j] not in ("end", "eff", "low", "troe", "sri", "plog"):
                     vals.append(float(t[j])); j += 1
-                troe = tuple(vals); i = j
+                if key == "troe":
+                    troe = tuple(vals)
+                else:
+                    sri = tuple(vals)
+                i = j
+            elif key == "plog":
+                n = int(t[i + 1])
+                plog = [tuple(float(x) for x in t[i + 2 + 4 * q:i + 6 + 4 * q]) for q in range(n)]
+                i += 2 + 4 * n
             else:
                 raise ValueError("unknown reaction key " + key)
-        reactions.append(Reaction(kind, reac, prod, A, b, th, rev, dup, eff, low, troe))
+        reactions.append(Reaction(kind, reac, prod, A, b, th, rev, dup, eff, low, troe, sri, plog))
     transport = None
     t = next(it, None)
     if t is not None and t[0] == "transport":
@@ -744,6 +801,8 @@ def config_states(index: int, n: Optional[int] = None, offset_seed: int = 0) -> 
     """States of workload ``index`` (seed 24286 + index), optionally fewer points."""
     cfg = CONFIGS[index]
     mech_cfg = CONFIGS[cfg["mech"]]
+    if "base" in mech_cfg:
+        mech_cfg = CONFIGS[mech_cfg["base"]]
     n = cfg["n_points"] if n is None else n
     return generate_states(mech_cfg["n_species"], n, cfg["T"], cfg["p_atm"],
                            seed=STATE_SEED_BASE + index + offset_seed)

@@ -19,10 +19,11 @@ def mech_dir(tmp_path_factory):
 
 @pytest.fixture(scope="session")
 def mech_files(mech_dir):
-    """Synthetic workload mechanisms written once per session: {0: path, 1: path, 4: path}."""
+    """Synthetic workload mechanisms written once per session: {index: path} for the
+    10-, 53-, 160-species mechanisms and the 53-species variant with SRI and PLOG (7)."""
     from paper_2503_24286_gb300 import synth
     out, objs = {}, {}
-    for i in (0, 1, 4):
+    for i in (0, 1, 4, 7):
         m = synth.config_mechanism(i)
         p = os.path.join(mech_dir, "mech%d.txt" % i)
         synth.write_mechanism(m, p)
