@@ -369,6 +369,43 @@ def crank_nicolson_rates(synth, dev, stream, args, rank):
     return res
 
 
+def pressure_dependent_rates(synth, dev, stream, args, rank):
+    """T from e + omega_k on 2^22 states of the 53-species variant with 10 SRI
+    falloff and 20 PLOG reactions (same kernel design as the headline)."""
+    import torch
+    from paper_2503_24286_gb300 import binding as B
+    d = tempfile.mkdtemp()
+    path = os.path.join(d, "mech7.txt")
+    cfg = synth.CONFIGS[7]
+    synth.write_mechanism(synth.config_mechanism(7), path)
+    m = B.Mechanism(path)
+    n = args.pdep_points
+    T, p, Y = synth.generate_states_torch(53, n, cfg["T"], cfg["p_atm"], synth.STATE_SEED_BASE + 7 + 7919 * rank, dev)
+    rho = m.density(p, T, Y)
+    e = m.internal_energy(T, Y)
+    del p
+    w = torch.empty((53, n), dtype=torch.float64, device=dev)
+    To = torch.empty(n, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        m.net_production_rates(rho, Y, e=e, T_out=To, out=w)
+    torch.cuda.synchronize(dev)
+    assert m.nonconverged() == 0
+    steps = max(2, min(args.steps, 5))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        m.net_production_rates(rho, Y, e=e, T_out=To, out=w)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, dev)
+    flops = m.stat("omega_fp64_flops_per_point") + 2 * m.stat("tsolve_collapse_fp64_ops") + \
+        3 * 2 * m.stat("tsolve_iter_fp64_ops_mixed")
+    return {"workload": "53 species / 325 reactions with 10 SRI falloff and 20 PLOG (3-5 nodes in [0.1, 100] atm) "
+                        "reactions, %d states, T ~ U[300, 2800] K, p ~ U[0.5, 20] atm; T from e + omega" % n,
+            "ms": ms, "states_per_s": n / (ms * 1e-3), "fp64_flops_per_state_static": flops,
+            "fp64_frac": flops * n / (ms * 1e-3) / (FP64_PEAK_GFLOPS * 1e9)}
+
+
 def transport_rates(mech, synth, dev, stream, args, rank):
     """Mixture-averaged mu, kappa and D_km (Sec. A.2) on 2^20 resident states of the
     53-species mechanism (T ~ U[300, 2800] K, Dirichlet Y)."""
@@ -502,6 +539,9 @@ def run_ours(args):
         warp53 = {"ms": ms_w, "states_per_s": n / (ms_w * 1e-3)}
         large = large_mechanism_rates(synth, dev, stream, args, rank)
 
+    pdep = None
+    if not args.no_pdep:
+        pdep = pressure_dependent_rates(synth, dev, stream, args, rank)
     transport = None
     if not args.no_transport:
         transport = transport_rates(mech, synth, dev, stream, args, rank)
@@ -546,6 +586,7 @@ def run_ours(args):
                 "large_mechanism": large,
                 "crank_nicolson": cn,
                 "transport": transport,
+                "pressure_dependent": pdep,
                 "kernel_source_hash": src_hash,
                 "kernel": "pyro_omega (fused Newton T(e,Y) + omega), %d threads/block, %d blocks/SM"
                           % (int(mech.stat("block")), int(mech.stat("omega_blocks_per_sm")))}
@@ -572,6 +613,8 @@ def main():
     ap.add_argument("--no-cn", action="store_true")
     ap.add_argument("--transport-points", type=int, default=2 ** 20)
     ap.add_argument("--no-transport", action="store_true")
+    ap.add_argument("--pdep-points", type=int, default=2 ** 22)
+    ap.add_argument("--no-pdep", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -330,6 +330,84 @@ void emit_arg(Src& s, const Mechanism& m, const Reaction& r, double A, double b,
   s << "\n";
 }
 
+bool has_plog(const Mechanism& m) {
+  for (auto& r : m.reactions) if (r.kind == RX_PLOG) return true;
+  return false;
+}
+
+// PLOG exponent (standard form: ln k linear in ln p between the bracketing nodes,
+// end nodes outside the node range) minus sum nu' L_i, into `var`.  Needs lnp =
+// ln(R T rho sum_k Y_k/W_k) (Eq. eos) in scope.  The bracketing segment is chosen
+// by FP64 comparisons, so both sides of a node pick values that agree to rounding.
+// With deriv: also <var>_tau = d var/dT at fixed p-argument terms plus the
+// pressure path d ln p/dT = 1/T, and <var>_pm = d var/d ln p (0 outside the range).
+void emit_plog_arg(Src& s, const Mechanism& m, const Reaction& r, const std::string& var, bool deriv) {
+  long double lnWs = 0;
+  for (auto& p : r.reactants) lnWs += p.second * logl((long double)m.species[p.first].W);
+  const int n = (int)r.plog.size();
+  std::vector<double> la(n), lp(n), inv(n > 1 ? n - 1 : 1);
+  for (int q = 0; q < n; ++q) {
+    la[q] = (double)(logl((long double)r.plog[q].A) - lnWs);
+    lp[q] = (double)logl((long double)r.plog[q].p);
+  }
+  for (int q = 0; q + 1 < n; ++q) inv[q] = (double)(1.0L / (logl((long double)r.plog[q + 1].p) - logl((long double)r.plog[q].p)));
+  auto node = [&](int q, const char* sfx) {
+    return "pla" + std::string(sfx) + " = " + lit(la[q]) + "; pb" + sfx + " = " + lit(r.plog[q].b) + "; pt" + sfx +
+           " = " + lit(r.plog[q].theta) + ";";
+  };
+  s << "      double plaa, pba, pta, plab, pbb, ptb; " << node(0, "a") << " " << node(1, "b") << "\n";
+  s << "      double plp = " << lit(lp[0]) << ", pinv = " << lit(inv[0]) << ";\n";
+  for (int q = 1; q + 1 < n; ++q)
+    s << "      if (lnp >= " << lit(lp[q]) << ") { " << node(q, "a") << " " << node(q + 1, "b") << " plp = "
+      << lit(lp[q]) << "; pinv = " << lit(inv[q]) << "; }\n";
+  s << "      double pxa = fma(pba, lnT, plaa); pxa = fma(-pta, invT, pxa);\n"
+       "      double pxb = fma(pbb, lnT, plab); pxb = fma(-ptb, invT, pxb);\n"
+       "      const double pfu = (lnp - plp) * pinv;\n"
+       "      const double pf = fmin(fmax(pfu, 0.0), 1.0);\n"
+       "      double " << var << " = fma(pf, pxb - pxa, pxa);";
+  s.fma(5); s.add(3); s.mul(1); s.add(2 + (n > 2 ? n - 2 : 0));
+  for (auto& p : r.reactants) {
+    if (p.second == 1) { s << " " << var << " -= sL" << sidx(p.first) << ";"; s.add(); }
+    else { s << " " << var << " = fma(" << lit(-(double)p.second) << ", sL" << sidx(p.first) << ", " << var << ");"; s.fma(); }
+  }
+  s << "\n";
+  if (deriv) {
+    s << "      const double pdx = (pfu > 0.0 && pfu < 1.0) ? (pxb - pxa) * pinv : 0.0;\n"
+         "      const double pta_ = fma(pba, invT, pta * invT2), ptb_ = fma(pbb, invT, ptb * invT2);\n"
+         "      const double " << var << "_tau = fma(pdx, invT, fma(pf, ptb_ - pta_, pta_));\n"
+         "      const double " << var << "_pm = pdx;\n";
+  }
+}
+
+// SRI falloff factor (standard form): F = d [a exp(-b/T) + exp(-T/c)]^X T^e,
+// X = 1/(1 + (log10 Pr)^2).  Needs lnPr, T, invT, lnT in scope; defines F and,
+// with deriv, dlnF_dlnPr and dlnF_dT (at fixed Pr).
+void emit_sri(Src& s, const Reaction& r, bool deriv) {
+  const double inv_ln10 = (double)(1.0L / logl(10.0L));
+  const double a = r.sri[0], b = r.sri[1], c = r.sri[2];
+  const double d = r.n_sri >= 5 ? r.sri[3] : 1.0, e = r.n_sri >= 5 ? r.sri[4] : 0.0;
+  s << "      const double su = lnPr * " << lit(inv_ln10) << ";\n"
+       "      const double sX = pdm::rcp(fma(su, su, 1.0));\n";
+  s.mul(); s.fma(); s.rcp_();
+  if (a > 0.0) {
+    s << "      const double sea = " << lit(a) << " * PEXP(" << lit(-b) << " * invT, s_exp);\n";
+    s.mul(2); s.exp_();
+  } else {
+    s << "      const double sea = 0.0;\n";
+  }
+  s << "      const double seb = PEXP(T * " << lit(-1.0 / c) << ", s_exp);\n"
+       "      const double sS = sea + seb;\n"
+       "      const double slS = pdm::log(sS, s_log);\n"
+       "      const double F = PEXP(fma(sX, slS, fma(" << lit(e) << ", lnT, " << lit((double)logl((long double)d))
+    << ")), s_exp);\n";
+  s.mul(); s.exp_(); s.add(); s.log_(); s.fma(2); s.exp_();
+  if (deriv) {
+    s << "      const double dlnF_dlnPr = slS * (-2.0 * su * sX * sX * " << lit(inv_ln10) << ");\n"
+         "      const double dlnF_dT = fma(sX * fma(sea, " << lit(b) << " * invT2, seb * " << lit(-1.0 / c)
+      << "), pdm::rcp(sS), " << lit(e) << " * invT);\n";
+  }
+}
+
 // Accumulators of the per-species sums (production rates, tangents, adjoints):
 // named registers, or -- for large mechanisms -- the kernel's output array
 // itself (read-modify-write through an opaque stride, L2-resident per block).
@@ -382,11 +460,13 @@ void emit_reaction_group(Src& s, const Mechanism& m, const std::vector<int>& grp
   const Reaction& r = m.reactions[grp[0]];
   s << "    { // reaction";
   for (int j : grp) s << " " << j;
-  s << (r.kind == RX_THREEBODY ? " (three-body)" : r.kind == RX_FALLOFF ? " (falloff)" : "") << "\n";
+  s << (r.kind == RX_THREEBODY ? " (three-body)" : r.kind == RX_FALLOFF ? " (falloff)"
+        : r.kind == RX_PLOG ? " (plog)" : "") << "\n";
   // k~ (sum over duplicates)
   for (size_t q = 0; q < grp.size(); ++q) {
     const Reaction& rq = m.reactions[grp[q]];
-    emit_arg(s, m, rq, rq.A, rq.b, rq.theta, "x" + std::to_string(q));
+    if (rq.kind == RX_PLOG) emit_plog_arg(s, m, rq, "x" + std::to_string(q), false);
+    else emit_arg(s, m, rq, rq.A, rq.b, rq.theta, "x" + std::to_string(q));
   }
   s << "      double kt = PEXP(x0, s_exp);";
   s.exp_();
@@ -405,7 +485,11 @@ void emit_reaction_group(Src& s, const Mechanism& m, const std::vector<int>& grp
     // Pr/(1+Pr) = 1/(1 + exp(-ln Pr))
     s << "      double fpr = pdm::rcp(1.0 + PEXP(-lnPr, s_exp));\n";
     s.exp_(); s.add(); s.rcp_();
-    if (r.n_troe >= 3) {
+    if (r.n_sri >= 3) {
+      emit_sri(s, r, false);
+      s << "      kt *= fpr * F;\n";
+      s.mul(2);
+    } else if (r.n_troe >= 3) {
       double a = r.troe[0], T3 = r.troe[1], T1 = r.troe[2];
       s << "      double fc = ";
       if (a < 1.0) {
@@ -555,11 +639,21 @@ std::string dprod(const std::vector<int>& f, const char* arr, const char* darr) 
 
 // emits, inside a reaction block: x, kt, tau, [mS, M, kM], kk, Pf, Pr, D, R
 void emit_reaction_core(Src& s, const Mechanism& m, const Reaction& r) {
-  emit_arg(s, m, r, r.A, r.b, r.theta, "x");
-  s << "      const double kt = PEXP(x, s_exp);\n";
-  s << "      double tau = fma(" << lit(r.b) << ", invT, " << lit(r.theta) << " * invT2);\n";
+  if (r.kind == RX_PLOG) {
+    emit_plog_arg(s, m, r, "x", true);
+    s << "      const double kt = PEXP(x, s_exp);\n";
+    s << "      double tau = x_tau;\n";
+  } else {
+    emit_arg(s, m, r, r.A, r.b, r.theta, "x");
+    s << "      const double kt = PEXP(x, s_exp);\n";
+    s << "      double tau = fma(" << lit(r.b) << ", invT, " << lit(r.theta) << " * invT2);\n";
+  }
   if (r.kind == RX_ARRHENIUS) {
     s << "      const double kk = kt;\n";
+  } else if (r.kind == RX_PLOG) {
+    // k depends on the total concentration M = rho sum Y/W through ln p = ln(R T M)
+    s << "      const double mS = ysum;\n      const double M = rho * mS;\n"
+         "      const double kk = kt; const double kM = kt * x_pm * pdm::rcp(M);\n";
   } else {
     s << "      double mS = ysum;";
     for (auto& e : r.efficiencies) {
@@ -575,7 +669,12 @@ void emit_reaction_core(Src& s, const Mechanism& m, const Reaction& r) {
         << ") + fma(" << lit(-(r.theta0 - r.theta)) << ", invT, pdm::log(M, s_log));\n";
       s << "      const double pT = fma(" << lit(r.b0 - r.b) << ", invT, " << lit(r.theta0 - r.theta) << " * invT2);\n";
       s << "      const double fpr = pdm::rcp(1.0 + PEXP(-lnPr, s_exp));\n";
-      if (r.n_troe >= 3) {
+      if (r.n_sri >= 3) {
+        emit_sri(s, r, true);
+        s << "      const double sPr = (1.0 - fpr) + dlnF_dlnPr;\n";
+        s << "      tau += fma(sPr, pT, dlnF_dT);\n";
+        s << "      const double kk = kt * fpr * F;\n";
+      } else if (r.n_troe >= 3) {
         double a = r.troe[0], T3 = r.troe[1], T1 = r.troe[2];
         if (a < 1.0)
           s << "      const double t1 = PEXP(fma(T, " << lit(-1.0 / T3) << ", " << lit((double)logl(1.0L - a)) << "), s_exp);\n";
@@ -647,6 +746,8 @@ void emit_jvp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
        "    const double drr = drho * pdm::rcp(rho);\n"
        "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
   emit_species_deriv(s, m, C, DMode::JVP);
+  if (has_plog(m))
+    s << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lit((double)logl(R_GAS)) << ";\n";
   g_acc.mem = opt.acc_mem;
   g_acc.base = "Wp";
   if (opt.acc_mem) s << "    double* Wp = g_dw + p;\n";
@@ -699,6 +800,8 @@ void emit_vjp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
        "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
        "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
   emit_species_deriv(s, m, C, DMode::VJP);
+  if (has_plog(m))
+    s << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lit((double)logl(R_GAS)) << ";\n";
   s << "    double Tb = 0.0, Mtot = 0.0, rhobM = 0.0;\n";
   g_acc.mem = opt.acc_mem;
   g_acc.base = "Ab";
@@ -833,6 +936,8 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
   s << "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
        "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
   emit_species_deriv(s, m, C, DMode::JAC);
+  if (has_plog(m))
+    s << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lit((double)logl(R_GAS)) << ";\n";
   // ---- phase 1
   for (int j = 0; j < M; ++j) {
     const Reaction& r = m.reactions[j];
@@ -1710,6 +1815,11 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, cons
        "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
   r.log_(); r.rcp_();
   emit_species_forward(r, m, C);
+  if (has_plog(m)) {
+    // mixture pressure for the PLOG reactions: ln p = ln(R T rho sum_k Y_k/W_k) (Eq. eos)
+    r << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lit((double)logl(R_GAS)) << ";\n";
+    r.log_(); r.mul(); r.add(2);
+  }
   g_acc.mem = opt.acc_mem;
   g_acc.base = "Wp";
   if (opt.acc_mem) r << "    double* Wp = g_omega + p;\n";

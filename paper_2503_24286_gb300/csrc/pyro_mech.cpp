@@ -124,6 +124,7 @@ bool parse_mechanism_file(const std::string& path, Mechanism& m, std::string& er
     if (kind == "arrhenius") r.kind = RX_ARRHENIUS;
     else if (kind == "threebody") r.kind = RX_THREEBODY;
     else if (kind == "falloff") r.kind = RX_FALLOFF;
+    else if (kind == "plog") r.kind = RX_PLOG;
     else return fail("unknown reaction kind '" + kind + "'");
     bool has_arr = false, ended = false;
     std::string tok;
@@ -156,12 +157,21 @@ bool parse_mechanism_file(const std::string& path, Mechanism& m, std::string& er
       } else if (tok == "troe") {
         r.n_troe = 0;
         while (ln.is_number_next() && r.n_troe < 4) ln.real(r.troe[r.n_troe++]);
+      } else if (tok == "sri") {
+        r.n_sri = 0;
+        while (ln.is_number_next() && r.n_sri < 5) ln.real(r.sri[r.n_sri++]);
+      } else if (tok == "plog") {
+        int n; if (!ln.integer(n) || n < 2) return fail("plog needs at least 2 nodes");
+        r.plog.resize(n);
+        for (auto& nd : r.plog)
+          if (!ln.real(nd.p) || !ln.real(nd.A) || !ln.real(nd.b) || !ln.real(nd.theta)) return fail("bad plog node");
       } else {
         return fail("unknown reaction token '" + tok + "'");
       }
     }
     if (!ended) return fail("reaction line without 'end'");
-    if (!has_arr) return fail("reaction without 'arr'");
+    if (!has_arr && r.kind != RX_PLOG) return fail("reaction without 'arr'");
+    if (r.kind == RX_PLOG && !has_arr) { r.A = r.plog[0].A; r.b = r.plog[0].b; r.theta = r.plog[0].theta; }
     if (r.reactants.empty() || r.products.empty()) return fail("reaction without reactants or products");
   }
   // optional transport section
@@ -237,8 +247,25 @@ bool validate_mechanism(const Mechanism& m, std::string& err) {
       if (!r.has_low || !(r.A0 > 0)) { err = tag + "falloff reaction without low-pressure limit"; return false; }
       if (r.n_troe != 0 && r.n_troe != 3 && r.n_troe != 4) { err = tag + "Troe needs 3 or 4 parameters"; return false; }
       if (r.n_troe >= 3 && !(r.troe[1] > 0 && r.troe[2] > 0)) { err = tag + "Troe T3, T1 must be positive"; return false; }
-    } else if (r.has_low || r.n_troe) {
-      err = tag + "low/troe data on a non-falloff reaction"; return false;
+      if (r.n_sri != 0 && r.n_sri != 3 && r.n_sri != 5) { err = tag + "SRI needs 3 or 5 parameters"; return false; }
+      if (r.n_sri && r.n_troe) { err = tag + "both Troe and SRI data"; return false; }
+      if (r.n_sri && !(r.sri[0] >= 0 && r.sri[1] >= 0 && r.sri[2] > 0 && r.sri[3] > 0 && std::isfinite(r.sri[4]))) {
+        err = tag + "SRI needs a >= 0, b >= 0, c > 0, d > 0"; return false;
+      }
+    } else if (r.has_low || r.n_troe || r.n_sri) {
+      err = tag + "low/troe/sri data on a non-falloff reaction"; return false;
+    }
+    if (r.kind == RX_PLOG) {
+      for (size_t q = 0; q < r.plog.size(); ++q) {
+        const PlogNode& nd = r.plog[q];
+        if (!(nd.p > 0) || !(nd.A > 0) || !std::isfinite(nd.b) || !std::isfinite(nd.theta) ||
+            (q > 0 && !(nd.p > r.plog[q - 1].p))) {
+          err = tag + "plog nodes need p > 0 increasing and A > 0"; return false;
+        }
+      }
+      if (!r.efficiencies.empty()) { err = tag + "efficiencies on a plog reaction"; return false; }
+    } else if (!r.plog.empty()) {
+      err = tag + "plog data on a non-plog reaction"; return false;
     }
     if (r.kind == RX_ARRHENIUS && !r.efficiencies.empty()) { err = tag + "efficiencies on a plain reaction"; return false; }
     int order_r = 0;

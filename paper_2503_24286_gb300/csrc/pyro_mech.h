@@ -21,7 +21,10 @@ struct Species {
   double low[7] = {0}, high[7] = {0};             // a1..a7 below / above t_mid
 };
 
-enum ReactionKind { RX_ARRHENIUS = 0, RX_THREEBODY = 1, RX_FALLOFF = 2 };
+enum ReactionKind { RX_ARRHENIUS = 0, RX_THREEBODY = 1, RX_FALLOFF = 2, RX_PLOG = 3 };
+
+// PLOG node: rate coefficient A T^b exp(-theta/T) at pressure p (Pa)
+struct PlogNode { double p = 0.0, A = 0.0, b = 0.0, theta = 0.0; };
 
 struct Reaction {
   ReactionKind kind = RX_ARRHENIUS;
@@ -35,6 +38,9 @@ struct Reaction {
   double A0 = 0.0, b0 = 0.0, theta0 = 0.0;        // low-pressure limit k0
   int n_troe = 0;                                 // 0: Lindemann, 3 or 4: Troe (a, T3, T1[, T2])
   double troe[4] = {0, 0, 0, 0};
+  int n_sri = 0;                                  // 0, or 3 / 5: SRI falloff (a, b, c[, d, e]), d = 1, e = 0 by default
+  double sri[5] = {0, 0, 0, 1, 0};
+  std::vector<PlogNode> plog;                     // RX_PLOG: nodes in increasing pressure
 };
 
 // Mixture-averaged transport data (Sec. A.2): per-species fits of viscosity

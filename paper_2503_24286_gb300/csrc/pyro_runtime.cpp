@@ -577,6 +577,13 @@ int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) 
   if (!parse_options(options, h->opt, err)) { delete h; return fail(PYRO_EINVAL, err); }
   if (!parse_mechanism_file(mech_path, h->m, err)) { delete h; return fail(PYRO_EMECH, err); }
   if (!validate_mechanism(h->m, err)) { delete h; return fail(PYRO_EMECH, err); }
+  if (h->opt.warp)
+    for (auto& r : h->m.reactions)
+      if (r.kind == RX_PLOG || r.n_sri) {
+        delete h;
+        return fail(PYRO_EINVAL, "variant=warp supports Arrhenius, third-body and Troe/Lindemann falloff "
+                                 "reactions only (this mechanism has SRI or PLOG reactions)");
+      }
   for (auto& s : h->m.species) h->W.push_back(s.W);
   EmitOptions eo;
   eo.block = h->opt.block;

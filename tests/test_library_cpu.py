@@ -102,6 +102,27 @@ def test_transport_kernels_compile_without_gpu(mech_files, tmp_path):
         mb.prepare("transport")
 
 
+def test_pressure_dependent_forms_parse_validate_and_compile(mech_files, tmp_path):
+    m = B.Mechanism(mech_files[0][7], "device=0")
+    assert m.stat("omega_fp64_flops_per_point") > 0
+    src = m.source()
+    assert "(plog)" in src and "lnp" in src
+    with pytest.raises(B.PyroError) as ei:                 # the table-driven variant has no SRI/PLOG
+        B.Mechanism(mech_files[0][7], "device=0;variant=warp")
+    assert ei.value.code == B.PYRO_EINVAL
+    mech = handmech.abcd_mechanism(kind="falloff", low=(1e16, -1.0, 1000.0))
+    mech.reactions[0].sri = (0.5, 100.0, -3.0)                # c must be positive
+    with pytest.raises(B.PyroError) as ei:
+        B.Mechanism(handmech.write(mech, str(tmp_path), "badsri.txt"), "device=0")
+    assert ei.value.code == B.PYRO_EMECH
+    mech = handmech.abcd_mechanism()
+    mech.reactions[0].kind = "plog"
+    mech.reactions[0].plog = [(1e5, 1e10, 0.0, 100.0), (1e4, 1e10, 0.0, 100.0)]   # decreasing pressures
+    with pytest.raises(B.PyroError) as ei:
+        B.Mechanism(handmech.write(mech, str(tmp_path), "badplog.txt"), "device=0")
+    assert ei.value.code == B.PYRO_EMECH
+
+
 def test_unbalanced_mechanism_is_rejected(tmp_path):
     mech = handmech.abcd_mechanism()
     mech.reactions[0].products = [(2, 1), (3, 2)]      # H + O2 -> OH + 2 O : O not balanced
