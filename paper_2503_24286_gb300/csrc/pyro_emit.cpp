@@ -997,8 +997,6 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
     if (mode == JacMode::CN) {
       s << "    const double hh = 0.5 * dt * pdm::rcp(rho);\n";
       s << "    const i64 nr = CN_G;\n";
-    } else {
-      s << "    const i64 nr = opq(n);\n";
     }
     std::vector<std::vector<std::pair<int, int>>> rows(N);
     for (int j = 0; j < M; ++j)
@@ -1030,6 +1028,8 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
       if (mode == JacMode::CN) s << "      const double F = -hh * " << lit(m.species[k].W) << ";\n";
       else s << "      const double F = " << lit(m.species[k].W) << ";\n";
       s << "      const double fu = F * u, fj = F * jt;\n";
+      // a fresh opaque stride per row keeps the compiler from holding all N^2 offsets live
+      if (mode != JacMode::CN) s << "      const i64 nr = opq(n);\n";
       s << "      double* Jr = Jp + (i64)" << k * N << " * nr;\n";
       s << "      #pragma unroll 1\n      for (int i = 0; i < NSP; ++i) Jr[(i64)i * nr] = fma(sL[i * BLKD + t], fu, fj * sA[i * BLKD + t]);\n";
       for (int i = 0; i < N; ++i) {
@@ -1178,13 +1178,17 @@ void emit_transport_kernel(Src& s, const Mechanism& m, int blk, bool gstore) {
       for (int i = 0; i < 5; ++i) s << (q++ ? "," : "") << lit(tf.diff[((size_t)k * N + j) * 5 + i]);
   if (q == 0) s << "0.0";
   s << "};\n";
+  s << "__device__ const double pyro_tr_visc[" << 5 * N << "] = {";
+  for (int k = 0; k < N; ++k)
+    for (int i = 0; i < 5; ++i) s << ((k | i) ? "," : "") << lit(tf.visc[(size_t)k * 5 + i]);
+  s << "};\n";
   s << "\n// mu, kappa, D_km of the mixture-averaged model (each output nullable)\n";
   s << "extern \"C\" __global__ void __launch_bounds__(" << blk << ") pyro_transport(i64 n, const double* __restrict__ g_T,\n"
        "    const double* __restrict__ g_Y, double* __restrict__ g_mu, double* __restrict__ g_kappa,\n"
        "    double* __restrict__ g_Dm, double* __restrict__ g_store) {\n"
        "  __shared__ double s_exp[512];\n  __shared__ double s_log[256];\n  extern __shared__ double s_dyn[];\n"
-       "  double* sX = " << (gstore ? "g_store + (i64)blockIdx.x * 4 * NSP * BLKD" : "s_dyn") << ";\n"
-       "  double* sP = sX + NSP * BLKD; double* sV = sP + NSP * BLKD; double* sW = sV + NSP * BLKD;\n"
+       "  double* sX = " << (gstore ? "g_store + (i64)blockIdx.x * 3 * NSP * BLKD" : "s_dyn") << ";\n"
+       "  double* sV = sX + NSP * BLKD; double* sW = sV + NSP * BLKD;\n"
        "  pyro_load_tables(s_exp, s_log);\n  __syncthreads();\n  const int t = threadIdx.x;\n"
        "  for (i64 p = (i64)blockIdx.x * BLKD + t; p < n; p += (i64)gridDim.x * BLKD) {\n"
        "    const double* Yp = g_Y + p;\n"
@@ -1201,8 +1205,7 @@ void emit_transport_kernel(Src& s, const Mechanism& m, int blk, bool gstore) {
       << "      double K = fma(L, " << lit(c[4]) << ", " << lit(c[3]) << "); K = fma(L, K, " << lit(c[2])
       << "); K = fma(L, K, " << lit(c[1]) << "); K = fma(L, K, " << lit(c[0]) << ");\n"
       << "      const double qv = pdm::rcp(P) * x;\n"
-      << "      sX" << sidx(k) << " = x; sP" << sidx(k) << " = P; sV" << sidx(k) << " = qv; sW" << sidx(k)
-      << " = qv * pdm::rcp(P);\n"
+      << "      sX" << sidx(k) << " = x; sV" << sidx(k) << " = qv; sW" << sidx(k) << " = qv * pdm::rcp(P);\n"
       << "      ka = fma(x, K, ka); kh = fma(x, pdm::rcp(K), kh); }\n";
   }
   s << "    if (g_kappa) g_kappa[p] = 0.5 * sqT * (ka + pdm::rcp(kh));\n";
@@ -1213,14 +1216,27 @@ void emit_transport_kernel(Src& s, const Mechanism& m, int blk, bool gstore) {
         const double* c0 = pyro_tr_wilke + k * NSP;
         const double* c1 = c0 + NSP * NSP;
         const double* c2 = c1 + NSP * NSP;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-        #pragma unroll 4
-        for (int j = 0; j < NSP; ++j) {
+        // two independent partial sums per product (even / odd j) for the FP64 pipe
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0;
+        int j = 0;
+        #pragma unroll 2
+        for (; j + 1 < NSP; j += 2) {
+          a0 = fma(__ldg(c0 + j), sX[j * BLKD + t], a0);
+          a1 = fma(__ldg(c1 + j), sV[j * BLKD + t], a1);
+          a2 = fma(__ldg(c2 + j), sW[j * BLKD + t], a2);
+          b0 = fma(__ldg(c0 + j + 1), sX[(j + 1) * BLKD + t], b0);
+          b1 = fma(__ldg(c1 + j + 1), sV[(j + 1) * BLKD + t], b1);
+          b2 = fma(__ldg(c2 + j + 1), sW[(j + 1) * BLKD + t], b2);
+        }
+        if (j < NSP) {
           a0 = fma(__ldg(c0 + j), sX[j * BLKD + t], a0);
           a1 = fma(__ldg(c1 + j), sV[j * BLKD + t], a1);
           a2 = fma(__ldg(c2 + j), sW[j * BLKD + t], a2);
         }
-        const double Pk = sP[k * BLKD + t];
+        a0 += b0; a1 += b1; a2 += b2;
+        const double* bk = pyro_tr_visc + 5 * k;
+        double Pk = fma(L, __ldg(bk + 4), __ldg(bk + 3));
+        Pk = fma(L, Pk, __ldg(bk + 2)); Pk = fma(L, Pk, __ldg(bk + 1)); Pk = fabs(fma(L, Pk, __ldg(bk)));
         const double den = fma(Pk, fma(Pk, a2, 2.0 * a1), a0);
         mu = fma(sX[k * BLKD + t] * (Pk * Pk), pdm::rcp(den), mu);
       }
@@ -1234,7 +1250,7 @@ void emit_transport_kernel(Src& s, const Mechanism& m, int blk, bool gstore) {
       for (int k = 0; k < NSP - 1; ++k) {
         const double xk = sX[k * BLKD + t];
         double sk = sV[k * BLKD + t];
-        #pragma unroll 2
+        #pragma unroll 4
         for (int j = k + 1; j < NSP; ++j, a += 5) {
           double pk = fma(L, __ldg(a + 4), __ldg(a + 3));
           pk = fma(L, pk, __ldg(a + 2)); pk = fma(L, pk, __ldg(a + 1)); pk = fma(L, pk, __ldg(a));
@@ -1857,12 +1873,17 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, cons
     out.group_sources["jad"] = d.o.str();
   }
   if (m.has_transport) {
-    Src d; d << pre.o.str();
-    emit_transport_kernel(d, m, opt.deriv_block, opt.dgstore);
+    Src d;
+    EmitOptions topt = opt;
+    topt.block = kTransportBlock;
+    emit_prelude(d, m, topt);
+    d << "#define BLKD " << kTransportBlock << "\n";
+    emit_transport_kernel(d, m, kTransportBlock, opt.dgstore);
+    out.smem_dyn_bytes_transport = opt.dgstore ? 0 : 3 * N * kTransportBlock * (int)sizeof(double);
     out.group_sources["tr"] = d.o.str();
     const int npair = N * (N - 1) / 2;
     // FP64-pipe operations per state (rcp = 4, log = 7, sqrt counted as 1)
-    out.stats["transport_fp64_ops_per_point"] = 7 + 1 + N + 4 + N * 23.0 + 4 + 3.0 * N * N + 8.0 * N + 10.0 * npair + 6.0 * N;
+    out.stats["transport_fp64_ops_per_point"] = 7 + 1 + N + 4 + N * 23.0 + 4 + 3.0 * N * N + 13.0 * N + 10.0 * npair + 6.0 * N;
   }
   out.stats["has_transport"] = m.has_transport ? 1 : 0;
   {

@@ -32,7 +32,12 @@ struct EmitResult {
   int smem_dyn_bytes_deriv = 0;           // dynamic shared memory of the derivative kernels
   int jac_slots = 0;                      // scratch doubles per point of the Jacobian kernel
   int smem_dyn_bytes_cn_solve = 0;        // dynamic shared memory of the Crank-Nicolson solve kernel
+  int smem_dyn_bytes_transport = 0;       // dynamic shared memory of the transport kernel
 };
+
+// Threads per block of the transport kernel (3 per-state arrays of N doubles in
+// shared memory: 32-thread blocks fit 5 per SM for 53 species).
+constexpr int kTransportBlock = 32;
 
 // States per group of the Crank-Nicolson Newton-matrix layout [n/G][N^2][G]
 // (also the warps per block of the batched solve).

@@ -116,12 +116,15 @@ bool nvrtc_compile(const std::string& src, std::vector<char>& cubin, std::string
     return false;
   }
   std::string arch = std::string("--gpu-architecture=") + kArch;
-  const char* opts[] = {arch.c_str(), "-std=c++17", "-lineinfo", "-default-device"};
-  nvrtcResult r = nvrtcCompileProgram(prog, 4, opts);
+  // PYRO_NVRTC_VERBOSE=1: ptxas resource usage (registers, spills, shared memory) to stderr
+  const bool verbose = std::getenv("PYRO_NVRTC_VERBOSE") != nullptr;
+  const char* opts[] = {arch.c_str(), "-std=c++17", "-lineinfo", "-default-device", "--ptxas-options=-v"};
+  nvrtcResult r = nvrtcCompileProgram(prog, verbose ? 5 : 4, opts);
   size_t ls = 0;
   nvrtcGetProgramLogSize(prog, &ls);
   log.assign(ls, '\0');
   if (ls) nvrtcGetProgramLog(prog, &log[0]);
+  if (verbose) std::fprintf(stderr, "%s\n", log.c_str());
   if (r != NVRTC_SUCCESS) { nvrtcDestroyProgram(&prog); return false; }
   size_t cs = 0;
   nvrtcGetCUBINSize(prog, &cs);
@@ -236,6 +239,8 @@ struct pyro_mech {
     double* store = nullptr;   // per-block species arrays of this group (large mechanisms)
     std::map<std::string, CUfunction> fn;   // further kernels of the group
     int solve_blocks_per_sm = 0;            // Crank-Nicolson batched solve
+    int block = 0;                          // threads per block (0: the derivative block size)
+    int smem = -1;                          // dynamic shared memory (-1: the derivative kernels')
   };
   std::map<std::string, Group> groups;
   std::mutex group_mu;
@@ -500,11 +505,13 @@ int ensure_groups(pyro_mech* h, const std::vector<std::string>& names) {
     if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "cuModuleLoadData: " + cu_err(r));
     r = d.ModuleGetFunction(&G.f, G.module, group_kernel(todo[i]));
     if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, std::string("missing kernel ") + group_kernel(todo[i]));
-    int smem = h->emitted.smem_dyn_bytes_deriv;
+    if (todo[i] == "tr") { G.block = pyro::kTransportBlock; G.smem = h->emitted.smem_dyn_bytes_transport; }
+    const int smem = G.smem >= 0 ? G.smem : h->emitted.smem_dyn_bytes_deriv;
+    const int blk = G.block > 0 ? G.block : h->opt.deriv_block;
     r = d.FuncSetAttribute(G.f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem);
     if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "shared memory request: " + cu_err(r));
     int nb = 0;
-    r = d.Occupancy(&nb, G.f, h->opt.deriv_block, smem);
+    r = d.Occupancy(&nb, G.f, blk, smem);
     if (r != CUDA_SUCCESS || nb < 1) return fail(PYRO_ECUDA, std::string(group_kernel(todo[i])) + " does not fit on an SM");
     G.blocks_per_sm = nb;
     h->emitted.stats[todo[i] + "_blocks_per_sm"] = nb;
@@ -552,12 +559,13 @@ int ensure_jac_scratch(pyro_mech* h, const pyro_mech::Group& G, int64_t n) {
 }
 
 int launch_deriv(const pyro_mech* h, const pyro_mech::Group& G, int64_t n, void* stream, void** params) {
-  int64_t need = (n + h->opt.deriv_block - 1) / h->opt.deriv_block;
+  const int blk = G.block > 0 ? G.block : h->opt.deriv_block;
+  const int smem = G.smem >= 0 ? G.smem : h->emitted.smem_dyn_bytes_deriv;
+  int64_t need = (n + blk - 1) / blk;
   int64_t cap = (int64_t)h->num_sms * G.blocks_per_sm;
   unsigned grid = (unsigned)(need < cap ? need : cap);
   if (grid == 0) return PYRO_OK;
-  CUresult r = driver().LaunchKernel(G.f, grid, 1, 1, h->opt.deriv_block, 1, 1, h->emitted.smem_dyn_bytes_deriv,
-                                     as_stream(stream), params, nullptr);
+  CUresult r = driver().LaunchKernel(G.f, grid, 1, 1, blk, 1, 1, smem, as_stream(stream), params, nullptr);
   if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
   return PYRO_OK;
 }
