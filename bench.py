@@ -349,9 +349,18 @@ def crank_nicolson_rates(synth, dev, stream, args, rank):
     assert m.nonconverged() == 0 and (it > 0).all().item()
     res["newton_iters_mean"] = float(it.double().mean().item())
     res["newton_iters_max"] = int(it.max().item())
+    # chord variant: the first iterate's factorisation kept for the whole step
+    mc = B.Mechanism(path, "cn_newton=chord")
+    mc.prepare("cn")
+    _, _, itc = mc.cn_step(dt, rho, T, Y, T_out=To, Y_out=Yo, max_newton=60, with_iters=True)
+    torch.cuda.synchronize(dev)
+    assert mc.nonconverged() == 0 and (itc > 0).all().item()
+    res["chord_newton_iters_mean"] = float(itc.double().mean().item())
+    res["chord_newton_iters_max"] = int(itc.max().item())
     steps = max(2, min(args.steps, 3))
     J = torch.empty((53 * 53, n), dtype=torch.float64, device=dev)
     calls = {"cn_step": lambda: m.cn_step(dt, rho, T, Y, T_out=To, Y_out=Yo),
+             "cn_step_chord": lambda: mc.cn_step(dt, rho, T, Y, T_out=To, Y_out=Yo, max_newton=60),
              "jacobian_adiabatic": lambda: m.jacobian_adiabatic(rho, T, Y, out=J)}
     for name, f in calls.items():
         f()

@@ -76,6 +76,15 @@ typedef struct pyro_mech pyro_mech;
  *                        handle must then not overlap on the GPU)
  *   device=0|1          (0: parse, validate, emit and compile only; no CUDA
  *                        device is touched and nothing can be launched)
+ *   cn_newton=full|chord (pyro_cn_step: Newton with the matrix re-assembled and
+ *                        re-factored at every iterate (full, default, as in
+ *                        Sec. A.3.2), or a chord iteration that keeps a
+ *                        factorisation for cn_refresh iterations (the iterates in
+ *                        between need only the right-hand side); same fixed
+ *                        point and stop rule, more iterations: give max_newton
+ *                        headroom)
+ *   cn_refresh=<k>      (chord: re-assemble and re-factor at iterations 0, k, 2k, ...;
+ *                        default 4)
  * On success *out receives a handle to free with pyro_mech_free. */
 int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out);
 void pyro_mech_free(pyro_mech* mech);

@@ -917,7 +917,8 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
          "    double* __restrict__ g_c, double* __restrict__ g_T, int* __restrict__ g_state, double dt,\n"
          "    int max_iter, double tol, double* __restrict__ g_A, double* __restrict__ g_b,\n"
          "    double* __restrict__ g_scratch, unsigned long long* __restrict__ g_fail,\n"
-         "    const int* __restrict__ g_list, const int* __restrict__ g_count, int* __restrict__ g_count_next) {\n" << prologue <<
+         "    const int* __restrict__ g_list, const int* __restrict__ g_count, int* __restrict__ g_count_next,\n"
+         "    int a_at_state) {\n" << prologue <<
          "  double* W = g_scratch + (i64)blockIdx.x * " << sl.n << " * BLKD + t;\n"
          "  const float tolf = (float)tol;\n"
          "  const i64 na = *g_count;\n"
@@ -926,7 +927,8 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
          "    const i64 p = g_list[q];\n"
          "    const int stp = g_state[p];\n"
          "    const double* Yp = g_Y + p;\n"
-         "    double* Jp = g_A + (q / CN_G) * (i64)(NSP * NSP * CN_G) + (q % CN_G);\n"
+         "    const i64 qa = a_at_state ? p : q;   // matrix at the state's own index (chord) or its slot\n"
+         "    double* Jp = g_A + (qa / CN_G) * (i64)(NSP * NSP * CN_G) + (qa % CN_G);\n"
          "    const double rho = g_rho[p];\n"
          "    int tit;\n"
          "    const double T = pyro_tsolve<false>(Yp, n, g_e[p], g_T[p], max_iter, tolf, &tit);\n"
@@ -1334,11 +1336,16 @@ __device__ __forceinline__ float pyro_scaled_f32(long long bits, int e) {
   return __uint_as_float(fb);
 }
 
+// mode 0: factor the matrix of slot q.  mode 1 (chord, iterations that re-assemble):
+// factor state p's matrix (at index p) and keep its FP32 factors, pivots and row
+// exponents in g_fac.  mode 2 (chord, the iterations between): reuse state p's kept
+// factors and refine against its kept FP64 matrix.
+#define CN_FAC_WORDS (NSP * CN_LDA + 2 * NSP)
 extern "C" __global__ void __launch_bounds__(CN_G * 32) pyro_cn_solve(i64 cnt, i64 n,
     const double* __restrict__ g_A, const double* __restrict__ g_b, double* __restrict__ g_Y,
     int* __restrict__ g_state, int* __restrict__ g_it, double tol, int max_newton, int refine,
     unsigned long long* __restrict__ g_fail, const int* __restrict__ g_list, const int* __restrict__ g_count,
-    int* __restrict__ g_list_next, int* __restrict__ g_count_next) {
+    int* __restrict__ g_list_next, int* __restrict__ g_count_next, int mode, float* __restrict__ g_fac) {
   extern __shared__ double s_cn[];
   const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
@@ -1356,7 +1363,21 @@ extern "C" __global__ void __launch_bounds__(CN_G * 32) pyro_cn_solve(i64 cnt, i
     const i64 p = g_list[q];
     const int st = g_state[p];
     if (st >= 3) continue;
-    const double* Ag = g_A + (q / CN_G) * (i64)(NSP * NSP * CN_G) + (q % CN_G);
+    const i64 qa = mode == 0 ? q : p;             // where this state's FP64 matrix is
+    const double* Ag = g_A + (qa / CN_G) * (i64)(NSP * NSP * CN_G) + (qa % CN_G);
+    float* fac = g_fac + p * (i64)CN_FAC_WORDS;
+    bool sing = false;
+    if (mode == 2) {
+      // kept factors: LU (rows of CN_LDA floats), pivots, row exponents
+      for (int e = l; e < NSP * CN_LDA; e += 32) sM[e] = fac[e];
+      for (int k = l; k < NSP; k += 32) {
+        spiv[k] = __float_as_int(fac[NSP * CN_LDA + k]);
+        se[k] = __float_as_int(fac[NSP * CN_LDA + NSP + k]);
+        sq[k] = __frcp_rn(fac[k * CN_LDA + k]);
+        sr[k] = g_b[(i64)k * cnt + q]; sx[k] = 0.0;
+      }
+      __syncwarp();
+    } else {
     // scaled FP32 copy of the matrix, one row at a time
     #pragma unroll 2
     for (int i = 0; i < NSP; ++i) {
@@ -1384,7 +1405,6 @@ extern "C" __global__ void __launch_bounds__(CN_G * 32) pyro_cn_solve(i64 cnt, i
     for (int k = l; k < NSP; k += 32) { sr[k] = g_b[(i64)k * cnt + q]; sx[k] = 0.0; }
     __syncwarp();
     // LU factorisation with partial pivoting (row exchanges applied to the whole rows)
-    bool sing = false;
     for (int k = 0; k < NSP; ++k) {
       float bv = -1.0f;
       int bi = k;
@@ -1431,6 +1451,14 @@ extern "C" __global__ void __launch_bounds__(CN_G * 32) pyro_cn_solve(i64 cnt, i
       }
       __syncwarp();
     }
+    if (mode == 1 && !sing) {
+      for (int e = l; e < NSP * CN_LDA; e += 32) fac[e] = sM[e];
+      for (int k = l; k < NSP; k += 32) {
+        fac[NSP * CN_LDA + k] = __int_as_float(spiv[k]);
+        fac[NSP * CN_LDA + NSP + k] = __int_as_float(se[k]);
+      }
+    }
+    }   // factorisation (modes 0, 1)
     double dmax = 0.0;
     if (!sing) {
       for (int pass = 0; pass <= refine; ++pass) {
@@ -1519,6 +1547,46 @@ extern "C" __global__ void __launch_bounds__(BLKD) pyro_cn_finish(i64 cnt, i64 n
   }
 }
 )";
+}
+
+// Right-hand side only (the chord variant of the Crank-Nicolson Newton iteration
+// keeps the matrix of its first iterate): T from (e, Y), omega by the forward
+// path, -F = c + (dt/2rho) W omega - Y into slot q.  Same state/list protocol as
+// pyro_cn_assemble.
+void emit_cn_residual_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C) {
+  const int N = m.n_species();
+  s << "\nextern \"C\" __global__ void __launch_bounds__(BLKD) pyro_cn_residual(i64 cnt, i64 n,\n"
+       "    const double* __restrict__ g_rho, const double* __restrict__ g_e, const double* __restrict__ g_Y,\n"
+       "    const double* __restrict__ g_c, double* __restrict__ g_T, int* __restrict__ g_state, double dt,\n"
+       "    int max_iter, double tol, double* __restrict__ g_b, unsigned long long* __restrict__ g_fail,\n"
+       "    const int* __restrict__ g_list, const int* __restrict__ g_count, int* __restrict__ g_count_next) {\n"
+       "  __shared__ double s_exp[512];\n  __shared__ double s_log[256];\n  extern __shared__ double s_dyn[];\n"
+       "  double* sL = s_dyn; double* sA = sL + NSP * BLKD;\n"
+       "  pyro_load_tables(s_exp, s_log);\n  __syncthreads();\n  const int t = threadIdx.x;\n"
+       "  const float tolf = (float)tol;\n  const i64 na = *g_count;\n"
+       "  if (blockIdx.x == 0 && t == 0) *g_count_next = 0;\n"
+       "  for (i64 q = (i64)blockIdx.x * BLKD + t; q < na; q += (i64)gridDim.x * BLKD) {\n"
+       "    const i64 p = g_list[q];\n"
+       "    const double* Yp = g_Y + p;\n    const double rho = g_rho[p];\n"
+       "    int tit;\n"
+       "    const double T = pyro_tsolve<false>(Yp, n, g_e[p], g_T[p], max_iter, tolf, &tit);\n"
+       "    if (tit < 0) { g_state[p] = 4; atomicAdd(g_fail, 1ull); continue; }\n"
+       "    g_T[p] = T;\n"
+       "    const double lnT = pdm::log(T, s_log);\n    const double invT = pdm::rcp(T);\n"
+       "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
+  Src r;
+  emit_species_forward(r, m, C);
+  if (has_plog(m))
+    r << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lit((double)logl(R_GAS)) << ";\n";
+  g_acc.mem = false;
+  emit_acc_init(r, "w", N);
+  for (auto& grp : reaction_groups(m)) emit_reaction_group(r, m, grp);
+  s << r.o.str();
+  s << "    const double hh = 0.5 * dt * pdm::rcp(rho);\n";
+  for (int k = 0; k < N; ++k)
+    s << "    g_b[(i64)" << k << " * cnt + q] = (g_c[(i64)" << k << " * cnt + p] + (hh * " << lit(m.species[k].W)
+      << ") * w" << k << ") - __ldg(Yp + (i64)" << k << " * n);\n";
+  s << "  }\n}\n";
 }
 
 // ---------------------------------------------------------------------------
@@ -1895,6 +1963,7 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, cons
     emit_tsolve(d, m, C, opt, dummy);
     emit_jacobian_kernel(d, m, C, opt.deriv_block, &ns2, JacMode::CN);
     emit_cn_kernels(d, m, C);
+    emit_cn_residual_kernel(d, m, C);
     out.group_sources["cn"] = d.o.str();
     const int half = (N + 1) / 2, lda = half % 2 == 1 ? 2 * half : 2 * half + 2;   // CN_LDA
     out.smem_dyn_bytes_cn_solve = kCnGroup * (2 * N * 8 + N * lda * 4 + 4 * N * 4);

@@ -10,6 +10,7 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -182,6 +183,8 @@ struct Options {
   bool warp = false;      // net production rates: warp per state (table-driven) instead of thread per state
   int exp_ops = 4;        // exponential flavour (4 or 2 FP64 ops)
   bool exp_call = false;  // exponential as a called function
+  bool cn_chord = false;  // Crank-Nicolson: keep a factorisation for several iterations (chord) instead of full Newton
+  int cn_refresh = 4;     // chord: re-assemble and re-factor every cn_refresh-th iteration
 };
 
 bool parse_options(const char* s, Options& o, std::string& err) {
@@ -207,6 +210,8 @@ bool parse_options(const char* s, Options& o, std::string& err) {
       else if (v == "4call") { o.exp_ops = 4; o.exp_call = true; }
       else { err = "exp=2|4|2call|4call"; return false; }
     }
+    else if (k == "cn_refresh") { o.cn_refresh = std::atoi(v.c_str()); if (o.cn_refresh < 1 || o.cn_refresh > 1000) { err = "cn_refresh must be in [1, 1000]"; return false; } }
+    else if (k == "cn_newton") { if (v == "full") o.cn_chord = false; else if (v == "chord") o.cn_chord = true; else { err = "cn_newton=full|chord"; return false; } }
     else if (k == "variant") { if (v == "thread") o.warp = false; else if (v == "warp") o.warp = true; else { err = "variant=thread|warp"; return false; } }
     else if (k == "store") { if (v == "auto") o.store = 0; else if (v == "shared") o.store = 1; else if (v == "global") o.store = 2; else { err = "store=auto|shared|global"; return false; } }
     else if (k == "deriv_block") { o.deriv_block = std::atoi(v.c_str()); if (o.deriv_block < 32 || o.deriv_block > 256 || o.deriv_block % 32) { err = "deriv_block must be a multiple of 32 in [32, 256]"; return false; } }
@@ -239,6 +244,7 @@ struct pyro_mech {
     double* store = nullptr;   // per-block species arrays of this group (large mechanisms)
     std::map<std::string, CUfunction> fn;   // further kernels of the group
     int solve_blocks_per_sm = 0;            // Crank-Nicolson batched solve
+    int residual_blocks_per_sm = 0;         // Crank-Nicolson right-hand side (chord iterations)
     int block = 0;                          // threads per block (0: the derivative block size)
     int smem = -1;                          // dynamic shared memory (-1: the derivative kernels')
   };
@@ -521,7 +527,7 @@ int ensure_groups(pyro_mech* h, const std::vector<std::string>& names) {
       if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("species-array store allocation: ") + cudaGetErrorString(e));
     }
     if (todo[i] == "cn") {
-      for (const char* nm : {"pyro_cn_prep", "pyro_cn_solve", "pyro_cn_finish"}) {
+      for (const char* nm : {"pyro_cn_prep", "pyro_cn_solve", "pyro_cn_finish", "pyro_cn_residual"}) {
         CUfunction f = nullptr;
         r = d.ModuleGetFunction(&f, G.module, nm);
         if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, std::string("missing kernel ") + nm);
@@ -535,6 +541,13 @@ int ensure_groups(pyro_mech* h, const std::vector<std::string>& names) {
       if (r != CUDA_SUCCESS || sb < 1) return fail(PYRO_ECUDA, "pyro_cn_solve does not fit on an SM");
       G.solve_blocks_per_sm = sb;
       h->emitted.stats["cn_solve_blocks_per_sm"] = sb;
+      const int rsm = 2 * h->m.n_species() * h->opt.deriv_block * (int)sizeof(double);
+      r = d.FuncSetAttribute(G.fn["pyro_cn_residual"], CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, rsm);
+      if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "shared memory request (Crank-Nicolson residual): " + cu_err(r));
+      int rb = 0;
+      r = d.Occupancy(&rb, G.fn["pyro_cn_residual"], h->opt.deriv_block, rsm);
+      if (r != CUDA_SUCCESS || rb < 1) return fail(PYRO_ECUDA, "pyro_cn_residual does not fit on an SM");
+      G.residual_blocks_per_sm = rb;
     }
     h->emitted.stats[todo[i] + "_cubin_bytes"] = (double)cubins[i].size();
   }
@@ -971,10 +984,22 @@ namespace {
 // per state): at most 8 GiB, a multiple of the matrix group size.  Chunks run one
 // after another and each ends in a tail of slowly converging states that keeps
 // only a few warps busy, so fewer, larger chunks are faster.
-int64_t cn_chunk(const pyro_mech* h, int64_t n) {
+// FP32 words per state of the kept factorisation (chord iterations): LU rows of
+// the solve kernel's leading dimension, pivots, row exponents.
+int64_t cn_fac_words(const pyro_mech* h) {
   const int64_t N = h->m.n_species();
+  const int64_t half = (N + 1) / 2, lda = half % 2 == 1 ? 2 * half : 2 * half + 2;
+  return N * lda + 2 * N;
+}
+
+size_t cn_bytes_per_state(const pyro_mech* h) {
+  const int64_t N = h->m.n_species();
+  return (size_t)(N * N + 2 * N + 3) * sizeof(double) + (h->opt.cn_chord ? (size_t)cn_fac_words(h) * 4 : 0);
+}
+
+int64_t cn_chunk(const pyro_mech* h, int64_t n) {
   const int64_t Gs = pyro::kCnGroup;
-  const size_t per_state = (size_t)(N * N + 2 * N + 3) * sizeof(double);
+  const size_t per_state = cn_bytes_per_state(h);
   int64_t m = std::max<int64_t>(4096, (int64_t)(((size_t)8 << 30) / per_state));
   m = std::min<int64_t>(m, (n + Gs - 1) / Gs * Gs);
   return (m + Gs - 1) / Gs * Gs;
@@ -987,7 +1012,8 @@ int cn_reserve(pyro_mech* h, int64_t n) {
   const int64_t m = cn_chunk(h, n);
   if (int rc = ensure_jac_scratch(h, h->groups["cn"], m)) return rc;
   std::lock_guard<std::mutex> lock(h->mu);
-  const size_t bytes = (size_t)m * (size_t)(N * N + 2 * N + 3) * sizeof(double) + 4 * sizeof(int);
+  const size_t bytes = (size_t)m * cn_bytes_per_state(h) + 64;   // + counters and alignment
+  (void)N;
   if (bytes > h->cn_bytes) {
     if (h->d_cn) cudaFree(h->d_cn);
     h->d_cn = nullptr;
@@ -1017,6 +1043,8 @@ int cn_run(pyro_mech* h, int64_t cnt, int64_t ld, double dt, const double* rho, 
   int* dit = dstate + m;                         // [m]
   int* dlist[2] = {dit + m, dit + 2 * m};        // active-state lists [m], built alternately
   int* dcount[2] = {dit + 3 * m, dit + 3 * m + 1};
+  float* dfac = h->opt.cn_chord ? (float*)(dcount[1] + 1) : nullptr;   // [m][fac words] (chord)
+  if (dfac) dfac = (float*)(((uintptr_t)dfac + 15) & ~(uintptr_t)15);
   Driver& d = driver();
   const int bd = h->opt.deriv_block;
   double Tg_tol = 1e-10;
@@ -1034,16 +1062,28 @@ int cn_run(pyro_mech* h, int64_t cnt, int64_t ld, double dt, const double* rho, 
     CUresult r = d.LaunchKernel(G.fn.at("pyro_cn_prep"), gs, 1, 1, bd, 1, 1, 0, as_stream(stream), pp, nullptr);
     if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
     unsigned gsolve = (unsigned)std::min<int64_t>((nc + Gs - 1) / Gs, (int64_t)h->num_sms * G.solve_blocks_per_sm);
+    const bool chord = h->opt.cn_chord;
+    unsigned gres = (unsigned)std::min<int64_t>((nc + bd - 1) / bd, (int64_t)h->num_sms * G.residual_blocks_per_sm);
+    const unsigned rsm = (unsigned)(2 * N * bd * sizeof(double));
     for (int it = 0; it <= max_newton; ++it) {
       int* li = dlist[it & 1];
       int* lo = dlist[(it + 1) & 1];
       int* ci = dcount[it & 1];
       int* co = dcount[(it + 1) & 1];
-      void* pa[] = {&nc, &nld, &rho_c, &de, &Yout_c, &dc, &Tout_c, &dstate, &dt, &t_iter, &Tg_tol, &dA, &db,
-                    &h->d_jac_scratch, &h->d_fail, &li, &ci, &co};
-      if (int rc = launch_deriv(h, G, nc, stream, pa)) return rc;
+      int mode = chord ? (it % h->opt.cn_refresh == 0 ? 1 : 2) : 0;
+      int a_at_state = chord ? 1 : 0;
+      if (mode == 2) {   // chord: right-hand side only, the first iterate's matrix is kept
+        void* pr[] = {&nc, &nld, &rho_c, &de, &Yout_c, &dc, &Tout_c, &dstate, &dt, &t_iter, &Tg_tol, &db,
+                      &h->d_fail, &li, &ci, &co};
+        r = d.LaunchKernel(G.fn.at("pyro_cn_residual"), gres, 1, 1, bd, 1, 1, rsm, as_stream(stream), pr, nullptr);
+        if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
+      } else {
+        void* pa[] = {&nc, &nld, &rho_c, &de, &Yout_c, &dc, &Tout_c, &dstate, &dt, &t_iter, &Tg_tol, &dA, &db,
+                      &h->d_jac_scratch, &h->d_fail, &li, &ci, &co, &a_at_state};
+        if (int rc = launch_deriv(h, G, nc, stream, pa)) return rc;
+      }
       void* ps[] = {&nc, &nld, &dA, &db, &Yout_c, &dstate, &dit, &tol, &max_newton, &refine, &h->d_fail,
-                    &li, &ci, &lo, &co};
+                    &li, &ci, &lo, &co, &mode, &dfac};
       r = d.LaunchKernel(G.fn.at("pyro_cn_solve"), gsolve, 1, 1, 32 * pyro::kCnGroup, 1, 1,
                          h->emitted.smem_dyn_bytes_cn_solve, as_stream(stream), ps, nullptr);
       if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));

@@ -186,3 +186,52 @@ def test_cn_step_full_size_sampled(mechs, dev):
     assert bad == 0
     assert np.max(np.abs(Y1[:, ii].cpu().numpy() - Yo)) <= TOL_Y
     assert np.max(np.abs(T1[ii].cpu().numpy() - To) / To) <= TOL_T
+
+
+# --- chord variant (the first iterate's factorisation kept for the whole step) ---------
+
+@pytest.fixture(scope="module")
+def chord(mech_files, dev):
+    from paper_2503_24286_gb300 import binding as B
+    paths, _ = mech_files
+    out = {}
+    for i in (0, 1):
+        m = B.Mechanism(paths[i], "cn_newton=chord")
+        m.prepare("cn")
+        out[i] = (m, O.Oracle(paths[i]))
+    return out
+
+
+@pytest.mark.parametrize("idx,mi,n", [(6, 0, 131), (5, 1, 24)])
+def test_cn_chord_matches_oracle(chord, dev, idx, mi, n):
+    """The chord iteration converges to the same Crank-Nicolson step as the oracle's
+    full Newton (same residual, same stop rule; more iterations)."""
+    m, orc = chord[mi]
+    st, rho, dt = _cn_case(idx, n, orc)
+    Yo, To, ito, bad = orc.cn_step(dt, rho, st.T, st.Y)
+    assert bad == 0
+    T1, Y1, it = m.cn_step(dt, _t(rho, dev), _t(st.T, dev), _t(st.Y, dev), max_newton=60, with_iters=True)
+    T1, Y1, it = T1.cpu().numpy(), Y1.cpu().numpy(), it.cpu().numpy()
+    assert np.all(it > 0) and m.nonconverged() == 0
+    assert np.max(np.abs(Y1 - Yo)) <= TOL_Y
+    assert np.max(np.abs(T1 - To) / To) <= TOL_T
+    assert np.all(it >= ito - 1)
+
+
+def test_cn_chord_full_size(chord, dev):
+    m, orc = chord[1]
+    cfg = synth.CONFIGS[5]
+    n = cfg["n_points"]
+    T0, p, Y = synth.generate_states_torch(53, n, cfg["T"], cfg["p_atm"], synth.STATE_SEED_BASE + 5, dev)
+    rho = m.density(p, T0, Y)
+    e0 = m.internal_energy(T0, Y)
+    T1, Y1, it = m.cn_step(cfg["dt"], rho, T0, Y, max_newton=60, with_iters=True)
+    assert (it > 0).all().item() and m.nonconverged() == 0
+    assert (Y1.sum(0) - Y.sum(0)).abs().max().item() <= 1e-13
+    e1 = m.internal_energy(T1, Y1)
+    assert ((e1 - e0).abs() <= 1e-12 * e0.abs() + 1e-6).all().item()
+    idx = np.array([0, 4097, n - 1])
+    ii = torch.tensor(idx, device=dev)
+    Yo, To, ito, bad = orc.cn_step(cfg["dt"], rho[ii].cpu().numpy(), T0[ii].cpu().numpy(), Y[:, ii].cpu().numpy())
+    assert bad == 0
+    assert np.max(np.abs(Y1[:, ii].cpu().numpy() - Yo)) <= TOL_Y
