@@ -316,6 +316,10 @@ std::string product_expr(Src& s, const std::vector<std::pair<int, int>>& side) {
 }
 
 // ln of the Arrhenius part of k~ minus species terms: emits "double x = ..."
+// With folded: the reactant sum sum nu'_i L_i is the variable nuL in scope (formed
+// from per-reaction folded coefficients) instead of per-species shared entries.
+bool g_fold = false;
+
 void emit_arg(Src& s, const Mechanism& m, const Reaction& r, double A, double b, double theta,
               const std::string& var) {
   long double lnA = logl((long double)A);
@@ -323,6 +327,7 @@ void emit_arg(Src& s, const Mechanism& m, const Reaction& r, double A, double b,
   s << "      double " << var << " = fma(" << lit(b) << ", lnT, " << lit((double)lnA) << ");";
   s << " " << var << " = fma(" << lit(-theta) << ", invT, " << var << ");";
   s.fma(2);
+  if (g_fold) { s << " " << var << " -= nuL;\n"; return; }
   for (auto& p : r.reactants) {
     if (p.second == 1) { s << " " << var << " -= sL" << sidx(p.first) << ";"; s.add(); }
     else { s << " " << var << " = fma(" << lit(-(double)p.second) << ", sL" << sidx(p.first) << ", " << var << ");"; s.fma(); }
@@ -366,7 +371,8 @@ void emit_plog_arg(Src& s, const Mechanism& m, const Reaction& r, const std::str
        "      const double pf = fmin(fmax(pfu, 0.0), 1.0);\n"
        "      double " << var << " = fma(pf, pxb - pxa, pxa);";
   s.fma(5); s.add(3); s.mul(1); s.add(2 + (n > 2 ? n - 2 : 0));
-  for (auto& p : r.reactants) {
+  if (g_fold) s << " " << var << " -= nuL;";
+  else for (auto& p : r.reactants) {
     if (p.second == 1) { s << " " << var << " -= sL" << sidx(p.first) << ";"; s.add(); }
     else { s << " " << var << " = fma(" << lit(-(double)p.second) << ", sL" << sidx(p.first) << ", " << var << ");"; s.fma(); }
   }
@@ -597,8 +603,8 @@ void emit_species_deriv(Src& s, const Mechanism& m, const std::vector<SpeciesCoe
     s << "      const double Lp = fma(-hr, invT, invT);\n";
     s << "      const double E = PEXP(q, s_exp);\n";
     s << "      const double a = E * (rho * y);\n";
-    s << "      sL" << sidx(k) << " = q; sA" << sidx(k) << " = a;";
-    if (mode == DMode::JAC) s << " sE" << sidx(k) << " = E * rho; sLp" << sidx(k) << " = Lp;";
+    if (mode == DMode::JAC) s << "      (void)Lp; sA" << sidx(k) << " = a; sE" << sidx(k) << " = E * rho;";
+    else s << "      sL" << sidx(k) << " = q; sA" << sidx(k) << " = a;";
     if (mode == DMode::VJP) s << " sLp" << sidx(k) << " = Lp; sC" << sidx(k) << " = 0.0;";
     if (mode == DMode::JVP) {
       s << "\n      const double dy = __ldg(dYp + (i64)" << k << " * n);\n";
@@ -881,9 +887,44 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
   }
   *nslots = sl.n;
   auto slot = [&](int q) { return "W[" + std::to_string(q) + " * BLKD]"; };
+  // Per reaction, folded at emit time (species share T_mid): the reactant sum
+  // sum_i nu'_i L_i (coefficients of lnT, 1/T, 1, T, .., T^4) and, for
+  // dS = sum_i c_i L'_i = (sum_i c_i - sum_i c_i h_i/RT)/T with c_i = nu'_i - nu''_i,
+  // the polynomial sum_i c_i h_i/RT (1, T, .., T^4, 1/T) -- per NASA range.  Only
+  // two per-state arrays (activities a_i and E_i rho) stay in shared memory.
+  s << "\n__device__ const double pyro_jfold_" << (int)mode << "[" << 26 * std::max(M, 1) << "] = {";
+  int qf = 0;
+  std::vector<long double> fold_c(M);
+  for (int j = 0; j < M; ++j) {
+    const Reaction& r = m.reactions[j];
+    std::set<int> sp;
+    for (auto& p : r.reactants) sp.insert(p.first);
+    if (r.reversible) for (auto& p : r.products) sp.insert(p.first);
+    long double csum = 0;
+    for (int rg = 0; rg < 2; ++rg) {
+      long double nl[7] = {0, 0, 0, 0, 0, 0, 0}, hh[6] = {0, 0, 0, 0, 0, 0};
+      for (auto& p : r.reactants) {
+        const SpeciesCoef& c = C[p.first];
+        long double v = p.second;
+        nl[0] += v * c.cl[rg]; nl[1] += v * c.ci[rg]; nl[2] += v * c.c0[rg]; nl[3] += v * c.c1[rg];
+        nl[4] += v * c.c2[rg]; nl[5] += v * c.c3[rg]; nl[6] += v * c.c4[rg];
+      }
+      for (int i : sp) {
+        long double ci = nu_of(r.reactants, i) - (r.reversible ? nu_of(r.products, i) : 0);
+        if (rg == 0) csum += ci;
+        for (int q = 0; q < 6; ++q) hh[q] += ci * C[i].h[rg][q];
+      }
+      for (int q = 0; q < 7; ++q) s << (qf++ ? "," : "") << lit((double)nl[q]);
+      for (int q = 0; q < 6; ++q) s << "," << lit((double)hh[q]), ++qf;
+    }
+    fold_c[j] = csum;
+  }
+  if (qf == 0) s << "0.0";
+  s << "};\n";
+  const std::string ftab = "pyro_jfold_" + std::to_string((int)mode);
   const char* prologue =
       "  __shared__ double s_exp[512];\n  __shared__ double s_log[256];\n  extern __shared__ double s_dyn[];\n"
-      "  double* sL = s_dyn; double* sA = sL + NSP * BLKD; double* sE = sA + NSP * BLKD; double* sLp = sE + NSP * BLKD;\n"
+      "  double* sA = s_dyn; double* sE = sA + NSP * BLKD;\n"
       "  pyro_load_tables(s_exp, s_log);\n  __syncthreads();\n  const int t = threadIdx.x;\n";
   if (mode == JacMode::TY) {
     s << "\n// Dense Jacobian d(Tdot, omega)/d(T, Y) at fixed rho, [(N+1)^2][n]; row 0 = Tdot of the adiabatic\n"
@@ -941,20 +982,24 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
   if (has_plog(m))
     s << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lit((double)logl(R_GAS)) << ";\n";
   // ---- phase 1
+  s << "    const int fr = hi ? 13 : 0;\n";
   for (int j = 0; j < M; ++j) {
     const Reaction& r = m.reactions[j];
     s << "    { // reaction " << j << "\n";
+    s << "      const double* fj = " << ftab << " + " << 26 * j << " + fr;\n"
+         "      const double nuL = fma(__ldg(fj), lnT, fma(__ldg(fj + 1), invT, fma(T, fma(T, fma(T, fma(T, __ldg(fj + 6), "
+         "__ldg(fj + 5)), __ldg(fj + 4)), __ldg(fj + 3)), __ldg(fj + 2))));\n";
+    g_fold = true;
     emit_reaction_core(s, m, r);
-    // S' - S'' = sum_i (nu'_i - nu''_i) L'_i
-    s << "      double dS = 0.0;";
+    g_fold = false;
     std::set<int> sp;
     for (auto& p : r.reactants) sp.insert(p.first);
     if (r.reversible) for (auto& p : r.products) sp.insert(p.first);
-    for (int i : sp) {
-      int c = nu_of(r.reactants, i) - (r.reversible ? nu_of(r.products, i) : 0);
-      if (c) s << " dS = fma(" << lit((double)c) << ", sLp" << sidx(i) << ", dS);";
-    }
-    s << "\n      " << slot(sl.R[j]) << " = R; " << slot(sl.Rt[j]) << " = kk * fma(D, tau, Pr * dS);\n";
+    // S' - S'' = sum_i (nu'_i - nu''_i) L'_i, L'_i = (1 - h_i/RT)/T, from the folded polynomial
+    s << "      const double Hj = fma(__ldg(fj + 12), invT, fma(T, fma(T, fma(T, fma(T, __ldg(fj + 11), __ldg(fj + 10)), "
+         "__ldg(fj + 9)), __ldg(fj + 8)), __ldg(fj + 7)));\n"
+         "      const double dS = (" << lit((double)fold_c[j]) << " - Hj) * invT;\n";
+    s << "      " << slot(sl.R[j]) << " = R; " << slot(sl.Rt[j]) << " = kk * fma(D, tau, Pr * dS);\n";
     if (sl.RM[j] >= 0) s << "      " << slot(sl.RM[j]) << " = kM * D;\n";
     auto fr = side_factors(r.reactants);
     auto fp = side_factors(r.products);
@@ -992,7 +1037,7 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
         << "); cp = fma(T, cp, " << sel(p1) << "); cp = fma(T, cp, " << sel(p0) << ");\n";
       s << "      sA" << sidx(i) << " = fma(RT, hr, -RT) * " << lit(1.0 / m.species[i].W) << ";\n";
       s << "      cv = fma(y * " << lit((double)R_GAS / m.species[i].W) << ", cp - 1.0, cv);\n";
-      s << "      sL" << sidx(i) << " = rho * " << lit(1.0 / m.species[i].W) << "; }\n";
+      s << "      sE" << sidx(i) << " = rho * " << lit(1.0 / m.species[i].W) << "; }\n";
     }
     s << "    const double mrcv = -pdm::rcp(cv);\n";
     s << "    #pragma unroll 1\n    for (int i = 0; i < NSP; ++i) sA[i * BLKD + t] *= mrcv;\n";
@@ -1033,9 +1078,9 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
       // a fresh opaque stride per row keeps the compiler from holding all N^2 offsets live
       if (mode != JacMode::CN) s << "      const i64 nr = opq(n);\n";
       s << "      double* Jr = Jp + (i64)" << k * N << " * nr;\n";
-      s << "      #pragma unroll 1\n      for (int i = 0; i < NSP; ++i) Jr[(i64)i * nr] = fma(sL[i * BLKD + t], fu, fj * sA[i * BLKD + t]);\n";
+      s << "      #pragma unroll 1\n      for (int i = 0; i < NSP; ++i) Jr[(i64)i * nr] = fma(sE[i * BLKD + t], fu, fj * sA[i * BLKD + t]);\n";
       for (int i = 0; i < N; ++i) {
-        std::string si = "sL" + sidx(i), ti = "sA" + sidx(i);
+        std::string si = "sE" + sidx(i), ti = "sA" + sidx(i);
         std::string dst = "Jr[(i64)" + std::to_string(i) + " * nr]";
         bool hs = acc.count(i), hc = cr.count(i), diag = mode == JacMode::CN && i == k;
         if (hs || hc) {
@@ -1063,7 +1108,7 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
   // The barrier keeps the compiler from forwarding phase-1 values through registers.
   s << "    asm volatile(\"\" ::: \"memory\");\n";
   for (int i = 0; i < N; ++i)
-    s << "    sL" << sidx(i) << " = rho * " << lit(1.0 / m.species[i].W) << "; sA" << sidx(i) << " = 0.0;\n";
+    s << "    sE" << sidx(i) << " = rho * " << lit(1.0 / m.species[i].W) << "; sA" << sidx(i) << " = 0.0;\n";
   s << "    const double RT = " << lit((double)R_GAS) << " * T;\n";
   s << "    double sum_ew = 0.0, sum_cpw = 0.0, sum_ejt = 0.0, U = 0.0;\n";
   // per-species row lists
@@ -1105,9 +1150,9 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
     s << "      const double eh = fma(RT, hr, -RT); const double cpm = " << lit((double)R_GAS) << " * (cp - 1.0);\n";
     s << "      sum_ew = fma(eh, w, sum_ew); sum_cpw = fma(cpm, w, sum_cpw); sum_ejt = fma(eh, jt, sum_ejt); U = fma(eh, u, U);\n";
     s << "      const i64 nr = opq(n);\n      double* Jr = Jp + (i64)" << (k + 1) * NP << " * nr;\n      Jr[0] = jt;\n";
-    s << "      #pragma unroll 1\n      for (int i = 0; i < NSP; ++i) Jr[(i64)(1 + i) * nr] = sL[i * BLKD + t] * u;\n";
+    s << "      #pragma unroll 1\n      for (int i = 0; i < NSP; ++i) Jr[(i64)(1 + i) * nr] = sE[i * BLKD + t] * u;\n";
     for (int i = 0; i < N; ++i) {
-      std::string si = "sL" + sidx(i);
+      std::string si = "sE" + sidx(i);
       std::string dst = "Jr[(i64)" + std::to_string(1 + i) + " * nr]";
       bool hs = acc.count(i), hc = cr.count(i);
       if (hs || hc) {
@@ -1130,14 +1175,21 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
     s << "      double cp = fma(T, " << sel(p4) << ", " << sel(p3) << "); cp = fma(T, cp, " << sel(p2)
       << "); cp = fma(T, cp, " << sel(p1) << "); cp = fma(T, cp, " << sel(p0) << ");\n";
     s << "      double cd = fma(T, " << sel(q3) << ", " << sel(q2) << "); cd = fma(T, cd, " << sel(q1) << "); cd = fma(T, cd, " << sel(q0) << ");\n";
-    s << "      cv = fma(yw, cp - 1.0, cv); cvT = fma(yw, cd, cvT);\n";
-    s << "      sE" << sidx(k) << " = (cp - 1.0) * " << lit((double)R_GAS / m.species[k].W) << "; }\n";
+    s << "      cv = fma(yw, cp - 1.0, cv); cvT = fma(yw, cd, cvT); }\n";
   }
   s << "    const double rcv = pdm::rcp(rho * cv);\n    const double Tdot = -sum_ew * rcv;\n"
        "    const double tcv = Tdot * pdm::rcp(cv);\n"
        "    Jp[0] = fma(-(sum_cpw + sum_ejt), rcv, -tcv * cvT);\n";
-  s << "    #pragma unroll 1\n    for (int i = 0; i < NSP; ++i) Jp[(i64)(1 + i) * n] = "
-       "fma(-fma(sL[i * BLKD + t], U, sA[i * BLKD + t]), rcv, -tcv * sE[i * BLKD + t]);\n";
+  // Tdot row: d c_v/dY_i = (cp_i/R - 1) R/W_i recomputed per entry
+  for (int k = 0; k < N; ++k) {
+    const SpeciesCoef& c = C[k];
+    double p4[2] = {c.cp[0][4], c.cp[1][4]}, p3[2] = {c.cp[0][3], c.cp[1][3]}, p2[2] = {c.cp[0][2], c.cp[1][2]};
+    double p1[2] = {c.cp[0][1], c.cp[1][1]}, p0[2] = {c.cp[0][0], c.cp[1][0]};
+    s << "    { double cp = fma(T, " << sel(p4) << ", " << sel(p3) << "); cp = fma(T, cp, " << sel(p2)
+      << "); cp = fma(T, cp, " << sel(p1) << "); cp = fma(T, cp, " << sel(p0) << ");\n"
+      << "      Jp[(i64)" << 1 + k << " * opq(n)] = fma(-fma(sE" << sidx(k) << ", U, sA" << sidx(k) << "), rcv, -tcv * ((cp - 1.0) * "
+      << lit((double)R_GAS / m.species[k].W) << ")); }\n";
+  }
   s << "  }\n}\n";
 }
 
@@ -1934,6 +1986,8 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, cons
     Src d; d << pre.o.str(); emit_jacobian_kernel(d, m, C, opt.deriv_block, &nslots); out.group_sources["jac"] = d.o.str();
   }
   out.jac_slots = nslots;
+  out.smem_dyn_bytes_jac = 2 * N * opt.deriv_block * (int)sizeof(double);
+  out.stats["jacobian_supported"] = common_tmid(m) ? 1 : 0;
   {
     int ns2 = 0;
     Src d; d << pre.o.str();

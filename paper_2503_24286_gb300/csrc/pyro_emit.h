@@ -33,6 +33,7 @@ struct EmitResult {
   int jac_slots = 0;                      // scratch doubles per point of the Jacobian kernel
   int smem_dyn_bytes_cn_solve = 0;        // dynamic shared memory of the Crank-Nicolson solve kernel
   int smem_dyn_bytes_transport = 0;       // dynamic shared memory of the transport kernel
+  int smem_dyn_bytes_jac = 0;             // dynamic shared memory of the Jacobian-type kernels
 };
 
 // Threads per block of the transport kernel (3 per-state arrays of N doubles in

@@ -512,6 +512,7 @@ int ensure_groups(pyro_mech* h, const std::vector<std::string>& names) {
     r = d.ModuleGetFunction(&G.f, G.module, group_kernel(todo[i]));
     if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, std::string("missing kernel ") + group_kernel(todo[i]));
     if (todo[i] == "tr") { G.block = pyro::kTransportBlock; G.smem = h->emitted.smem_dyn_bytes_transport; }
+    if (todo[i] == "jac" || todo[i] == "jad" || todo[i] == "cn") G.smem = h->emitted.smem_dyn_bytes_jac;
     const int smem = G.smem >= 0 ? G.smem : h->emitted.smem_dyn_bytes_deriv;
     const int blk = G.block > 0 ? G.block : h->opt.deriv_block;
     r = d.FuncSetAttribute(G.f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem);
@@ -918,6 +919,8 @@ int pyro_jacobian(const pyro_mech* hc, int64_t n, const double* rho, const doubl
                   double* J, void* stream) {
   pyro_mech* h = const_cast<pyro_mech*>(hc);
   if (!h || n < 0 || (n > 0 && (!rho || !T || !Y || !J))) return fail(PYRO_EINVAL, "pyro_jacobian: bad arguments");
+  if (h && h->emitted.stats["jacobian_supported"] <= 0)
+    return fail(PYRO_EINVAL, "the dense Jacobian kernels need all species to share one NASA-7 T_mid");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
   if (h->emitted.stats["deriv_store_global"] > 0)
@@ -962,6 +965,8 @@ int pyro_jacobian_adiabatic(const pyro_mech* hc, int64_t n, const double* rho, c
   pyro_mech* h = const_cast<pyro_mech*>(hc);
   if (!h || n < 0 || (n > 0 && (!rho || !T || !Y || !J)))
     return fail(PYRO_EINVAL, "pyro_jacobian_adiabatic: bad arguments");
+  if (h && h->emitted.stats["jacobian_supported"] <= 0)
+    return fail(PYRO_EINVAL, "the dense Jacobian kernels need all species to share one NASA-7 T_mid");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
   if (h->emitted.stats["deriv_store_global"] > 0)
@@ -1101,6 +1106,8 @@ int pyro_cn_step(const pyro_mech* hc, int64_t n, double dt, const double* rho, c
   pyro_mech* h = const_cast<pyro_mech*>(hc);
   if (!h || n < 0 || (n > 0 && (!rho || !T || !Y || !T_out || !Y_out)))
     return fail(PYRO_EINVAL, "pyro_cn_step: bad arguments");
+  if (h && h->emitted.stats["jacobian_supported"] <= 0)
+    return fail(PYRO_EINVAL, "the dense Jacobian kernels need all species to share one NASA-7 T_mid");
   if (!(dt >= 0.0) || !(tol > 0.0) || max_newton < 1 || max_newton > 1000)
     return fail(PYRO_EINVAL, "pyro_cn_step: need dt >= 0, tol > 0 and 1 <= max_newton <= 1000");
   if (n == 0) return PYRO_OK;
