@@ -922,10 +922,22 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
   if (qf == 0) s << "0.0";
   s << "};\n";
   const std::string ftab = "pyro_jfold_" + std::to_string((int)mode);
+  // the exp/log tables in global memory (read through L1 instead of staged in shared memory)
+  s << "__device__ const double pyro_tab_exp_g[512] = {";
+  for (int j = 0; j < 512; ++j) s << (j ? "," : "") << lit((double)exp2l((j + 0.5L) / 512.0L));
+  s << "};\n__device__ const double pyro_tab_log_g[256] = {";
+  for (int j = 0; j < 128; ++j) {
+    long double c = 1.0L + (j + 0.5L) / 128.0L;
+    s << (j ? "," : "") << lit((double)(1.0L / c)) << "," << lit((double)logl(c));
+  }
+  s << "};\n";
+  // exp/log tables read through L1: the 6 KB they would take in shared memory is
+  // what lets a fourth 64-thread block fit on an SM
   const char* prologue =
-      "  __shared__ double s_exp[512];\n  __shared__ double s_log[256];\n  extern __shared__ double s_dyn[];\n"
+      "  const double* __restrict__ s_exp = pyro_tab_exp_g;\n  const double* __restrict__ s_log = pyro_tab_log_g;\n"
+      "  extern __shared__ double s_dyn[];\n"
       "  double* sA = s_dyn; double* sE = sA + NSP * BLKD;\n"
-      "  pyro_load_tables(s_exp, s_log);\n  __syncthreads();\n  const int t = threadIdx.x;\n";
+      "  const int t = threadIdx.x;\n";
   if (mode == JacMode::TY) {
     s << "\n// Dense Jacobian d(Tdot, omega)/d(T, Y) at fixed rho, [(N+1)^2][n]; row 0 = Tdot of the adiabatic\n"
          "// isochoric reactor, rows 1..N = omega; column 0 = T, columns 1..N = Y.  Phase 1 writes the\n"
