@@ -179,7 +179,9 @@ int pyro_vjp(const pyro_mech* mech, int64_t n, const double* rho, const double* 
  * J: [(N+1)*(N+1)][n], entry (r, c) at J[(r*(N+1) + c)*n + p]; row 0 = Tdot,
  * row 1+k = omega_k; column 0 = T, column 1+i = Y_i.  The library keeps a
  * per-handle scratch buffer for the per-reaction partials (allocated on first
- * use, grown as needed). */
+ * use, grown as needed): calls on one handle that use it (pyro_jacobian,
+ * pyro_jacobian_adiabatic, pyro_cn_step) must not overlap on the GPU.  Needs
+ * all species to share one NASA-7 T_mid. */
 int pyro_jacobian(const pyro_mech* mech, int64_t n, const double* rho, const double* T, const double* Y,
                   double* J, void* stream);
 
@@ -208,8 +210,10 @@ int pyro_jacobian_adiabatic(const pyro_mech* mech, int64_t n, const double* rho,
  * t^m + dt (may alias T and Y); iters_out: nullable int32 [n], Newton steps
  * taken or -1 where the step failed (no convergence, singular matrix or a
  * failed temperature solve; counted by pyro_nonconverged).
- * Work arrays (about 8 (N^2 + 2N + 3) bytes per state, in chunks of at most
- * 8 GiB) are allocated on first use and kept by the handle.  Returns
+ * Work arrays (about 8 (N^2 + 2N + 3) bytes per state, plus the kept FP32
+ * factors with cn_newton=chord, in chunks of at most 8 GiB) are allocated on
+ * first use and kept by the handle; calls on one handle must not overlap on the
+ * GPU.  Returns
  * PYRO_EINVAL for dt < 0, tol <= 0 or max_newton outside [1, 1000]. */
 int pyro_cn_step(const pyro_mech* mech, int64_t n, double dt, const double* rho, const double* T,
                  const double* Y, double tol, int max_newton, double* T_out, double* Y_out,
