@@ -143,6 +143,11 @@ def test_missing_file_and_bad_options(tmp_path, mech_files):
     with pytest.raises(B.PyroError) as ei:
         B.Mechanism(mech_files[0][0], "device=0;frobnicate=1")
     assert ei.value.code == B.PYRO_EINVAL
+    for bad in ("cn_newton=quasi", "cn_refresh=0", "cn_refresh=5000"):
+        with pytest.raises(B.PyroError) as ei:
+            B.Mechanism(mech_files[0][0], "device=0;" + bad)
+        assert ei.value.code == B.PYRO_EINVAL
+    B.Mechanism(mech_files[0][0], "device=0;cn_newton=chord;cn_refresh=8").close()
 
 
 def test_cp_margin_validation(tmp_path):
