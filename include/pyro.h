@@ -30,6 +30,11 @@
  *     before anything is launched.  pyro_last_error() gives the message of the
  *     calling thread's last failure.
  *   - n == 0 is a no-op that returns PYRO_OK.
+ *   - A handle keeps per-handle work arrays (Jacobian partials, Crank-Nicolson
+ *     work arrays, staging buffers of host-pointer calls) and compiles kernel
+ *     groups on first use: calls on one handle from several host threads, or
+ *     on several streams at once, must be serialised by the caller.  Separate
+ *     handles are independent.
  */
 #ifndef PYRO_H
 #define PYRO_H
