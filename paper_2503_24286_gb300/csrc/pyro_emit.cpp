@@ -1277,29 +1277,44 @@ void emit_transport_kernel(Src& s, const Mechanism& m, int blk, bool gstore) {
   s << "    if (g_kappa) g_kappa[p] = 0.5 * sqT * (ka + pdm::rcp(kh));\n";
   s << R"(    if (g_mu) {
       double mu = 0.0;
+      // two rows k, k+1 per pass: each X_j, X_j/P_j, X_j/P_j^2 load feeds six
+      // independent FMA chains (the three Wilke products of both rows)
+      int k = 0;
       #pragma unroll 1
-      for (int k = 0; k < NSP; ++k) {
+      for (; k + 1 < NSP; k += 2) {
         const double* c0 = pyro_tr_wilke + k * NSP;
         const double* c1 = c0 + NSP * NSP;
         const double* c2 = c1 + NSP * NSP;
-        // two independent partial sums per product (even / odd j) for the FP64 pipe
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0;
-        int j = 0;
         #pragma unroll 2
-        for (; j + 1 < NSP; j += 2) {
+        for (int j = 0; j < NSP; ++j) {
+          const double xj = sX[j * BLKD + t], vj = sV[j * BLKD + t], wj = sW[j * BLKD + t];
+          a0 = fma(__ldg(c0 + j), xj, a0);
+          a1 = fma(__ldg(c1 + j), vj, a1);
+          a2 = fma(__ldg(c2 + j), wj, a2);
+          b0 = fma(__ldg(c0 + NSP + j), xj, b0);
+          b1 = fma(__ldg(c1 + NSP + j), vj, b1);
+          b2 = fma(__ldg(c2 + NSP + j), wj, b2);
+        }
+        #pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const double* bk = pyro_tr_visc + 5 * (k + r);
+          double Pk = fma(L, __ldg(bk + 4), __ldg(bk + 3));
+          Pk = fma(L, Pk, __ldg(bk + 2)); Pk = fma(L, Pk, __ldg(bk + 1)); Pk = fabs(fma(L, Pk, __ldg(bk)));
+          const double den = r == 0 ? fma(Pk, fma(Pk, a2, 2.0 * a1), a0) : fma(Pk, fma(Pk, b2, 2.0 * b1), b0);
+          mu = fma(sX[(k + r) * BLKD + t] * (Pk * Pk), pdm::rcp(den), mu);
+        }
+      }
+      if (k < NSP) {
+        const double* c0 = pyro_tr_wilke + k * NSP;
+        const double* c1 = c0 + NSP * NSP;
+        const double* c2 = c1 + NSP * NSP;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int j = 0; j < NSP; ++j) {
           a0 = fma(__ldg(c0 + j), sX[j * BLKD + t], a0);
           a1 = fma(__ldg(c1 + j), sV[j * BLKD + t], a1);
           a2 = fma(__ldg(c2 + j), sW[j * BLKD + t], a2);
-          b0 = fma(__ldg(c0 + j + 1), sX[(j + 1) * BLKD + t], b0);
-          b1 = fma(__ldg(c1 + j + 1), sV[(j + 1) * BLKD + t], b1);
-          b2 = fma(__ldg(c2 + j + 1), sW[(j + 1) * BLKD + t], b2);
         }
-        if (j < NSP) {
-          a0 = fma(__ldg(c0 + j), sX[j * BLKD + t], a0);
-          a1 = fma(__ldg(c1 + j), sV[j * BLKD + t], a1);
-          a2 = fma(__ldg(c2 + j), sW[j * BLKD + t], a2);
-        }
-        a0 += b0; a1 += b1; a2 += b2;
         const double* bk = pyro_tr_visc + 5 * k;
         double Pk = fma(L, __ldg(bk + 4), __ldg(bk + 3));
         Pk = fma(L, Pk, __ldg(bk + 2)); Pk = fma(L, Pk, __ldg(bk + 1)); Pk = fabs(fma(L, Pk, __ldg(bk)));
