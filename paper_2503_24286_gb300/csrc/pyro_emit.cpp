@@ -1326,12 +1326,45 @@ void emit_transport_kernel(Src& s, const Mechanism& m, int blk, bool gstore) {
     if (g_Dm) {
       #pragma unroll 1
       for (int k = 0; k < NSP; ++k) sV[k * BLKD + t] = 0.0;
-      const double* a = pyro_tr_pair;
+      // pairs {k, j}, j > k, in row order k: pyro_tr_pair + 5 (k (N-1) - k (k-1)/2 + j - k - 1);
+      // rows k and k+1 are taken together so that each X_j load and each update
+      // of the sum of species j serves two pairs
+      int k = 0;
       #pragma unroll 1
-      for (int k = 0; k < NSP - 1; ++k) {
+      for (; k + 1 < NSP - 1; k += 2) {
+        const double* a0p = pyro_tr_pair + 5 * (k * (NSP - 1) - k * (k - 1) / 2);   // pair (k, k+1)
+        const double* a1p = a0p + 5 * (NSP - 1 - k);                                // pair (k+1, k+2)
+        const double xk = sX[k * BLKD + t], xk1 = sX[(k + 1) * BLKD + t];
+        double sk, sk1;
+        {   // the pair (k, k+1)
+          double pk = fma(L, __ldg(a0p + 4), __ldg(a0p + 3));
+          pk = fma(L, pk, __ldg(a0p + 2)); pk = fma(L, pk, __ldg(a0p + 1)); pk = fma(L, pk, __ldg(a0p));
+          const double r = pdm::rcp(pk);
+          sk = fma(xk1, r, sV[k * BLKD + t]);
+          sk1 = fma(xk, r, sV[(k + 1) * BLKD + t]);
+        }
+        const double* a = a0p + 5;
+        const double* b = a1p;
+        #pragma unroll 2
+        for (int j = k + 2; j < NSP; ++j, a += 5, b += 5) {
+          double pa = fma(L, __ldg(a + 4), __ldg(a + 3));
+          double pb = fma(L, __ldg(b + 4), __ldg(b + 3));
+          pa = fma(L, pa, __ldg(a + 2)); pb = fma(L, pb, __ldg(b + 2));
+          pa = fma(L, pa, __ldg(a + 1)); pb = fma(L, pb, __ldg(b + 1));
+          pa = fma(L, pa, __ldg(a));     pb = fma(L, pb, __ldg(b));
+          const double ra = pdm::rcp(pa), rb = pdm::rcp(pb);
+          const double xj = sX[j * BLKD + t];
+          sk = fma(xj, ra, sk);
+          sk1 = fma(xj, rb, sk1);
+          sV[j * BLKD + t] = fma(xk, ra, fma(xk1, rb, sV[j * BLKD + t]));
+        }
+        sV[k * BLKD + t] = sk;
+        sV[(k + 1) * BLKD + t] = sk1;
+      }
+      for (; k < NSP - 1; ++k) {     // a last single row
+        const double* a = pyro_tr_pair + 5 * (k * (NSP - 1) - k * (k - 1) / 2);
         const double xk = sX[k * BLKD + t];
         double sk = sV[k * BLKD + t];
-        #pragma unroll 4
         for (int j = k + 1; j < NSP; ++j, a += 5) {
           double pk = fma(L, __ldg(a + 4), __ldg(a + 3));
           pk = fma(L, pk, __ldg(a + 2)); pk = fma(L, pk, __ldg(a + 1)); pk = fma(L, pk, __ldg(a));
