@@ -355,16 +355,37 @@ int64_t chunk_points(int64_t n, size_t bytes_per_point) {
   return std::min(m, n);
 }
 
+// Chunk sizes of a host-pointer call, each at most m points (one staging slot).
+// Large calls ramp up from m/8 at the start and down to m/8 at the end: nothing
+// overlaps the first copy-in and the last copy-out, so those stay short.
+std::vector<int64_t> chunk_plan(int64_t n, int64_t m) {
+  std::vector<int64_t> ramp, plan;
+  if (m >= 8 * 256)
+    for (int64_t a = m / 8; a < m; a *= 2) ramp.push_back((a + 255) / 256 * 256);
+  int64_t ends = 0;
+  for (int64_t a : ramp) ends += 2 * a;
+  if (ramp.empty() || n < ends + m) {
+    for (int64_t p = 0; p < n; p += m) plan.push_back(std::min(m, n - p));
+    return plan;
+  }
+  for (int64_t a : ramp) plan.push_back(a);
+  const int64_t mid = n - ends;
+  for (int64_t p = 0; p < mid; p += m) plan.push_back(std::min(m, mid - p));
+  for (auto it = ramp.rbegin(); it != ramp.rend(); ++it) plan.push_back(*it);
+  return plan;
+}
+
 // Run `launch(device pointers, points, stream)` over n points.  Device pointers:
 // one launch on the caller's stream.  Host pointers: chunks of points go through
 // kSlots staging slots, each with its own stream, so that the copy-in of chunk
-// c+1 and the copy-out of chunk c-1 overlap the kernel of chunk c; the kernels
-// themselves run one after another (event chain: they share per-block scratch).
-// A chunk of a [rows][n] array is a pitched 2D copy into a dense [rows][m]
-// staging array, so the kernel sees the chunk as a problem of m points.  The
-// call returns after the last copy-out has completed.
+// c+1 and the copy-out of chunk c-1 overlap the kernel of chunk c.  Kernels that
+// keep per-block scratch in global memory run one after another (event chain);
+// with `concurrent` (no such scratch) the kernel of chunk c+1 may start while
+// chunk c's last blocks still run.  A chunk of a [rows][n] array is a pitched 2D
+// copy into a dense [rows][m] staging array, so the kernel sees the chunk as a
+// problem of m points.  The call returns after the last copy-out has completed.
 template <class F>
-int with_args(pyro_mech* h, int64_t n, std::vector<ArgSpec> args, void* stream, F launch) {
+int with_args(pyro_mech* h, int64_t n, std::vector<ArgSpec> args, void* stream, F launch, bool concurrent = false) {
   std::vector<const void*> ptrs;
   for (auto& a : args) ptrs.push_back(a.host);
   int kind = classify(ptrs);
@@ -379,7 +400,8 @@ int with_args(pyro_mech* h, int64_t n, std::vector<ArgSpec> args, void* stream, 
   size_t per_point = 0;
   for (auto& a : args) if (a.host) per_point += (size_t)a.rows * a.elem;
   const int64_t m = chunk_points(n, per_point);
-  const int64_t n_chunks = (n + m - 1) / m;
+  const std::vector<int64_t> plan = chunk_plan(n, m);
+  const int64_t n_chunks = (int64_t)plan.size();
   const int slots = (int)std::min<int64_t>(pyro_mech::kSlots, n_chunks);
   for (int s = 0; s < slots; ++s)
     for (size_t i = 0; i < args.size(); ++i)
@@ -393,10 +415,11 @@ int with_args(pyro_mech* h, int64_t n, std::vector<ArgSpec> args, void* stream, 
   if (cudaEventRecord(h->pipe_start, (cudaStream_t)stream) != cudaSuccess) return fail(PYRO_ECUDA, "event record");
   for (int s = 0; s < slots; ++s)
     if (cudaStreamWaitEvent(h->pipe_stream[s], h->pipe_start, 0) != cudaSuccess) return drain(PYRO_ECUDA, "stream wait");
-  for (int64_t c = 0; c < n_chunks; ++c) {
+  int64_t p0 = 0;
+  for (int64_t c = 0; c < n_chunks; p0 += plan[c], ++c) {
     const int s = (int)(c % slots);
     cudaStream_t st = h->pipe_stream[s];
-    const int64_t p0 = c * m, nc = std::min(m, n - p0);
+    const int64_t nc = plan[c];
     for (size_t i = 0; i < args.size(); ++i) {
       if (!args[i].host) continue;
       dev[i] = h->stage[s][i];
@@ -406,10 +429,10 @@ int with_args(pyro_mech* h, int64_t n, std::vector<ArgSpec> args, void* stream, 
       cudaError_t e = copy_rows(dev[i], w, src, (size_t)n * args[i].elem, w, args[i].rows, cudaMemcpyHostToDevice, st);
       if (e != cudaSuccess) return drain(PYRO_ECUDA, std::string("H2D copy: ") + cudaGetErrorString(e));
     }
-    if (c > 0 && cudaStreamWaitEvent(st, h->pipe_kdone[(c - 1) % slots], 0) != cudaSuccess)
+    if (!concurrent && c > 0 && cudaStreamWaitEvent(st, h->pipe_kdone[(c - 1) % slots], 0) != cudaSuccess)
       return drain(PYRO_ECUDA, "stream wait");
     if (int rc = launch(dev, nc, (void*)st)) { for (int q = 0; q < slots; ++q) cudaStreamSynchronize(h->pipe_stream[q]); return rc; }
-    if (cudaEventRecord(h->pipe_kdone[s], st) != cudaSuccess) return drain(PYRO_ECUDA, "event record");
+    if (!concurrent && cudaEventRecord(h->pipe_kdone[s], st) != cudaSuccess) return drain(PYRO_ECUDA, "event record");
     for (size_t i = 0; i < args.size(); ++i) {
       if (!args[i].host || !args[i].out) continue;
       const size_t w = (size_t)nc * args[i].elem;
@@ -738,7 +761,7 @@ int pyro_density(const pyro_mech* hc, int64_t n, const double* p, const double* 
                      long long nn = nc;
                      void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3]};
                      return launch(h, h->f_density, nc, 8, 0, st, params);
-                   });
+                   }, true);
 }
 
 int pyro_internal_energy(const pyro_mech* hc, int64_t n, const double* T, const double* Y, double* e,
@@ -753,7 +776,7 @@ int pyro_internal_energy(const pyro_mech* hc, int64_t n, const double* T, const 
                      long long nn = nc;
                      void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3]};
                      return launch(h, h->f_energy, nc, 8, 0, st, params);
-                   });
+                   }, true);
 }
 
 int pyro_enthalpy(const pyro_mech* hc, int64_t n, const double* T, const double* Y, double* hm, double* cp,
@@ -768,7 +791,7 @@ int pyro_enthalpy(const pyro_mech* hc, int64_t n, const double* T, const double*
                      long long nn = nc;
                      void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3]};
                      return launch(h, h->f_enthalpy, nc, 8, 0, st, params);
-                   });
+                   }, true);
 }
 
 int pyro_temperature_enthalpy(const pyro_mech* hc, int64_t n, const double* hm, const double* Y,
@@ -787,7 +810,7 @@ int pyro_temperature_enthalpy(const pyro_mech* hc, int64_t n, const double* hm, 
                        int max_iter = 50;
                        void* params[] = {&nn, &d[0], &d[1], &d[2], &Tg, &max_iter, &tol, &d[3], &d[4], &h->d_fail};
                        return launch(h, h->f_temperature_h, nc, 8, 0, st, params);
-                     });
+                     }, true);
   if (rc) return rc;
   return maybe_checked(h, stream);
 }
@@ -816,7 +839,7 @@ int pyro_temperature(const pyro_mech* hc, int64_t n, const double* e, const doub
                        }
                        void* params[] = {&nn, &d[0], &d[1], &d[2], &Tg, &max_iter, &tol, &d[3], &d[4], &h->d_fail};
                        return launch(h, h->f_temperature, nc, 8, 0, st, params);
-                     });
+                     }, true);
   if (rc) return rc;
   return maybe_checked(h, stream);
 }
@@ -846,7 +869,7 @@ int pyro_net_production_rates(const pyro_mech* hc, int64_t n, const double* rho,
                                          &h->d_store};
                        return launch(h, h->f_omega, nc, h->omega_blocks_per_sm, h->emitted.smem_dyn_bytes_omega,
                                      st, params);
-                     });
+                     }, !h->warp && h->emitted.stats["omega_store_global"] <= 0);   // shared-memory variant: no scratch
   if (rc) return rc;
   return input_is_energy ? maybe_checked(h, stream) : PYRO_OK;
 }

@@ -193,9 +193,11 @@ def test_host_pointer_path_matches(mechs, dev):
 
 def test_host_pointer_pipeline_chunks(mechs, dev):
     """Host arrays larger than one staging chunk (65536 points) go through the
-    chunked copy/kernel pipeline: several chunks over the three staging slots and a
-    ragged last chunk, for [N][n] and [n] arrays, FP64 and int32 outputs; every
-    output equals the device-pointer call bit for bit."""
+    chunked copy/kernel pipeline: chunks ramping from 8192 points up to 65536 and
+    back down, over the three staging slots, with a ragged chunk, for [N][n] and [n]
+    arrays, FP64 and int32 outputs, with the chunks' kernels overlapping (forward,
+    temperature) or chained (Jacobian); every output equals the device-pointer
+    call bit for bit."""
     m, orc = mechs[0]
     n = 5 * 65536 + 37
     cfg = synth.CONFIGS[0]
@@ -209,8 +211,9 @@ def test_host_pointer_pipeline_chunks(mechs, dev):
     Th2, ith = m.temperature(he, hY, with_iters=True)
     assert np.array_equal(wh, wd.cpu().numpy()) and np.array_equal(Th, Td.cpu().numpy())
     assert np.array_equal(Th2, Tt.cpu().numpy()) and np.array_equal(ith, itd.cpu().numpy())
-    # Jacobian ([(N+1)^2][n] output) over a chunk boundary
-    nj = 2 * 65536 + 5
+    # Jacobian ([(N+1)^2][n] output; its kernels share per-block scratch, so the
+    # chunks' kernels run one after another) over ramped chunks and a ragged one
+    nj = 3 * 65536 + 5
     Jd = m.jacobian(rho[:nj].contiguous(), Td[:nj].contiguous(), Y[:, :nj].contiguous())
     Jh = m.jacobian(hr[:nj].copy(), np.ascontiguousarray(Th[:nj]), np.ascontiguousarray(hY[:, :nj]))
     assert np.array_equal(Jh, Jd.cpu().numpy())
