@@ -321,6 +321,56 @@ def large_mechanism_rates(synth, dev, stream, args, rank):
     return res
 
 
+def large_derivative_rates(synth, dev, stream, args, rank):
+    """The Jacobian-type kernels on the 160-species mechanism (rows from tables,
+    species arrays in the global scratch): dense 161 x 161 Jacobian and dS/dY at
+    fixed (rho, e) on 2^15 states, one Crank-Nicolson step of 2^14 states at
+    dt = 1e-46 s.  Off by default (the three units take minutes to compile)."""
+    import torch
+    from paper_2503_24286_gb300 import binding as B
+    d = tempfile.mkdtemp()
+    path = os.path.join(d, "mech4.txt")
+    synth.write_mechanism(synth.config_mechanism(4), path)
+    m = B.Mechanism(path)
+    m.prepare("jacobian,jacobian_adiabatic,cn")
+    cfg, ccfg = synth.CONFIGS[4], synth.CONFIGS[8]
+    n, nc = 2 ** 15, 2 ** 14
+    res = {"workload": "160 species / 1100 reactions; Jacobian and dS/dY on %d states (T ~ U[300, 2800] K), "
+                       "Crank-Nicolson on %d states (T ~ U[2000, 2800] K, dt = 1e-46 s)" % (n, nc)}
+    T, p, Y = synth.generate_states_torch(160, n, cfg["T"], cfg["p_atm"], synth.STATE_SEED_BASE + 4 + 7919 * rank, dev)
+    rho = m.density(p, T, Y)
+    J = torch.empty((161 * 161, n), dtype=torch.float64, device=dev)
+    Ja = torch.empty((160 * 160, n), dtype=torch.float64, device=dev)
+
+    def timed(fn, steps=3):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return max_over_ranks(e0.elapsed_time(e1) / steps, dev)
+
+    ms = timed(lambda: m.jacobian(rho, T, Y, out=J))
+    res.update(jacobian_ms=ms, jacobian_per_s=n / (ms * 1e-3), jacobian_out_GB_per_s=J.numel() * 8 / (ms * 1e6))
+    ms = timed(lambda: m.jacobian_adiabatic(rho, T, Y, out=Ja))
+    res.update(jacobian_adiabatic_ms=ms, jacobian_adiabatic_per_s=n / (ms * 1e-3))
+    del J, Ja
+    T, p, Y = synth.generate_states_torch(160, nc, ccfg["T"], ccfg["p_atm"], synth.STATE_SEED_BASE + 8 + 7919 * rank, dev)
+    rho = m.density(p, T, Y)
+    To, Yo = torch.empty_like(T), torch.empty_like(Y)
+    last = []
+    ms = timed(lambda: last.append(m.cn_step(ccfg["dt"], rho, T, Y, T_out=To, Y_out=Yo, with_iters=True)[2]), steps=2)
+    torch.cuda.synchronize(dev)
+    it = last[-1]
+    res.update(cn_step_ms=ms, cn_step_per_s=nc / (ms * 1e-3), newton_iters_mean=float(it.float().mean().item()),
+               newton_iters_max=int(it.max().item()), cn_failed=int((it < 0).sum().item()))
+    return res
+
+
 def crank_nicolson_rates(synth, dev, stream, args, rank):
     """One Crank-Nicolson step (Sec. A.3.2) of 2^18 states of the 53-species
     mechanism at T ~ U[2000, 2800] K with dt = 3e-41 s (the synthetic kinetics'
@@ -554,6 +604,8 @@ def run_ours(args):
         ms_w = max_over_ranks(e0.elapsed_time(e1) / 3, dev)
         warp53 = {"ms": ms_w, "states_per_s": n / (ms_w * 1e-3)}
         large = large_mechanism_rates(synth, dev, stream, args, rank)
+        if args.large_derivatives:
+            large["derivatives"] = large_derivative_rates(synth, dev, stream, args, rank)
 
     pdep = None
     if not args.no_pdep:
@@ -625,6 +677,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--large-points", type=int, default=2 ** 21)
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--large-derivatives", action="store_true",
+                    help="also time the Jacobian, dS/dY and Crank-Nicolson kernels on the 160-species mechanism")
     ap.add_argument("--cn-points", type=int, default=2 ** 18)
     ap.add_argument("--no-cn", action="store_true")
     ap.add_argument("--transport-points", type=int, default=2 ** 20)

@@ -79,6 +79,12 @@ typedef struct pyro_mech pyro_mech;
  *                        not fit, e.g. 160 species -- a library-owned global
  *                        scratch per kernel; calls of the same kernel on one
  *                        handle must then not overlap on the GPU)
+ *   jac_rows=auto|inline|table (pyro_jacobian, pyro_jacobian_adiabatic,
+ *                        pyro_cn_step: each row of the Jacobian as straight-line
+ *                        code specialised to its species (inline), or as loops
+ *                        over emitted per-row tables of reactions and species
+ *                        partials (table; compiles in a fraction of the time for
+ *                        large mechanisms); auto: table above 64 species)
  *   device=0|1          (0: parse, validate, emit and compile only; no CUDA
  *                        device is touched and nothing can be launched)
  *   cn_newton=full|chord (pyro_cn_step: Newton with the matrix re-assembled and

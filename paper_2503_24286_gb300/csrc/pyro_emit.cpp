@@ -420,12 +420,13 @@ void emit_sri(Src& s, const Reaction& r, bool deriv) {
 struct AccCfg {
   bool mem = false;
   std::string base;   // pointer to the point's entry of the output array
+  std::string stride = "n";   // row stride of that array
 };
 AccCfg g_acc;
 
 std::string acc(const std::string& name, int k) {
   if (!g_acc.mem) return name + std::to_string(k);
-  return g_acc.base + "[(i64)" + std::to_string(k) + " * opq(n)]";
+  return g_acc.base + "[(i64)" + std::to_string(k) + " * opq(" + g_acc.stride + ")]";
 }
 
 void emit_acc_init(Src& s, const std::string& name, int N) {
@@ -434,7 +435,7 @@ void emit_acc_init(Src& s, const std::string& name, int N) {
     for (int k = 0; k < N; ++k) s << (k ? ", " : "") << name << k << " = 0.0";
     s << ";\n";
   } else {
-    s << "    #pragma unroll 1\n    for (int k = 0; k < NSP; ++k) " << g_acc.base << "[(i64)k * n] = 0.0;\n";
+    s << "    #pragma unroll 1\n    for (int k = 0; k < NSP; ++k) " << g_acc.base << "[(i64)k * " << g_acc.stride << "] = 0.0;\n";
   }
 }
 
@@ -870,8 +871,106 @@ struct JacSlots {
 //        reads) and right-hand side -F = c + (dt/2rho) S - Y, c = Y^m + (dt/2rho) S^m.
 enum class JacMode { TY, ADIA, CN };
 
+// Tables of the row assembly of the Jacobian-type kernels (table mode): per row k
+// the reactions with nu_kj != 0 (slots of R_j, Rt_j, RM_j, index j; nu_kj), per
+// reaction the species partial slots (i, slot) and the third-body efficiency
+// terms (i, eps_i - 1), per species W, 1/W and the NASA h/RT and cp/R
+// coefficients of both ranges.
+void emit_jac_tables(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, const JacSlots& sl,
+                     const std::string& sfx) {
+  const int N = m.n_species(), M = m.n_reactions();
+  std::vector<std::vector<std::pair<int, int>>> rows(N);
+  for (int j = 0; j < M; ++j)
+    for (auto& q : net_nu(m.reactions[j])) if (q.second) rows[q.first].push_back({j, q.second});
+  std::vector<int> rptr{0}, rent, qptr{0}, qent, eptr{0}, ei;
+  std::vector<double> rnu, ec, sp;
+  for (int k = 0; k < N; ++k) {
+    for (auto& jn : rows[k]) {
+      const int j = jn.first;
+      rent.insert(rent.end(), {sl.R[j], sl.Rt[j], sl.RM[j], j});
+      rnu.push_back((double)jn.second);
+    }
+    rptr.push_back((int)rnu.size());
+  }
+  for (int j = 0; j < M; ++j) {
+    for (auto& qi : sl.Q[j]) qent.insert(qent.end(), {qi.first, qi.second});
+    qptr.push_back((int)qent.size() / 2);
+    if (sl.RM[j] >= 0)
+      for (auto& e : m.reactions[j].efficiencies) {
+        if (e.second == 1.0) continue;
+        ei.push_back(e.first);
+        ec.push_back(e.second - 1.0);
+      }
+    eptr.push_back((int)ei.size());
+  }
+  for (int k = 0; k < N; ++k) {
+    sp.push_back(m.species[k].W);
+    sp.push_back(1.0 / m.species[k].W);
+    for (int rg = 0; rg < 2; ++rg) {
+      for (int q = 0; q < 6; ++q) sp.push_back(C[k].h[rg][q]);
+      for (int q = 0; q < 5; ++q) sp.push_back(C[k].cp[rg][q]);
+    }
+  }
+  auto ints = [&](const char* nm, const std::vector<int>& v) {
+    s << "__device__ const int " << nm << sfx << "[" << std::max<size_t>(v.size(), 1) << "] = {";
+    for (size_t i = 0; i < v.size(); ++i) s << (i ? "," : "") << v[i];
+    if (v.empty()) s << "0";
+    s << "};\n";
+  };
+  auto dbls = [&](const char* nm, const std::vector<double>& v) {
+    s << "__device__ const double " << nm << sfx << "[" << std::max<size_t>(v.size(), 1) << "] = {";
+    for (size_t i = 0; i < v.size(); ++i) s << (i ? "," : "") << lit(v[i]);
+    if (v.empty()) s << "0.0";
+    s << "};\n";
+  };
+  s << "\n";
+  ints("pyro_jr_ptr", rptr); ints("pyro_jr_ent", rent); dbls("pyro_jr_nu", rnu);
+  ints("pyro_jq_ptr", qptr); ints("pyro_jq_ent", qent);
+  ints("pyro_je_ptr", eptr); ints("pyro_je_i", ei); dbls("pyro_je_c", ec);
+  dbls("pyro_jsp", sp);
+}
+
+// Row k's sums over its reactions: w = sum nu R, jt = sum nu Rt, u = sum nu RM
+// (table mode).  Needs the tables with suffix sfx, W, and the row bounds re0, re1.
+std::string jac_table_row_sums(const std::string& sfx) {
+  return "      double w = 0.0, jt = 0.0, u = 0.0;\n"
+         "      for (int ie = re0; ie < re1; ++ie) {\n"
+         "        const double nu = __ldg(pyro_jr_nu" + sfx + " + ie);\n"
+         "        const int* en = pyro_jr_ent" + sfx + " + 4 * ie;\n"
+         "        w = fma(nu, W[(i64)__ldg(en) * BLKD], w); jt = fma(nu, W[(i64)__ldg(en + 1) * BLKD], jt);\n"
+         "        const int rm = __ldg(en + 2);\n"
+         "        if (rm >= 0) u = fma(nu, W[(i64)rm * BLKD], u);\n"
+         "      }\n";
+}
+
+// Row k's species terms (table mode): for every reaction j of the row and every
+// species i with a partial of R_j, ADD(i, v) with v = nu_kj dR_j/dY_i at fixed T
+// (the activity partial, and the third-body term (eps_i - 1) RM_j rho/W_i).
+std::string jac_table_row_terms(const std::string& sfx, const std::string& add) {
+  return "      for (int ie = re0; ie < re1; ++ie) {\n"
+         "        const double nu = __ldg(pyro_jr_nu" + sfx + " + ie);\n"
+         "        const int* en = pyro_jr_ent" + sfx + " + 4 * ie;\n"
+         "        const int jr = __ldg(en + 3), rm = __ldg(en + 2);\n"
+         "        const int iq1 = __ldg(pyro_jq_ptr" + sfx + " + jr + 1);\n"
+         "        for (int iq = __ldg(pyro_jq_ptr" + sfx + " + jr); iq < iq1; ++iq) {\n"
+         "          const int i = __ldg(pyro_jq_ent" + sfx + " + 2 * iq);\n"
+         "          const double v = nu * W[(i64)__ldg(pyro_jq_ent" + sfx + " + 2 * iq + 1) * BLKD];\n"
+         "          " + add + "\n"
+         "        }\n"
+         "        if (rm >= 0) {\n"
+         "          const double ru = nu * W[(i64)rm * BLKD];\n"
+         "          const int if1 = __ldg(pyro_je_ptr" + sfx + " + jr + 1);\n"
+         "          for (int ifc = __ldg(pyro_je_ptr" + sfx + " + jr); ifc < if1; ++ifc) {\n"
+         "            const int i = __ldg(pyro_je_i" + sfx + " + ifc);\n"
+         "            const double v = (__ldg(pyro_je_c" + sfx + " + ifc) * ru) * sE[i * BLKD + t];\n"
+         "            " + add + "\n"
+         "          }\n"
+         "        }\n"
+         "      }\n";
+}
+
 void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, int blk, int* nslots,
-                          JacMode mode = JacMode::TY) {
+                          JacMode mode = JacMode::TY, bool gstore = false, bool table = false) {
   int N = m.n_species(), M = m.n_reactions(), NP = N + 1;
   JacSlots sl;
   sl.R.resize(M); sl.Rt.resize(M); sl.RM.assign(M, -1); sl.Q.resize(M);
@@ -885,7 +984,9 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
     if (r.reversible) for (auto& p : r.products) sp.insert(p.first);
     for (int i : sp) sl.Q[j][i] = sl.n++;
   }
-  *nslots = sl.n;
+  // per-block scratch: the slots, then (gstore) the two per-state species arrays
+  const int stride = sl.n + (gstore ? 2 * N : 0);
+  *nslots = stride;
   auto slot = [&](int q) { return "W[" + std::to_string(q) + " * BLKD]"; };
   // Per reaction, folded at emit time (species share T_mid): the reactant sum
   // sum_i nu'_i L_i (coefficients of lnT, 1/T, 1, T, .., T^4) and, for
@@ -933,10 +1034,13 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
   s << "};\n";
   // exp/log tables read through L1: the 6 KB they would take in shared memory is
   // what lets a fourth 64-thread block fit on an SM
-  const char* prologue =
-      "  const double* __restrict__ s_exp = pyro_tab_exp_g;\n  const double* __restrict__ s_log = pyro_tab_log_g;\n"
-      "  extern __shared__ double s_dyn[];\n"
-      "  double* sA = s_dyn; double* sE = sA + NSP * BLKD;\n"
+  const std::string sfx = "_" + std::to_string((int)mode);
+  if (table) emit_jac_tables(s, m, C, sl, sfx);
+  const std::string prologue =
+      "  const double* __restrict__ s_exp = pyro_tab_exp_g;\n  const double* __restrict__ s_log = pyro_tab_log_g;\n" +
+      (gstore ? "  double* sA = g_scratch + (i64)blockIdx.x * " + std::to_string(stride) + " * BLKD + " +
+                    std::to_string(sl.n) + " * BLKD;\n  double* sE = sA + NSP * BLKD;\n"
+              : std::string("  extern __shared__ double s_dyn[];\n  double* sA = s_dyn; double* sE = sA + NSP * BLKD;\n")) +
       "  const int t = threadIdx.x;\n";
   if (mode == JacMode::TY) {
     s << "\n// Dense Jacobian d(Tdot, omega)/d(T, Y) at fixed rho, [(N+1)^2][n]; row 0 = Tdot of the adiabatic\n"
@@ -945,7 +1049,7 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
     s << "extern \"C\" __global__ void __launch_bounds__(" << blk << ") pyro_jacobian(i64 n, const double* __restrict__ g_rho,\n"
          "    const double* __restrict__ g_T, const double* __restrict__ g_Y, double* __restrict__ g_J,\n"
          "    double* __restrict__ g_scratch) {\n" << prologue <<
-         "  double* W = g_scratch + (i64)blockIdx.x * " << sl.n << " * BLKD + t;\n"
+         "  double* W = g_scratch + (i64)blockIdx.x * " << stride << " * BLKD + t;\n"
          "  for (i64 p = (i64)blockIdx.x * BLKD + t; p < n; p += (i64)gridDim.x * BLKD) {\n"
          "    const double* Yp = g_Y + p;\n    double* Jp = g_J + p;\n"
          "    const double rho = g_rho[p], T = g_T[p];\n";
@@ -955,7 +1059,7 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
     s << "extern \"C\" __global__ void __launch_bounds__(" << blk << ") pyro_jacobian_adiabatic(i64 n,\n"
          "    const double* __restrict__ g_rho, const double* __restrict__ g_T, const double* __restrict__ g_Y,\n"
          "    double* __restrict__ g_J, double* __restrict__ g_scratch) {\n" << prologue <<
-         "  double* W = g_scratch + (i64)blockIdx.x * " << sl.n << " * BLKD + t;\n"
+         "  double* W = g_scratch + (i64)blockIdx.x * " << stride << " * BLKD + t;\n"
          "  for (i64 p = (i64)blockIdx.x * BLKD + t; p < n; p += (i64)gridDim.x * BLKD) {\n"
          "    const double* Yp = g_Y + p;\n    double* Jp = g_J + p;\n"
          "    const double rho = g_rho[p], T = g_T[p];\n";
@@ -972,7 +1076,7 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
          "    double* __restrict__ g_scratch, unsigned long long* __restrict__ g_fail,\n"
          "    const int* __restrict__ g_list, const int* __restrict__ g_count, int* __restrict__ g_count_next,\n"
          "    int a_at_state) {\n" << prologue <<
-         "  double* W = g_scratch + (i64)blockIdx.x * " << sl.n << " * BLKD + t;\n"
+         "  double* W = g_scratch + (i64)blockIdx.x * " << stride << " * BLKD + t;\n"
          "  const float tolf = (float)tol;\n"
          "  const i64 na = *g_count;\n"
          "  if (blockIdx.x == 0 && t == 0) *g_count_next = 0;\n"
@@ -1057,6 +1161,31 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
       s << "    const double hh = 0.5 * dt * pdm::rcp(rho);\n";
       s << "    const i64 nr = CN_G;\n";
     }
+    if (table) {
+      // rows by loops over the tables; the entries of row k accumulate in place
+      s << "    #pragma unroll 1\n    for (int k = 0; k < NSP; ++k) {\n"
+           "      const int re0 = __ldg(pyro_jr_ptr" << sfx << " + k), re1 = __ldg(pyro_jr_ptr" << sfx << " + k + 1);\n"
+        << jac_table_row_sums(sfx) <<
+           "      const double Wk = __ldg(pyro_jsp" << sfx << " + 24 * k);\n";
+      if (mode == JacMode::CN) s << "      const double F = -hh * Wk;\n";
+      else s << "      const double F = Wk;\n      const i64 nr = n;\n";
+      s << "      const double fu = F * u, fj = F * jt;\n"
+           "      double* Jr = Jp + (i64)k * NSP * nr;\n"
+           "      #pragma unroll 1\n"
+           "      for (int i = 0; i < NSP; ++i) Jr[(i64)i * nr] = fma(sE[i * BLKD + t], fu, fj * sA[i * BLKD + t]);\n";
+      if (mode == JacMode::CN) s << "      Jr[(i64)k * nr] += 1.0;\n";
+      s << jac_table_row_terms(sfx, "Jr[(i64)i * nr] = fma(F, v, Jr[(i64)i * nr]);");
+      if (mode == JacMode::CN)
+        s << "      { const double y = __ldg(Yp + (i64)k * n);\n"
+             "        const double sk = (hh * Wk) * w;\n"
+             "        double ck;\n"
+             "        if (stp == 0) { ck = y + sk; g_c[(i64)k * cnt + p] = ck; } else { ck = g_c[(i64)k * cnt + p]; }\n"
+             "        g_b[(i64)k * cnt + q] = (ck + sk) - y; }\n";
+      else
+        s << "      (void)w;\n";
+      s << "    }\n  }\n}\n";
+      return;
+    }
     std::vector<std::vector<std::pair<int, int>>> rows(N);
     for (int j = 0; j < M; ++j)
       for (auto& q : net_nu(m.reactions[j])) if (q.second) rows[q.first].push_back({j, q.second});
@@ -1127,7 +1256,26 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
   std::vector<std::vector<std::pair<int, int>>> rows(N);
   for (int j = 0; j < M; ++j)
     for (auto& q : net_nu(m.reactions[j])) if (q.second) rows[q.first].push_back({j, q.second});
-  for (int k = 0; k < N; ++k) {
+  if (table) {
+    // rows by loops over the tables; the entries of row k accumulate in place and
+    // each species term also feeds the Tdot column accumulator sA_i (weight e_k)
+    s << "    #pragma unroll 1\n    for (int k = 0; k < NSP; ++k) {\n"
+         "      const int re0 = __ldg(pyro_jr_ptr" << sfx << " + k), re1 = __ldg(pyro_jr_ptr" << sfx << " + k + 1);\n"
+      << jac_table_row_sums(sfx) <<
+         "      const double* cf = pyro_jsp" << sfx << " + 24 * k + (hi ? 13 : 2);\n"
+         "      double hr = fma(T, __ldg(cf + 4), __ldg(cf + 3)); hr = fma(T, hr, __ldg(cf + 2)); "
+         "hr = fma(T, hr, __ldg(cf + 1)); hr = fma(T, hr, __ldg(cf)); hr = fma(__ldg(cf + 5), invT, hr);\n"
+         "      double cp = fma(T, __ldg(cf + 10), __ldg(cf + 9)); cp = fma(T, cp, __ldg(cf + 8)); "
+         "cp = fma(T, cp, __ldg(cf + 7)); cp = fma(T, cp, __ldg(cf + 6));\n"
+         "      const double eh = fma(RT, hr, -RT); const double cpm = " << lit((double)R_GAS) << " * (cp - 1.0);\n"
+         "      sum_ew = fma(eh, w, sum_ew); sum_cpw = fma(cpm, w, sum_cpw); sum_ejt = fma(eh, jt, sum_ejt); U = fma(eh, u, U);\n"
+         "      const i64 nr = n;\n      double* Jr = Jp + (i64)(k + 1) * " << NP << " * nr;\n      Jr[0] = jt;\n"
+         "      #pragma unroll 1\n"
+         "      for (int i = 0; i < NSP; ++i) Jr[(i64)(1 + i) * nr] = sE[i * BLKD + t] * u;\n"
+      << jac_table_row_terms(sfx, "Jr[(i64)(1 + i) * nr] += v; sA[i * BLKD + t] = fma(eh, v, sA[i * BLKD + t]);") <<
+         "    }\n";
+  }
+  for (int k = 0; k < (table ? 0 : N); ++k) {
     const SpeciesCoef& c = C[k];
     s << "    { // row of species " << k << "\n      double w = 0.0, jt = 0.0, u = 0.0;\n";
     std::map<int, std::string> acc, cr;
@@ -1413,7 +1561,7 @@ void emit_cn_kernels(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
        "    g_Tout[p] = T;\n    g_state[p] = 0;\n    g_it[p] = 0;\n    g_list[p] = (int)p;\n  }\n"
        "  if (blockIdx.x == 0 && threadIdx.x == 0) *g_count = (int)cnt;\n}\n";
 
-  // batched solve: one warp per state
+  // batched solve: one warp per state, CN_W states per block (matrices in groups of CN_G)
   s << R"(
 // Newton update of one Crank-Nicolson iteration, one warp per state: solve
 // (I - dt/(2 rho) J) dY = -F by LU with partial pivoting in FP32 and `refine`
@@ -1453,7 +1601,7 @@ __device__ __forceinline__ float pyro_scaled_f32(long long bits, int e) {
 // exponents in g_fac.  mode 2 (chord, the iterations between): reuse state p's kept
 // factors and refine against its kept FP64 matrix.
 #define CN_FAC_WORDS (NSP * CN_LDA + 2 * NSP)
-extern "C" __global__ void __launch_bounds__(CN_G * 32) pyro_cn_solve(i64 cnt, i64 n,
+extern "C" __global__ void __launch_bounds__(CN_W * 32) pyro_cn_solve(i64 cnt, i64 n,
     const double* __restrict__ g_A, const double* __restrict__ g_b, double* __restrict__ g_Y,
     int* __restrict__ g_state, int* __restrict__ g_it, double tol, int max_newton, int refine,
     unsigned long long* __restrict__ g_fail, const int* __restrict__ g_list, const int* __restrict__ g_count,
@@ -1462,16 +1610,16 @@ extern "C" __global__ void __launch_bounds__(CN_G * 32) pyro_cn_solve(i64 cnt, i
   const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
   double* sx = s_cn + wi * NSP;                       // solution (FP64)
-  double* sr = s_cn + (CN_G + wi) * NSP;              // right-hand side / residual (FP64)
-  float* fb = (float*)(s_cn + 2 * CN_G * NSP);
+  double* sr = s_cn + (CN_W + wi) * NSP;              // right-hand side / residual (FP64)
+  float* fb = (float*)(s_cn + 2 * CN_W * NSP);
   float* sM = fb + wi * (NSP * CN_LDA);                                // scaled LU factors
-  float* sv = fb + CN_G * NSP * CN_LDA + wi * NSP;                      // FP32 solve vector
-  float* sq = fb + CN_G * NSP * CN_LDA + CN_G * NSP + wi * NSP;         // reciprocal pivots
-  int* spiv = (int*)(fb + CN_G * NSP * CN_LDA + 2 * CN_G * NSP) + wi * NSP;   // pivot rows
-  int* se = spiv + CN_G * NSP;                                          // row scale exponents
+  float* sv = fb + CN_W * NSP * CN_LDA + wi * NSP;                      // FP32 solve vector
+  float* sq = fb + CN_W * NSP * CN_LDA + CN_W * NSP + wi * NSP;         // reciprocal pivots
+  int* spiv = (int*)(fb + CN_W * NSP * CN_LDA + 2 * CN_W * NSP) + wi * NSP;   // pivot rows
+  int* se = spiv + CN_W * NSP;                                          // row scale exponents
   const int tr = l >> 1, tc = l & 1;                  // lane's place in the 16 x 2 update tile
   const i64 na = *g_count;
-  for (i64 q = ((i64)blockIdx.x * CN_G + wi); q < na; q += (i64)gridDim.x * CN_G) {
+  for (i64 q = ((i64)blockIdx.x * CN_W + wi); q < na; q += (i64)gridDim.x * CN_W) {
     const i64 p = g_list[q];
     const int st = g_state[p];
     if (st >= 3) continue;
@@ -1665,7 +1813,7 @@ extern "C" __global__ void __launch_bounds__(BLKD) pyro_cn_finish(i64 cnt, i64 n
 // keeps the matrix of its first iterate): T from (e, Y), omega by the forward
 // path, -F = c + (dt/2rho) W omega - Y into slot q.  Same state/list protocol as
 // pyro_cn_assemble.
-void emit_cn_residual_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C) {
+void emit_cn_residual_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, bool acc_mem) {
   const int N = m.n_species();
   s << "\nextern \"C\" __global__ void __launch_bounds__(BLKD) pyro_cn_residual(i64 cnt, i64 n,\n"
        "    const double* __restrict__ g_rho, const double* __restrict__ g_e, const double* __restrict__ g_Y,\n"
@@ -1690,15 +1838,21 @@ void emit_cn_residual_kernel(Src& s, const Mechanism& m, const std::vector<Speci
   emit_species_forward(r, m, C);
   if (has_plog(m))
     r << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lit((double)logl(R_GAS)) << ";\n";
-  g_acc.mem = false;
+  // large mechanisms: the species sums accumulate in the right-hand side itself
+  g_acc.mem = acc_mem;
+  g_acc.base = "Bq";
+  g_acc.stride = "cnt";
+  if (acc_mem) r << "    double* Bq = g_b + q;\n";
   emit_acc_init(r, "w", N);
   for (auto& grp : reaction_groups(m)) emit_reaction_group(r, m, grp);
   s << r.o.str();
   s << "    const double hh = 0.5 * dt * pdm::rcp(rho);\n";
   for (int k = 0; k < N; ++k)
     s << "    g_b[(i64)" << k << " * cnt + q] = (g_c[(i64)" << k << " * cnt + p] + (hh * " << lit(m.species[k].W)
-      << ") * w" << k << ") - __ldg(Yp + (i64)" << k << " * n);\n";
+      << ") * " << acc("w", k) << ") - __ldg(Yp + (i64)" << k << " * n);\n";
   s << "  }\n}\n";
+  g_acc.mem = false;
+  g_acc.stride = "n";
 }
 
 // ---------------------------------------------------------------------------
@@ -2043,15 +2197,20 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, cons
   }
   int nslots = 0;
   {
-    Src d; d << pre.o.str(); emit_jacobian_kernel(d, m, C, opt.deriv_block, &nslots); out.group_sources["jac"] = d.o.str();
+    Src d; d << pre.o.str();
+    emit_jacobian_kernel(d, m, C, opt.deriv_block, &nslots, JacMode::TY, opt.dgstore, opt.jac_table);
+    out.group_sources["jac"] = d.o.str();
   }
+  // Jacobian-type kernels: two per-state species arrays, in shared memory or (large
+  // mechanisms) after the slots in the per-block global scratch
   out.jac_slots = nslots;
-  out.smem_dyn_bytes_jac = 2 * N * opt.deriv_block * (int)sizeof(double);
+  out.smem_dyn_bytes_jac = opt.dgstore ? 0 : 2 * N * opt.deriv_block * (int)sizeof(double);
+  out.stats["jacobian_rows_from_tables"] = opt.jac_table ? 1 : 0;
   out.stats["jacobian_supported"] = common_tmid(m) ? 1 : 0;
   {
     int ns2 = 0;
     Src d; d << pre.o.str();
-    emit_jacobian_kernel(d, m, C, opt.deriv_block, &ns2, JacMode::ADIA);
+    emit_jacobian_kernel(d, m, C, opt.deriv_block, &ns2, JacMode::ADIA, opt.dgstore, opt.jac_table);
     out.group_sources["jad"] = d.o.str();
   }
   if (m.has_transport) {
@@ -2072,15 +2231,23 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, cons
     // Crank-Nicolson: temperature solve + Newton-system assembly + batched solve
     int ns2 = 0;
     Src d; d << pre.o.str();
-    d << "#define CN_G " << kCnGroup << "\n#define opt_mixed " << (opt.mixed_newton ? 1 : 0) << "\n";
+    // shared memory of one state of the batched solve; states per block: as many
+    // as fit in 227 KB, at most kCnGroup (2 for 160 species)
+    const int half = (N + 1) / 2, lda = half % 2 == 1 ? 2 * half : 2 * half + 2;   // CN_LDA
+    const int per_warp = 2 * N * 8 + N * lda * 4 + 4 * N * 4;
+    const int cnw = std::max(1, std::min(kCnGroup, (227 * 1024) / per_warp));
+    d << "#define CN_G " << kCnGroup << "\n#define CN_W " << cnw << "\n#define opt_mixed "
+      << (opt.mixed_newton ? 1 : 0) << "\n";
     std::map<std::string, double> dummy;
     emit_tsolve(d, m, C, opt, dummy);
-    emit_jacobian_kernel(d, m, C, opt.deriv_block, &ns2, JacMode::CN);
+    emit_jacobian_kernel(d, m, C, opt.deriv_block, &ns2, JacMode::CN, opt.dgstore, opt.jac_table);
     emit_cn_kernels(d, m, C);
-    emit_cn_residual_kernel(d, m, C);
+    if (opt.cn_residual) emit_cn_residual_kernel(d, m, C, opt.acc_mem);
+    out.stats["cn_residual_kernel"] = opt.cn_residual ? 1 : 0;
     out.group_sources["cn"] = d.o.str();
-    const int half = (N + 1) / 2, lda = half % 2 == 1 ? 2 * half : 2 * half + 2;   // CN_LDA
-    out.smem_dyn_bytes_cn_solve = kCnGroup * (2 * N * 8 + N * lda * 4 + 4 * N * 4);
+    out.cn_solve_warps = cnw;
+    out.stats["cn_solve_warps"] = cnw;
+    out.smem_dyn_bytes_cn_solve = cnw * per_warp;
   }
   out.smem_dyn_bytes_deriv = opt.dgstore ? 0 : 4 * N * opt.deriv_block * (int)sizeof(double);
   out.stats["jacobian_scratch_doubles_per_point"] = nslots;

@@ -19,6 +19,11 @@ struct EmitOptions {
   bool gstore = false;
   bool dgstore = false;
   bool acc_mem = false;
+  // Jacobian-type kernels: rows assembled by loops over emitted tables (per-row
+  // reaction lists, per-reaction species partials) instead of straight-line code
+  bool jac_table = false;
+  // Crank-Nicolson unit: also emit the right-hand-side-only kernel of the chord iteration
+  bool cn_residual = false;
   int exp_ops = 4;            // device exponential: 4 (default) or 2 FP64-pipe operations
   bool exp_call = false;      // one called body instead of inlining at every use
 };
@@ -34,6 +39,7 @@ struct EmitResult {
   int smem_dyn_bytes_cn_solve = 0;        // dynamic shared memory of the Crank-Nicolson solve kernel
   int smem_dyn_bytes_transport = 0;       // dynamic shared memory of the transport kernel
   int smem_dyn_bytes_jac = 0;             // dynamic shared memory of the Jacobian-type kernels
+  int cn_solve_warps = 4;                 // states (warps) per block of the Crank-Nicolson solve kernel
 };
 
 // Threads per block of the transport kernel (3 per-state arrays of N doubles in

@@ -185,6 +185,7 @@ struct Options {
   bool exp_call = false;  // exponential as a called function
   bool cn_chord = false;  // Crank-Nicolson: keep a factorisation for several iterations (chord) instead of full Newton
   int cn_refresh = 4;     // chord: re-assemble and re-factor every cn_refresh-th iteration
+  int jac_rows = 0;       // Jacobian row assembly: 0 auto (tables above 64 species), 1 inline, 2 tables
 };
 
 bool parse_options(const char* s, Options& o, std::string& err) {
@@ -210,6 +211,7 @@ bool parse_options(const char* s, Options& o, std::string& err) {
       else if (v == "4call") { o.exp_ops = 4; o.exp_call = true; }
       else { err = "exp=2|4|2call|4call"; return false; }
     }
+    else if (k == "jac_rows") { if (v == "auto") o.jac_rows = 0; else if (v == "inline") o.jac_rows = 1; else if (v == "table") o.jac_rows = 2; else { err = "jac_rows=auto|inline|table"; return false; } }
     else if (k == "cn_refresh") { o.cn_refresh = std::atoi(v.c_str()); if (o.cn_refresh < 1 || o.cn_refresh > 1000) { err = "cn_refresh must be in [1, 1000]"; return false; } }
     else if (k == "cn_newton") { if (v == "full") o.cn_chord = false; else if (v == "chord") o.cn_chord = true; else { err = "cn_newton=full|chord"; return false; } }
     else if (k == "variant") { if (v == "thread") o.warp = false; else if (v == "warp") o.warp = true; else { err = "variant=thread|warp"; return false; } }
@@ -545,13 +547,14 @@ int ensure_groups(pyro_mech* h, const std::vector<std::string>& names) {
     if (r != CUDA_SUCCESS || nb < 1) return fail(PYRO_ECUDA, std::string(group_kernel(todo[i])) + " does not fit on an SM");
     G.blocks_per_sm = nb;
     h->emitted.stats[todo[i] + "_blocks_per_sm"] = nb;
-    if (h->emitted.stats["deriv_store_global"] > 0 && todo[i] != "jac") {
+    if (h->emitted.stats["deriv_store_global"] > 0 && todo[i] != "jac" && todo[i] != "jad" && todo[i] != "cn") {
       size_t bytes = (size_t)h->num_sms * nb * 4 * h->m.n_species() * h->opt.deriv_block * sizeof(double);
       cudaError_t e = cudaMalloc(&G.store, bytes);
       if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("species-array store allocation: ") + cudaGetErrorString(e));
     }
     if (todo[i] == "cn") {
       for (const char* nm : {"pyro_cn_prep", "pyro_cn_solve", "pyro_cn_finish", "pyro_cn_residual"}) {
+        if (h->emitted.stats["cn_residual_kernel"] <= 0 && std::string(nm) == "pyro_cn_residual") continue;
         CUfunction f = nullptr;
         r = d.ModuleGetFunction(&f, G.module, nm);
         if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, std::string("missing kernel ") + nm);
@@ -561,17 +564,19 @@ int ensure_groups(pyro_mech* h, const std::vector<std::string>& names) {
       r = d.FuncSetAttribute(G.fn["pyro_cn_solve"], CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, ssm);
       if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "shared memory request (Crank-Nicolson solve): " + cu_err(r));
       int sb = 0;
-      r = d.Occupancy(&sb, G.fn["pyro_cn_solve"], 32 * pyro::kCnGroup, ssm);
+      r = d.Occupancy(&sb, G.fn["pyro_cn_solve"], 32 * h->emitted.cn_solve_warps, ssm);
       if (r != CUDA_SUCCESS || sb < 1) return fail(PYRO_ECUDA, "pyro_cn_solve does not fit on an SM");
       G.solve_blocks_per_sm = sb;
       h->emitted.stats["cn_solve_blocks_per_sm"] = sb;
-      const int rsm = 2 * h->m.n_species() * h->opt.deriv_block * (int)sizeof(double);
-      r = d.FuncSetAttribute(G.fn["pyro_cn_residual"], CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, rsm);
-      if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "shared memory request (Crank-Nicolson residual): " + cu_err(r));
-      int rb = 0;
-      r = d.Occupancy(&rb, G.fn["pyro_cn_residual"], h->opt.deriv_block, rsm);
-      if (r != CUDA_SUCCESS || rb < 1) return fail(PYRO_ECUDA, "pyro_cn_residual does not fit on an SM");
-      G.residual_blocks_per_sm = rb;
+      if (h->emitted.stats["cn_residual_kernel"] > 0) {   // chord iterations
+        const int rsm = 2 * h->m.n_species() * h->opt.deriv_block * (int)sizeof(double);
+        r = d.FuncSetAttribute(G.fn["pyro_cn_residual"], CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, rsm);
+        if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "shared memory request (Crank-Nicolson residual): " + cu_err(r));
+        int rb = 0;
+        r = d.Occupancy(&rb, G.fn["pyro_cn_residual"], h->opt.deriv_block, rsm);
+        if (r != CUDA_SUCCESS || rb < 1) return fail(PYRO_ECUDA, "pyro_cn_residual does not fit on an SM");
+        G.residual_blocks_per_sm = rb;
+      }
     }
     h->emitted.stats[todo[i] + "_cubin_bytes"] = (double)cubins[i].size();
   }
@@ -643,6 +648,8 @@ int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) 
     eo.gstore = h->opt.store == 2 || (h->opt.store == 0 && (size_t)2 * N * eo.block * 8 > lim);
     eo.dgstore = h->opt.store == 2 || (h->opt.store == 0 && (size_t)4 * N * eo.deriv_block * 8 > lim);
     eo.acc_mem = N > 64;
+    eo.jac_table = h->opt.jac_rows == 2 || (h->opt.jac_rows == 0 && N > 64);
+    eo.cn_residual = h->opt.cn_chord || !eo.jac_table;   // large mechanisms: only where chord asks for it
     if (eo.gstore && eo.block > 64) eo.min_blocks = 1;
   }
   h->emitted = emit_module(h->m, eo);
@@ -881,8 +888,7 @@ int pyro_mech_prepare(const pyro_mech* hc, const char* kernels) {
   std::string k = kernels ? kernels : "all";
   std::vector<std::string> names;
   if (k == "all") {
-    names = {"jvp", "vjp"};
-    if (h->emitted.stats["deriv_store_global"] <= 0) names.push_back("jac");
+    names = {"jvp", "vjp", "jac"};
   }
   else {
     std::string item;
@@ -946,9 +952,6 @@ int pyro_jacobian(const pyro_mech* hc, int64_t n, const double* rho, const doubl
     return fail(PYRO_EINVAL, "the dense Jacobian kernels need all species to share one NASA-7 T_mid");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
-  if (h->emitted.stats["deriv_store_global"] > 0)
-    return fail(PYRO_EINVAL, "the dense Jacobian needs the per-state species arrays in shared memory "
-                             "(4 N deriv_block 8 B <= 160 KB); use pyro_jvp / pyro_vjp for this mechanism");
   if (int rc = ensure_groups(h, {"jac"})) return rc;
   const pyro_mech::Group& G = h->groups["jac"];
   int NP = h->m.n_species() + 1;
@@ -992,9 +995,6 @@ int pyro_jacobian_adiabatic(const pyro_mech* hc, int64_t n, const double* rho, c
     return fail(PYRO_EINVAL, "the dense Jacobian kernels need all species to share one NASA-7 T_mid");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
-  if (h->emitted.stats["deriv_store_global"] > 0)
-    return fail(PYRO_EINVAL, "the dense Jacobian needs the per-state species arrays in shared memory "
-                             "(4 N deriv_block 8 B <= 160 KB); use pyro_jvp / pyro_vjp for this mechanism");
   if (int rc = ensure_groups(h, {"jad"})) return rc;
   const pyro_mech::Group& G = h->groups["jad"];
   const int64_t NS = h->m.n_species();
@@ -1061,7 +1061,6 @@ int cn_run(pyro_mech* h, int64_t cnt, int64_t ld, double dt, const double* rho, 
            void* stream) {
   const pyro_mech::Group& G = h->groups["cn"];
   const int64_t N = h->m.n_species();
-  const int64_t Gs = pyro::kCnGroup;
   const int64_t m = cn_chunk(h, cnt);
   double* dA = (double*)h->d_cn;                 // [m/G][N^2][G]
   double* dc = dA + (size_t)m * N * N;           // [N][m]
@@ -1089,7 +1088,8 @@ int cn_run(pyro_mech* h, int64_t cnt, int64_t ld, double dt, const double* rho, 
     void* pp[] = {&nc, &nld, &Tin_c, &Yin_c, &Tout_c, &Yout_c, &de, &dstate, &dit, &dlist[0], &dcount[0]};
     CUresult r = d.LaunchKernel(G.fn.at("pyro_cn_prep"), gs, 1, 1, bd, 1, 1, 0, as_stream(stream), pp, nullptr);
     if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
-    unsigned gsolve = (unsigned)std::min<int64_t>((nc + Gs - 1) / Gs, (int64_t)h->num_sms * G.solve_blocks_per_sm);
+    const int64_t Ws = h->emitted.cn_solve_warps;   // states per block of the solve
+    unsigned gsolve = (unsigned)std::min<int64_t>((nc + Ws - 1) / Ws, (int64_t)h->num_sms * G.solve_blocks_per_sm);
     const bool chord = h->opt.cn_chord;
     unsigned gres = (unsigned)std::min<int64_t>((nc + bd - 1) / bd, (int64_t)h->num_sms * G.residual_blocks_per_sm);
     const unsigned rsm = (unsigned)(2 * N * bd * sizeof(double));
@@ -1112,7 +1112,7 @@ int cn_run(pyro_mech* h, int64_t cnt, int64_t ld, double dt, const double* rho, 
       }
       void* ps[] = {&nc, &nld, &dA, &db, &Yout_c, &dstate, &dit, &tol, &max_newton, &refine, &h->d_fail,
                     &li, &ci, &lo, &co, &mode, &dfac};
-      r = d.LaunchKernel(G.fn.at("pyro_cn_solve"), gsolve, 1, 1, 32 * pyro::kCnGroup, 1, 1,
+      r = d.LaunchKernel(G.fn.at("pyro_cn_solve"), gsolve, 1, 1, 32 * (unsigned)Ws, 1, 1,
                          h->emitted.smem_dyn_bytes_cn_solve, as_stream(stream), ps, nullptr);
       if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
     }
@@ -1135,9 +1135,6 @@ int pyro_cn_step(const pyro_mech* hc, int64_t n, double dt, const double* rho, c
     return fail(PYRO_EINVAL, "pyro_cn_step: need dt >= 0, tol > 0 and 1 <= max_newton <= 1000");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
-  if (h->emitted.stats["deriv_store_global"] > 0)
-    return fail(PYRO_EINVAL, "the Crank-Nicolson step needs the dense Jacobian, which needs the per-state species "
-                             "arrays in shared memory (4 N deriv_block 8 B <= 160 KB)");
   if (int rc = ensure_groups(h, {"cn"})) return rc;
   const int64_t NS = h->m.n_species();
   const int refine = 1;

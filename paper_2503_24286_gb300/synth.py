@@ -173,6 +173,12 @@ CONFIGS = {
     # PLOG reactions (3-5 pressure nodes between 0.1 and 100 atm)
     7: dict(name="gri-53sp-pdep", mech=7, base=1, n_sri=10, n_plog=20, n_points=2 ** 22,
             T=(300.0, 2800.0), p_atm=(0.5, 20.0)),
+    # Crank-Nicolson step on the 160-species mechanism (161 x 161 Newton systems with
+    # the temperature row folded out: 160 x 160).  Its gross rates reach ~1e42
+    # kmol/m^3/s at 2000-2800 K, six orders above the 53-species mechanism's, so
+    # the step is dt = 1e-46 s (T moves by up to ~10 K, Newton converges in 3-7 steps).
+    8: dict(name="large-160sp-crank-nicolson", mech=4, n_points=2 ** 14, T=(2000.0, 2800.0),
+            p_atm=(1.0, 40.0), dt=1.0e-46),
 }
 PDEP_SEED_OFFSET = 2000
 

@@ -2,7 +2,9 @@
 thread-per-point kernels with the per-state species arrays in a global scratch
 and the species accumulators in the output arrays, against the oracle --
 forward (temperature input and energy input), JVP and VJP (recomputed
-intermediates, no stored Jacobian) -- plus the full-size workload sampled."""
+intermediates, no stored Jacobian), the dense 161 x 161 Jacobian, dS/dY at fixed
+(rho, e) and the Crank-Nicolson step (Jacobian rows assembled from tables) --
+plus the full-size workload sampled."""
 import numpy as np
 import pytest
 
@@ -29,7 +31,7 @@ def large(mech_files, dev):
     from paper_2503_24286_gb300 import build as BLD
     BLD.build()
     m = B.Mechanism(mech_files[0][4])
-    m.prepare("all")
+    m.prepare("jvp,vjp,jacobian,jacobian_adiabatic,cn")
     return m, O.Oracle(mech_files[0][4])
 
 
@@ -85,13 +87,73 @@ def test_large_jvp_vjp_parity(large, dev):
     assert np.all(np.abs(Yb - refb[2:]) <= TOL_D * sc[2:] + 1e-300)
 
 
-def test_large_jacobian_refused(large, dev):
-    from paper_2503_24286_gb300 import binding as B
+def test_large_jacobian_matches_oracle(large, dev):
+    """Dense d(Tdot, omega)/d(T, Y), 161 x 161 per state, rows from tables, species
+    arrays in the global scratch: against the oracle's complex-step Jacobian, with
+    the column scales and row-relative bound of the 53-species test."""
     m, orc = large
-    st = synth.config_states(4, n=4)
-    with pytest.raises(B.PyroError) as ei:
-        m.jacobian(_t(np.ones(4), dev), _t(st.T, dev), _t(st.Y, dev))
-    assert ei.value.code == B.PYRO_EINVAL
+    assert m.stat("jacobian_rows_from_tables") == 1 and m.stat("deriv_store_global") == 1
+    n, NP = 12, 161
+    st = synth.config_states(4, n=n, offset_seed=50)
+    rho = orc.density(st.p, st.T, st.Y)
+    J = m.jacobian(_t(rho, dev), _t(st.T, dev), _t(st.Y, dev)).cpu().numpy().reshape(NP, NP, n)
+    Jo = orc.jacobian(rho, st.T, st.Y).reshape(NP, NP, n)
+    xs = np.concatenate([st.T[None], np.maximum(st.Y, 1e-3)], axis=0)
+    row = np.max(np.abs(Jo) * xs[None], axis=1, keepdims=True) + 1e-300
+    assert np.all(np.isfinite(J))
+    assert np.max(np.abs(J - Jo) * xs[None] / row) <= TOL_D
+
+
+def test_large_adiabatic_jacobian_oracle_chain_rule_and_columns(large, dev):
+    """dS/dY at fixed (rho, e), 160 x 160: against the oracle on a few states, and on
+    more states than one block (ragged tail) against the chain rule applied to the
+    library's own (T, Y) Jacobian, W_j (d omega_j/dY_k - d omega_j/dT e_k/c_v);
+    columns sum to zero (mass conservation)."""
+    m, orc = large
+    N, NP = 160, 161
+    st = synth.config_states(4, n=8, offset_seed=51)
+    rho = orc.density(st.p, st.T, st.Y)
+    J = m.jacobian_adiabatic(_t(rho, dev), _t(st.T, dev), _t(st.Y, dev)).cpu().numpy().reshape(N, N, 8)
+    Jo = orc.jacobian_adiabatic(rho, st.T, st.Y).reshape(N, N, 8)
+    xs = np.maximum(st.Y, 1e-3)[None]
+    row = np.max(np.abs(Jo) * xs, axis=1, keepdims=True) + 1e-300
+    assert np.max(np.abs(J - Jo) * xs / row) <= TOL_D
+    n = 193
+    st = synth.config_states(4, n=n, offset_seed=52)
+    rho = orc.density(st.p, st.T, st.Y)
+    r, T, Y = _t(rho, dev), _t(st.T, dev), _t(st.Y, dev)
+    Ja = m.jacobian_adiabatic(r, T, Y).reshape(N, N, n)
+    Jty = m.jacobian(r, T, Y).reshape(NP, NP, n)
+    e, cv = m.internal_energy(T, Y, with_cv=True)
+    ek = torch.stack([m.internal_energy(T, torch.nn.functional.one_hot(
+        torch.full((n,), k, device=dev), N).T.contiguous().double()) for k in range(N)])
+    Wt = torch.tensor(orc.W, device=dev, dtype=torch.float64)
+    ref = Wt[:, None, None] * (Jty[1:, 1:] - Jty[1:, :1] * (ek / cv)[None])
+    xt = torch.clamp(Y, min=1e-3)[None]
+    rw = (ref.abs() * xt).amax(dim=1, keepdim=True) + 1e-300
+    assert ((Ja - ref).abs() * xt / rw).max().item() <= 1e-11
+    colsum = Ja.sum(dim=0).abs() / (Ja.abs().sum(dim=0) + 1e-300)
+    assert colsum.max().item() <= 1e-12
+
+
+def test_large_cn_step_matches_oracle(large, dev):
+    """One Crank-Nicolson step on the 160-species mechanism (dt = 1e-46 s, T in
+    [2000, 2800] K): 160 x 160 Newton systems, two states per block of the batched
+    solve; against the oracle's step."""
+    m, orc = large
+    cfg = synth.CONFIGS[8]
+    st = synth.config_states(8, n=16)
+    rho = orc.density(st.p, st.T, st.Y)
+    Yo, To, ito, bad = orc.cn_step(cfg["dt"], rho, st.T, st.Y)
+    assert bad == 0
+    T1, Y1, it = m.cn_step(cfg["dt"], _t(rho, dev), _t(st.T, dev), _t(st.Y, dev), with_iters=True)
+    T1, Y1, it = T1.cpu().numpy(), Y1.cpu().numpy(), it.cpu().numpy()
+    assert np.all(it > 0) and m.nonconverged() == 0
+    assert np.max(np.abs(Y1 - Yo)) <= 1e-10
+    assert np.max(np.abs(T1 - To) / To) <= 1e-10
+    assert np.max(np.abs(it - ito)) <= 1
+    assert np.max(np.abs(Y1 - st.Y)) > 1e-4
+    assert m.stat("cn_solve_warps") == 2
 
 
 def test_large_full_size_sampled(large, dev):

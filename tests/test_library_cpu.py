@@ -84,6 +84,21 @@ def test_adiabatic_jacobian_and_crank_nicolson_kernels_compile_without_gpu(mech_
     assert L.pyro_jacobian_adiabatic(m.handle, 4, None, px, px, px, None) == B.PYRO_EINVAL
 
 
+def test_table_row_jacobian_kernels_compile_without_gpu(mech_files):
+    """Jacobian rows from emitted tables (the assembly large mechanisms use), with the
+    per-state species arrays in the global scratch (store=global): the Jacobian,
+    dS/dY and Crank-Nicolson units compile; the scratch holds the slots plus the two
+    species arrays; the solve takes four states per block at 10 species."""
+    m = B.Mechanism(mech_files[0][0], "device=0;jac_rows=table;store=global")
+    m.prepare("jacobian,jacobian_adiabatic,cn")
+    assert m.stat("jacobian_rows_from_tables") == 1 and m.stat("deriv_store_global") == 1
+    assert m.stat("jac_cubin_bytes") > 1000 and m.stat("jad_cubin_bytes") > 1000 and m.stat("cn_cubin_bytes") > 1000
+    inline = B.Mechanism(mech_files[0][0], "device=0")
+    assert inline.stat("jacobian_rows_from_tables") == 0
+    assert m.stat("jacobian_scratch_doubles_per_point") == inline.stat("jacobian_scratch_doubles_per_point") + 2 * 10
+    assert m.stat("cn_solve_warps") == 4
+
+
 def test_transport_kernels_compile_without_gpu(mech_files, tmp_path):
     m = B.Mechanism(mech_files[0][0], "device=0")
     assert m.stat("has_transport") == 1
@@ -143,7 +158,7 @@ def test_missing_file_and_bad_options(tmp_path, mech_files):
     with pytest.raises(B.PyroError) as ei:
         B.Mechanism(mech_files[0][0], "device=0;frobnicate=1")
     assert ei.value.code == B.PYRO_EINVAL
-    for bad in ("cn_newton=quasi", "cn_refresh=0", "cn_refresh=5000"):
+    for bad in ("cn_newton=quasi", "cn_refresh=0", "cn_refresh=5000", "jac_rows=sparse"):
         with pytest.raises(B.PyroError) as ei:
             B.Mechanism(mech_files[0][0], "device=0;" + bad)
         assert ei.value.code == B.PYRO_EINVAL
