@@ -325,22 +325,23 @@ def large_derivative_rates(synth, dev, stream, args, rank):
     """The Jacobian-type kernels on the 160-species mechanism (rows from tables,
     species arrays in the global scratch): dense 161 x 161 Jacobian and dS/dY at
     fixed (rho, e) on 2^15 states, one Crank-Nicolson step of 2^14 states at
-    dt = 1e-46 s.  Off by default (the three units take minutes to compile)."""
+    dt = 1e-46 s (sizes: --large-deriv-points and half of it).  Off by default
+    (the three units take minutes to compile)."""
     import torch
     from paper_2503_24286_gb300 import binding as B
     d = tempfile.mkdtemp()
     path = os.path.join(d, "mech4.txt")
     synth.write_mechanism(synth.config_mechanism(4), path)
+    parts = args.large_derivatives.split(",")
     m = B.Mechanism(path)
-    m.prepare("jacobian,jacobian_adiabatic,cn")
+    m.prepare(args.large_derivatives)
     cfg, ccfg = synth.CONFIGS[4], synth.CONFIGS[8]
-    n, nc = 2 ** 15, 2 ** 14
+    n, nc = args.large_deriv_points, args.large_deriv_points // 2
     res = {"workload": "160 species / 1100 reactions; Jacobian and dS/dY on %d states (T ~ U[300, 2800] K), "
-                       "Crank-Nicolson on %d states (T ~ U[2000, 2800] K, dt = 1e-46 s)" % (n, nc)}
+                       "Crank-Nicolson on %d states (T ~ U[2000, 2800] K, dt = 1e-46 s); timed: %s"
+                       % (n, nc, args.large_derivatives)}
     T, p, Y = synth.generate_states_torch(160, n, cfg["T"], cfg["p_atm"], synth.STATE_SEED_BASE + 4 + 7919 * rank, dev)
     rho = m.density(p, T, Y)
-    J = torch.empty((161 * 161, n), dtype=torch.float64, device=dev)
-    Ja = torch.empty((160 * 160, n), dtype=torch.float64, device=dev)
 
     def timed(fn, steps=3):
         for _ in range(2):
@@ -354,11 +355,18 @@ def large_derivative_rates(synth, dev, stream, args, rank):
         torch.cuda.synchronize(dev)
         return max_over_ranks(e0.elapsed_time(e1) / steps, dev)
 
-    ms = timed(lambda: m.jacobian(rho, T, Y, out=J))
-    res.update(jacobian_ms=ms, jacobian_per_s=n / (ms * 1e-3), jacobian_out_GB_per_s=J.numel() * 8 / (ms * 1e6))
-    ms = timed(lambda: m.jacobian_adiabatic(rho, T, Y, out=Ja))
-    res.update(jacobian_adiabatic_ms=ms, jacobian_adiabatic_per_s=n / (ms * 1e-3))
-    del J, Ja
+    if "jacobian" in parts:
+        J = torch.empty((161 * 161, n), dtype=torch.float64, device=dev)
+        ms = timed(lambda: m.jacobian(rho, T, Y, out=J))
+        res.update(jacobian_ms=ms, jacobian_per_s=n / (ms * 1e-3), jacobian_out_GB_per_s=J.numel() * 8 / (ms * 1e6))
+        del J
+    if "jacobian_adiabatic" in parts:
+        Ja = torch.empty((160 * 160, n), dtype=torch.float64, device=dev)
+        ms = timed(lambda: m.jacobian_adiabatic(rho, T, Y, out=Ja))
+        res.update(jacobian_adiabatic_ms=ms, jacobian_adiabatic_per_s=n / (ms * 1e-3))
+        del Ja
+    if "cn" not in parts:
+        return res
     T, p, Y = synth.generate_states_torch(160, nc, ccfg["T"], ccfg["p_atm"], synth.STATE_SEED_BASE + 8 + 7919 * rank, dev)
     rho = m.density(p, T, Y)
     To, Yo = torch.empty_like(T), torch.empty_like(Y)
@@ -677,8 +685,10 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--large-points", type=int, default=2 ** 21)
     ap.add_argument("--no-large", action="store_true")
-    ap.add_argument("--large-derivatives", action="store_true",
-                    help="also time the Jacobian, dS/dY and Crank-Nicolson kernels on the 160-species mechanism")
+    ap.add_argument("--large-derivatives", nargs="?", const="jacobian,jacobian_adiabatic,cn", default=None,
+                    help="also time the Jacobian, dS/dY and Crank-Nicolson kernels on the 160-species "
+                         "mechanism (or the comma list given of jacobian, jacobian_adiabatic, cn)")
+    ap.add_argument("--large-deriv-points", type=int, default=2 ** 15)
     ap.add_argument("--cn-points", type=int, default=2 ** 18)
     ap.add_argument("--no-cn", action="store_true")
     ap.add_argument("--transport-points", type=int, default=2 ** 20)
