@@ -151,6 +151,19 @@ def cpu_oracle_rate(path: str, n: int, seed_offset: int = 0):
     return n / dt, O.threads(), dt
 
 
+def cpu_oracle_rate_one_core(path: str, n: int):
+    """The same on one host core (OpenMP limited to one thread for the call)."""
+    from oracle import oracle as O
+    O.build()
+    prev = O.threads()
+    O.set_threads(1)
+    try:
+        rate, _, dt = cpu_oracle_rate(path, n, seed_offset=7)
+    finally:
+        O.set_threads(prev)
+    return rate, dt
+
+
 def run_reference(args):
     rank, world = rank_world()
     if rank != 0:
@@ -637,6 +650,8 @@ def run_ours(args):
     line = None
     if rank == 0:
         rate_cpu, cores, dt = cpu_oracle_rate(path, args.cpu_sample)
+        n1 = max(256, min(args.cpu_sample // 128, 8192))
+        rate_1, dt_1 = cpu_oracle_rate_one_core(path, n1)
         line = {"metric": METRIC, "value": value, "unit": "states/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(n),
@@ -649,7 +664,9 @@ def run_ours(args):
                                                        if clocks.get("sm_mhz") else None)},
                 "cpu_baseline": {"value": rate_cpu, "unit": "states/s", "cores": cores, "kind": "oracle",
                                  "sample": "%d states of the same workload (seeded), T solve + omega, %.1f s"
-                                           % (args.cpu_sample, dt)},
+                                           % (args.cpu_sample, dt),
+                                 "value_one_core": rate_1,
+                                 "sample_one_core": "%d states, 1 thread, %.1f s" % (n1, dt_1)},
                 "e2e": {"value": world * n / e2e_s, "unit": "states/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches,
