@@ -190,3 +190,42 @@ def test_cn_second_order_against_ode_integration(tmp_path):
         assert abs(o.internal_energy(Tn, Yn)[0] - e[0]) <= 1e-12 * abs(e[0]) + 1e-9
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 6.5 < r1 < 9.5 and 6.5 < r2 < 9.5, errs
+
+
+# --- the 160-species mechanism (the references of the large GPU tests) -------------
+
+def test_large_mechanism_adiabatic_jacobian_and_cn_step(mech_files):
+    """On the 160-species / 1100-reaction mechanism: dS/dY at fixed (rho, e) against
+    central differences of S with T re-solved from e, zero column sums; the
+    Crank-Nicolson step (dt = 1e-46 s) satisfies its defining equation
+    Y+ - Y - dt/(2 rho) (S(Y+) + S(Y)) = 0 (Eq. crank_nicol_rhs) to rounding,
+    conserves mass, and keeps e(T+, Y+) = e(T, Y)."""
+    o = O.Oracle(mech_files[0][4])
+    N = o.N
+    st = synth.config_states(4, n=2, offset_seed=60)
+    rho = o.density(st.p, st.T, st.Y)
+    e = o.internal_energy(st.T, st.Y)
+    J = o.jacobian_adiabatic(rho, st.T, st.Y).reshape(N, N, 2)
+    Jfd = np.zeros_like(J)
+    for k in range(N):
+        hk = 1e-7 * np.maximum(np.abs(st.Y[k]), 1e-3)
+        Yp, Ym = st.Y.copy(), st.Y.copy()
+        Yp[k] += hk
+        Ym[k] -= hk
+        Jfd[:, k] = (o.source_at_energy(rho, e, Yp) - o.source_at_energy(rho, e, Ym)) / (2 * hk)
+    xs = np.maximum(st.Y, 1e-3)[None]
+    row = np.max(np.abs(J) * xs, axis=1, keepdims=True) + 1e-300
+    assert np.max(np.abs(J - Jfd) * xs / row) < 1e-5
+    assert np.max(np.abs(J.sum(axis=0)) / (np.abs(J).sum(axis=0) + 1e-300)) < 1e-12
+
+    dt = synth.CONFIGS[8]["dt"]
+    st = synth.config_states(8, n=4, offset_seed=5)
+    rho = o.density(st.p, st.T, st.Y)
+    e = o.internal_energy(st.T, st.Y)
+    Yn, Tn, it, bad = o.cn_step(dt, rho, st.T, st.Y)
+    assert bad == 0 and np.all(it >= 2)
+    assert np.max(np.abs(Yn - st.Y)) > 1e-5
+    F = Yn - st.Y - dt / (2 * rho) * (o.source_at_energy(rho, e, Yn) + o.source_at_energy(rho, e, st.Y))
+    assert np.max(np.abs(F)) < 1e-14
+    assert np.max(np.abs(Yn.sum(axis=0) - st.Y.sum(axis=0))) < 1e-14
+    assert np.max(np.abs(o.internal_energy(Tn, Yn) - e) / np.abs(e)) < 1e-13
