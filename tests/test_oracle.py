@@ -313,6 +313,56 @@ def test_jacobian_complex_step_vs_central_fd(orc, idx):
 
 
 @pytest.mark.parametrize("idx", [0, 1])
+def test_jacobian_first_order_fd_error_is_linear_in_delta(orc, idx):
+    """The check of the paper's Jacobian section: the error of first-order forward
+    differences against the Jacobian falls linearly with the step until roundoff
+    takes over.  Per state, the column-scaled relative error E(delta) drops 10x
+    per decade from 1e-3 to 1e-6 (truncation, slope 1).  A missing or wrong term
+    in J would make E level off at the size of that term.  Below delta ~ 1e-8,
+    roundoff makes E grow again (E(1e-12) > 10 E(1e-8))."""
+    o = orc[0][idx]
+    n = 4
+    st = synth.config_states(idx, n=n, offset_seed=77)
+    rho = o.density(st.p, st.T, st.Y)
+    NP = o.N + 1
+    J = o.jacobian(rho, st.T, st.Y).reshape(NP, NP, n)
+    xs = np.concatenate([st.T[None], np.maximum(st.Y, 1e-3)], axis=0)
+
+    def rows(T, Y):
+        return np.concatenate([o.temperature_rate(rho, T, Y)[None], o.net_production_rates(rho, T, Y)], axis=0)
+
+    f0 = rows(st.T, st.Y)
+    Jfd = {}
+    for d in (1e-3, 1e-4, 1e-5, 1e-6, 1e-8, 1e-12):
+        Jfd[d] = np.zeros_like(J)
+        for c in range(NP):
+            h = d * xs[c]
+            T, Y = st.T.copy(), st.Y.copy()
+            if c == 0:
+                T = T + h
+            else:
+                Y[c - 1] = Y[c - 1] + h
+            Jfd[d][:, c] = (rows(T, Y) - f0) / h
+
+    def err(Jref):
+        return {d: np.array([np.linalg.norm((F[:, :, i] - Jref[:, :, i]) * xs[None, :, i]) /
+                             np.linalg.norm(Jref[:, :, i] * xs[None, :, i]) for i in range(n)])
+                for d, F in Jfd.items()}
+
+    E = err(J)
+    for d, d10 in ((1e-3, 1e-4), (1e-4, 1e-5), (1e-5, 1e-6)):
+        ratio = E[d] / E[d10]
+        assert np.all((ratio > 8.0) & (ratio < 12.0)), (d, ratio)
+    assert np.all(E[1e-6] < 1e-4)
+    assert np.all(E[1e-12] > 10 * E[1e-8])
+    # the check has teeth: a 0.1 % error in the T column levels E off
+    Jbad = J.copy()
+    Jbad[:, 0] *= 1.001
+    Eb = err(Jbad)
+    assert np.any(Eb[1e-5] / Eb[1e-6] < 8.0)
+
+
+@pytest.mark.parametrize("idx", [0, 1])
 def test_jvp_vjp_dot_product_identity(orc, idx):
     o = orc[0][idx]
     n = 8
