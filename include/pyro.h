@@ -191,7 +191,7 @@ int pyro_vjp(const pyro_mech* mech, int64_t n, const double* rho, const double* 
  * row 1+k = omega_k; column 0 = T, column 1+i = Y_i.  The library keeps a
  * per-handle scratch buffer for the per-reaction partials (allocated on first
  * use, grown as needed; 8 B x pyro_mech_stat("jacobian_scratch_doubles_per_point")
- * x 64 per resident block: ~0.1 GB for 53 species, ~3 GB for 160 species
+ * x 64 per resident block: ~0.6 GB for 53 species, ~3 GB for 160 species
  * and 1100 reactions): calls on one handle that use it (pyro_jacobian,
  * pyro_jacobian_adiabatic, pyro_cn_step) must not overlap on the GPU.  Needs
  * all species to share one NASA-7 T_mid. */
