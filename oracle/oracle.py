@@ -62,6 +62,7 @@ def lib():
         L.orc_net_production_rates_ld.argtypes = [P, I64, D, D, D, D]
         L.orc_temperature_rate.argtypes = [P, I64, D, D, D, D]
         L.orc_jacobian.argtypes = [P, I64, D, D, D, D]
+        L.orc_jacobian_gross.argtypes = [P, I64, D, D, D, D]
         L.orc_jvp.argtypes = [P, I64, D, D, D, D, D, D, D]
         L.orc_vjp.argtypes = [P, I64, D, D, D, D, D, D, D]
         L.orc_enthalpy.argtypes = [P, I64, D, D, D, D]
@@ -232,6 +233,41 @@ class Oracle:
         J = np.zeros((NP * NP, T.size))
         lib().orc_jacobian(self._h, T.size, _d(rho), _d(T), _d(Y), _d(J))
         return J
+
+    def jacobian_gross(self, rho, T, Y):
+        """[N+1, N+2, n] gross scale of each derivative entry (reading c15 carried
+        to derivatives): rows (Tdot, omega_1..N) x columns (rho, T, Y_1..N), the
+        magnitudes of the forward and reverse rates' derivatives summed with |nu|."""
+        rho, T, Y = _c(rho), _c(T), _c(Y)
+        G = np.zeros(((self.N + 1) * (self.N + 2), T.size))
+        lib().orc_jacobian_gross(self._h, T.size, _d(rho), _d(T), _d(Y), _d(G))
+        return G.reshape(self.N + 1, self.N + 2, T.size)
+
+    def jvp_scale(self, rho, T, Y, drho, dT, dY):
+        """[N, n] per-entry scale of the JVP: sum_c GJ_kc |v_c|."""
+        G = self.jacobian_gross(rho, T, Y)[1:]
+        v = np.concatenate([np.abs(_c(drho))[None], np.abs(_c(dT))[None], np.abs(_c(dY))], axis=0)
+        return np.einsum("kcn,cn->kn", G, v)
+
+    def vjp_scale(self, rho, T, Y, wbar):
+        """[N+2, n] per-entry scale of the VJP (rho_bar, T_bar, Y_bar): sum_k |u_k| GJ_kc."""
+        G = self.jacobian_gross(rho, T, Y)[1:]
+        return np.einsum("kcn,kn->cn", G, np.abs(_c(wbar)))
+
+    def jacobian_adiabatic_gross(self, rho, T, Y):
+        """[N*N, n] per-entry scale of dS_j/dY_k at fixed (rho, e):
+        W_j (GJ_jk + GJ_jT |dT/dY_k|), dT/dY_k = -e_k/c_v (Eq. int_energy, Eq. cv)."""
+        rho, T, Y = _c(rho), _c(T), _c(Y)
+        G = self.jacobian_gross(rho, T, Y)[1:]
+        _, cv = self.internal_energy(T, Y, with_cv=True)
+        ek = np.zeros((self.N, T.size))
+        for k in range(self.N):
+            Yk = np.zeros_like(Y)
+            Yk[k] = 1.0
+            ek[k] = self.internal_energy(T, Yk)
+        dTdY = np.abs(ek) / cv
+        S = self.W[:, None, None] * (G[:, 2:] + G[:, 1:2] * dTdY[None])
+        return S.reshape(self.N * self.N, T.size)
 
     def jacobian_adiabatic(self, rho, T, Y):
         """[N*N, n]: dS_j/dY_k (row j, column k) of S = W omega at fixed (rho, e)."""

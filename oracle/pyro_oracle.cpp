@@ -978,6 +978,62 @@ void orc_vjp(void* h, int64_t n, const double* rho, const double* T, const doubl
   }
 }
 
+// Gross scale of every derivative entry: reading (c15) carried over to the
+// derivatives.  The tolerance of a production-rate entry is set by the sizes of
+// the terms that cancel in it, so for omega_k and a variable x_c
+//   GJ_kc = sum_j |nu_kj| (|d Rf_j/d x_c| + |d Rr_j/d x_c|),
+// the forward and reverse rates of progress (Eq. reaction_rates) differentiated
+// separately by complex step.  For the temperature rate of the adiabatic
+// isochoric reactor, Tdot = -sum_k ehat_k omega_k / (rho c_v) with
+// ehat_k = h_k - R T (reading (c13)), the same magnitudes are carried through
+// its product and quotient rules:
+//   GJ_0c = [sum_k (|d ehat_k/d x_c| G_k + |ehat_k| GJ_kc)] / (rho c_v)
+//           + Tg |d(rho c_v)/d x_c| / (rho c_v),   Tg = sum_k |ehat_k| G_k / (rho c_v),
+// G_k = sum_j |nu_kj| (|Rf_j| + |Rr_j|) the gross scale of omega_k.
+// GJ[(r*(N+2) + c)*n + p]: rows r = 0 (Tdot), 1..N (omega_1..N); columns c = 0 (rho),
+// 1 (T), 2..N+1 (Y_1..Y_N).
+void orc_jacobian_gross(void* h, int64_t n, const double* rho, const double* T, const double* Y, double* GJ) {
+  OMech* m = (OMech*)h; const int N = m->N(), M = m->M(), NC = N + 2;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N), Rf(M), Rr(M), G(N, 0.0), eh(N), deh(N);
+    std::vector<cplx> yc(N), Rfc(M), Rrc(M);
+    for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
+    rates_of_progress(*m, rho[i], T[i], y.data(), Rf.data(), Rr.data());
+    std::vector<std::map<int, int>> nu(M);
+    for (int j = 0; j < M; ++j) {
+      for (auto& p : m->rx[j].prod) nu[j][p.first] += p.second;
+      for (auto& p : m->rx[j].reac) nu[j][p.first] -= p.second;
+      for (auto& q : nu[j]) G[q.first] += std::abs(q.second) * (std::fabs(Rf[j]) + std::fabs(Rr[j]));
+    }
+    const double cv = cv_mass(*m, T[i], y.data()), rcv = rho[i] * cv;
+    double Tg = 0.0;
+    for (int k = 0; k < N; ++k) {
+      eh[k] = R_GAS * T[i] * h_RT(m->sp[k], T[i]) - R_GAS * T[i];
+      cplx Tc(T[i], CS_H);
+      deh[k] = (R_GAS * Tc * h_RT(m->sp[k], Tc) - R_GAS * Tc).imag() / CS_H;   // cp_k - R
+      Tg += std::fabs(eh[k]) * G[k] / rcv;
+    }
+    for (int c = 0; c < NC; ++c) {
+      cplx rc(rho[i], c == 0 ? CS_H : 0.0), Tc(T[i], c == 1 ? CS_H : 0.0);
+      for (int k = 0; k < N; ++k) yc[k] = cplx(y[k], (c == k + 2) ? CS_H : 0.0);
+      rates_of_progress<cplx>(*m, rc, Tc, yc.data(), Rfc.data(), Rrc.data());
+      std::vector<double> col(N, 0.0);
+      for (int j = 0; j < M; ++j) {
+        const double df = std::fabs(Rfc[j].imag() / CS_H), dr = std::fabs(Rrc[j].imag() / CS_H);
+        for (auto& q : nu[j]) col[q.first] += std::abs(q.second) * (df + dr);
+      }
+      const double drcv = std::fabs((rc * cv_mass<cplx>(*m, Tc, yc.data())).imag() / CS_H);
+      double g0 = Tg * drcv / rcv;
+      for (int k = 0; k < N; ++k) {
+        g0 += ((c == 1 ? std::fabs(deh[k]) * G[k] : 0.0) + std::fabs(eh[k]) * col[k]) / rcv;
+        GJ[((int64_t)(k + 1) * NC + c) * n + i] = col[k];
+      }
+      GJ[(int64_t)c * n + i] = g0;
+    }
+  }
+}
+
 // Chemical Jacobian dS/dY at fixed (rho, e), [N*N][n]: J[(j*N + k)*n + p] = dS_j/dY_k.
 void orc_jacobian_adiabatic(void* h, int64_t n, const double* rho, const double* T, const double* Y,
                             double* J) {
