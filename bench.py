@@ -35,11 +35,28 @@ import numpy as np  # noqa: E402
 METRIC = "state-evals/sec (T solve + omega_k, FP64)"
 CONFIG_INDEX = 1
 # FP64 pipe of GB300: 2 DFMA lanes per SM per clock (measured by a DFMA
-# microbenchmark: 2.07 lanes/SM/clk), 152 SMs, 2070 MHz maximum SM clock.
+# microbenchmark: 2.07 lanes/SM/clk).  The SM count is read from the device and
+# the maximum SM clock from nvidia-smi (clocks.max.sm) at run time; the values
+# below (152 SMs, 2070 MHz: 1258.6 GFLOP/s) are used only where they cannot be read.
 FP64_LANES_PER_SM = 2
-N_SM = 152
-SM_MAX_MHZ = 2070.0
-FP64_PEAK_GFLOPS = 2.0 * FP64_LANES_PER_SM * N_SM * SM_MAX_MHZ / 1e3   # 1258.6 GFLOP/s (DFMA = 2 flops)
+N_SM_DEFAULT = 152
+SM_MAX_MHZ_DEFAULT = 2070.0
+FP64_PEAK_GFLOPS = 2.0 * FP64_LANES_PER_SM * N_SM_DEFAULT * SM_MAX_MHZ_DEFAULT / 1e3   # DFMA = 2 flops
+
+
+def fp64_peak_gflops(n_sm: int, sm_max_mhz: float) -> float:
+    return 2.0 * FP64_LANES_PER_SM * n_sm * sm_max_mhz / 1e3
+
+
+def sm_max_mhz_of(gpu_index: int) -> float:
+    """clocks.max.sm of the GPU from nvidia-smi (MHz), else the GB300 default."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        v = float(out.stdout.strip().splitlines()[0])
+        return v if v > 0 else SM_MAX_MHZ_DEFAULT
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        return SM_MAX_MHZ_DEFAULT
 
 # DRAM traffic of one launch of the timed kernel, from an ncu capture of this
 # kernel source (hash of the emitted source); None once the kernel changes.
@@ -234,6 +251,15 @@ def derivative_rates(mech, synth, dev, stream, args, rank):
         res[name + "_ms"] = ms
         res[name + "_per_s"] = n / (ms * 1e-3)
     res["jacobian_out_GB_per_s"] = 54 * 54 * 8 * n / (res["jacobian_ms"] * 1e-3) / 1e9
+    # FP64 roofline of each derivative kernel: the emitter's static FP64 flops per
+    # state x states/s, against the FP64 peak (Jacobian-evals/s vs FP64 roofline)
+    for name, key in (("jvp", "jvp_fp64_flops_per_point"), ("vjp", "vjp_fp64_flops_per_point"),
+                      ("jacobian", "jacobian_fp64_flops_per_point"),
+                      ("omega_isothermal", "omega_fp64_flops_per_point")):
+        f = mech.stat(key)
+        res[name + "_fp64_flops_per_state_static"] = f
+        res[name + "_gflops"] = f * res[name + "_per_s"] / 1e9
+        res[name + "_frac"] = f * res[name + "_per_s"] / (args.fp64_peak * 1e9)
     del J
     return res
 
@@ -294,19 +320,47 @@ def learned_guess_rates(mech, path, synth, dev, stream, args, rank):
 
 
 
-def large_mechanism_rates(synth, dev, stream, args, rank):
-    """160 species / 1100 reactions at 2^21 states (energy input): one thread per
-    state (emitted, species arrays in global scratch) against one warp per state
-    (table-driven); also the warp variant on the 53-species workload."""
-    import torch
-    from paper_2503_24286_gb300 import binding as B
+def large_mechanism_path(synth):
     d = tempfile.mkdtemp()
     path = os.path.join(d, "mech4.txt")
     synth.write_mechanism(synth.config_mechanism(4), path)
+    return path
+
+
+def start_large_compile(path):
+    """Compile the large mechanism's derivative groups (NVRTC, written to the
+    on-disk kernel cache) in a host thread on a compile-only handle, so the
+    minutes of compilation overlap the other rows; join() before the rows that
+    need them and before any CPU timing."""
+    import threading
+    from paper_2503_24286_gb300 import binding as B
+    err = []
+
+    def run():
+        try:
+            for opts in ("device=0", "device=0;variant=warp"):
+                B.Mechanism(path, opts).prepare("jvp,vjp")
+        except Exception as e:  # reported by the rows that need the groups
+            err.append(repr(e))
+    t = threading.Thread(target=run, daemon=True)
+    t.start()
+    return t, err
+
+
+def large_mechanism_rates(path, synth, dev, stream, args, rank):
+    """160 species / 1100 reactions at 2^21 states: T from e + omega, and the JVP and
+    VJP (intermediates recomputed, nothing stored), each with one thread per state
+    (emitted straight-line code, species arrays in a global scratch) against one
+    warp per state (lanes split the reactions); also the warp variant of the
+    forward on the 53-species workload.  Each row with its FP64 roofline fraction
+    (emitter's static FP64 flops per state)."""
+    import torch
+    from paper_2503_24286_gb300 import binding as B
     cfg = synth.CONFIGS[4]
     n = args.large_points
     res = {"workload": "synthetic 160 species / 1100 reactions (80 third-body, 60 Troe), %d states, "
-                       "T ~ U[300, 2800] K, p ~ U[1, 40] atm, T from e + omega" % n}
+                       "T ~ U[300, 2800] K, p ~ U[1, 40] atm; T from e + omega, JVP and VJP (unit-scale random "
+                       "seed vectors)" % n}
     mt = B.Mechanism(path)
     mw = B.Mechanism(path, "variant=warp")
     T, p, Y = synth.generate_states_torch(160, n, cfg["T"], cfg["p_atm"], synth.STATE_SEED_BASE + 4 + 7919 * rank, dev)
@@ -316,25 +370,61 @@ def large_mechanism_rates(synth, dev, stream, args, rank):
     w = torch.empty((160, n), dtype=torch.float64, device=dev)
     To = torch.empty(n, dtype=torch.float64, device=dev)
     steps = max(2, min(args.steps, 5))
-    for tag, m in (("thread_per_state", mt), ("warp_per_state", mw)):
+
+    def timed(f):
         for _ in range(3):
-            m.net_production_rates(rho, Y, e=e, T_out=To, out=w)
+            f()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
-            m.net_production_rates(rho, Y, e=e, T_out=To, out=w)
+            f()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        ms = max_over_ranks(e0.elapsed_time(e1) / steps, dev)
+        return max_over_ranks(e0.elapsed_time(e1) / steps, dev)
+
+    peak = args.fp64_peak * 1e9
+    f_fwd = mt.stat("omega_fp64_flops_per_point") + 2 * mt.stat("tsolve_collapse_fp64_ops") + \
+        3 * 2 * mt.stat("tsolve_iter_fp64_ops_mixed")
+    res["fp64_flops_per_state_static"] = f_fwd
+    for tag, m in (("thread_per_state", mt), ("warp_per_state", mw)):
+        ms = timed(lambda: m.net_production_rates(rho, Y, e=e, T_out=To, out=w))
         res[tag + "_ms"] = ms
         res[tag + "_states_per_s"] = n / (ms * 1e-3)
+        res[tag + "_frac"] = f_fwd * n / (ms * 1e-3) / peak
         assert m.nonconverged() == 0
-    res["fp64_flops_per_state_static"] = mt.stat("omega_fp64_flops_per_point")
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    d_rho = torch.randn(n, dtype=torch.float64, device=dev, generator=g) * rho * 1e-3
+    d_T = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+    d_Y = torch.randn((160, n), dtype=torch.float64, device=dev, generator=g) * 1e-4
+    w_bar = torch.randn((160, n), dtype=torch.float64, device=dev, generator=g)
+    args.large_compile.join()
+    deriv = {}
+    for tag, m in (("thread_per_state", mt), ("warp_per_state", mw)):
+        try:
+            if tag == "warp_per_state" and m.stat("deriv_warp_per_state") <= 0:
+                deriv[tag] = {"unavailable": "no warp-per-state derivative kernels for this mechanism"}
+                continue
+            m.prepare("jvp,vjp")
+        except B.PyroError as ex:
+            deriv[tag] = {"unavailable": str(ex)}
+            continue
+        r = {}
+        for name, f, key in (("jvp", lambda: m.jvp(rho, T, Y, d_rho, d_T, d_Y, out=w), "jvp_fp64_flops_per_point"),
+                             ("vjp", lambda: m.vjp(rho, T, Y, w_bar), "vjp_fp64_flops_per_point")):
+            ms = timed(f)
+            fl = m.stat(key)
+            r[name + "_ms"] = ms
+            r[name + "_states_per_s"] = n / (ms * 1e-3)
+            r[name + "_fp64_flops_per_state_static"] = fl
+            r[name + "_frac"] = fl * n / (ms * 1e-3) / peak
+        deriv[tag] = r
+    res["derivatives"] = deriv
     return res
 
 
-def large_derivative_rates(synth, dev, stream, args, rank):
+def large_derivative_rates(path, synth, dev, stream, args, rank):
     """The Jacobian-type kernels on the 160-species mechanism (rows from tables,
     species arrays in the global scratch): dense 161 x 161 Jacobian and dS/dY at
     fixed (rho, e) on 2^15 states, one Crank-Nicolson step of 2^14 states at
@@ -342,9 +432,6 @@ def large_derivative_rates(synth, dev, stream, args, rank):
     (the three units take minutes to compile)."""
     import torch
     from paper_2503_24286_gb300 import binding as B
-    d = tempfile.mkdtemp()
-    path = os.path.join(d, "mech4.txt")
-    synth.write_mechanism(synth.config_mechanism(4), path)
     parts = args.large_derivatives.split(",")
     m = B.Mechanism(path)
     m.prepare(args.large_derivatives)
@@ -483,7 +570,7 @@ def pressure_dependent_rates(synth, dev, stream, args, rank):
     return {"workload": "53 species / 325 reactions with 10 SRI falloff and 20 PLOG (3-5 nodes in [0.1, 100] atm) "
                         "reactions, %d states, T ~ U[300, 2800] K, p ~ U[0.5, 20] atm; T from e + omega" % n,
             "ms": ms, "states_per_s": n / (ms * 1e-3), "fp64_flops_per_state_static": flops,
-            "fp64_frac": flops * n / (ms * 1e-3) / (FP64_PEAK_GFLOPS * 1e9)}
+            "fp64_frac": flops * n / (ms * 1e-3) / (args.fp64_peak * 1e9)}
 
 
 def transport_rates(mech, synth, dev, stream, args, rank):
@@ -518,7 +605,7 @@ def transport_rates(mech, synth, dev, stream, args, rank):
     return {"workload": "53 species, %d states, T ~ U[300, 2800] K, Dirichlet Y; mu (Wilke), kappa, D_km" % n,
             "ms": ms, "states_per_s": n / (ms * 1e-3),
             "fp64_ops_per_state_static": ops,
-            "fp64_pipe_frac": ops * n / (ms * 1e-3) / (FP64_PEAK_GFLOPS * 1e9 / 2)}
+            "fp64_pipe_frac": ops * n / (ms * 1e-3) / (args.fp64_peak * 1e9 / 2)}
 
 
 def run_ours(args):
@@ -535,6 +622,14 @@ def run_ours(args):
         BLD.build()
     barrier()
     BLD.build()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = sm_max_mhz_of(local)
+    args.fp64_peak = fp64_peak_gflops(n_sm, sm_max)
+    path4 = None
+    if not args.no_large:
+        # the large mechanism's derivative units take minutes to compile: start now
+        path4 = large_mechanism_path(synth)
+        args.large_compile, large_compile_err = start_large_compile(path4)
     d = tempfile.mkdtemp()
     path = os.path.join(d, "mech.txt")
     synth.write_mechanism(synth.config_mechanism(CONFIG_INDEX), path)
@@ -592,13 +687,19 @@ def run_ours(args):
     h_T = torch.empty(n, dtype=torch.float64, pin_memory=True)
     h_w = torch.empty((53, n), dtype=torch.float64, pin_memory=True)
     a_rho, a_e, a_Y, a_T, a_w = (x.numpy() for x in (h_rho, h_e, h_Y, h_T, h_w))
-    e2e_steps = max(2, min(args.steps, 5))
-    mech.net_production_rates(a_rho, a_Y, e=a_e, T_out=a_T, out=a_w)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    h_T.zero_(); h_w.zero_()                      # every output page touched before timing
+    # each call is synchronous (host in, host out); its wall time is the step
+    e2e_calls = max(10, args.steps)
+    for _ in range(2):
         mech.net_production_rates(a_rho, a_Y, e=a_e, T_out=a_T, out=a_w)
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
+    barrier()
+    e2e_times = []
+    for _ in range(e2e_calls):
+        t0 = time.perf_counter()
+        mech.net_production_rates(a_rho, a_Y, e=a_e, T_out=a_T, out=a_w)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(statistics.median(e2e_times), dev)
+    e2e_min_s = max_over_ranks(min(e2e_times), dev)
     h2d = (n + n + 53 * n) * 8
     d2h = (53 * n + n) * 8
 
@@ -624,9 +725,11 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         ms_w = max_over_ranks(e0.elapsed_time(e1) / 3, dev)
         warp53 = {"ms": ms_w, "states_per_s": n / (ms_w * 1e-3)}
-        large = large_mechanism_rates(synth, dev, stream, args, rank)
+        large = large_mechanism_rates(path4, synth, dev, stream, args, rank)
+        if large_compile_err:
+            large["compile_error"] = large_compile_err[0]
         if args.large_derivatives:
-            large["derivatives"] = large_derivative_rates(synth, dev, stream, args, rank)
+            large["jacobian_type"] = large_derivative_rates(path4, synth, dev, stream, args, rank)
 
     pdep = None
     if not args.no_pdep:
@@ -656,11 +759,12 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(n),
                 "parallelism": "points sharded across ranks, no collective" if world > 1 else "1 GPU",
-                "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                             "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
-                             "peak_source": "FP64 pipe: 2 lanes/SM/clk x 152 SMs x 2070 MHz x 2 flops/DFMA",
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": args.fp64_peak, "unit": "GFLOP/s",
+                             "frac": achieved / args.fp64_peak, "traffic": traffic,
+                             "peak_source": "FP64 pipe: 2 lanes/SM/clk (DFMA microbenchmark) x %d SMs (device) x "
+                                            "%.0f MHz (nvidia-smi clocks.max.sm) x 2 flops/DFMA" % (n_sm, sm_max),
                              "flops_per_state": flops_pt,
-                             "frac_at_sampled_clock": (achieved / (FP64_PEAK_GFLOPS * clocks["sm_mhz"] / SM_MAX_MHZ)
+                             "frac_at_sampled_clock": (achieved / (args.fp64_peak * clocks["sm_mhz"] / sm_max)
                                                        if clocks.get("sm_mhz") else None)},
                 "cpu_baseline": {"value": rate_cpu, "unit": "states/s", "cores": cores, "kind": "oracle",
                                  "sample": "%d states of the same workload (seeded), T solve + omega, %.1f s"
@@ -668,7 +772,8 @@ def run_ours(args):
                                  "value_one_core": rate_1,
                                  "sample_one_core": "%d states, 1 thread, %.1f s" % (n1, dt_1)},
                 "e2e": {"value": world * n / e2e_s, "unit": "states/s", "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h},
+                        "d2h_bytes_per_step": d2h, "calls": e2e_calls, "statistic": "median call",
+                        "value_best_call": world * n / e2e_min_s},
                 "gpu_launches": launches,
                 "clocks": clocks,
                 "newton_iters_mean": iters_mean,

@@ -191,8 +191,8 @@ int pyro_vjp(const pyro_mech* mech, int64_t n, const double* rho, const double* 
  * row 1+k = omega_k; column 0 = T, column 1+i = Y_i.  The library keeps a
  * per-handle scratch buffer for the per-reaction partials (allocated on first
  * use, grown as needed; 8 B x pyro_mech_stat("jacobian_scratch_doubles_per_point")
- * x 64 per resident block: ~0.6 GB for 53 species, ~3 GB for 160 species
- * and 1100 reactions): calls on one handle that use it (pyro_jacobian,
+ * x deriv_block (default 64) x the resident blocks: with the defaults ~0.6 GB for
+ * 53 species, ~3 GB for 160 species and 1100 reactions): calls on one handle that use it (pyro_jacobian,
  * pyro_jacobian_adiabatic, pyro_cn_step) must not overlap on the GPU.  Needs
  * all species to share one NASA-7 T_mid. */
 int pyro_jacobian(const pyro_mech* mech, int64_t n, const double* rho, const double* T, const double* Y,
@@ -299,17 +299,25 @@ int pyro_mlp_load(pyro_mech* mech, const char* path);
  * staging buffers.  This entry point allocates nothing: the arrays (host or
  * device pointers, same layout and meaning as pyro_net_production_rates) and
  * the Newton failure counter are staged through one fixed scratch array of
- * PYRO_NOALLOC_SCRATCH_BYTES that the library holds, as a static device
- * variable, on every GPU that loads it, until the process exits.
+ * PYRO_NOALLOC_SCRATCH_BYTES that the library holds as a static device
+ * variable.  The array's 32 MiB are taken on a GPU when the first mechanism
+ * handle is loaded there (pyro_mech_load, which may allocate), and the GPU
+ * keeps them until the process exits.
  *  - Limit: the staged arrays need about 8 (2N + 3) bytes per state (N
  *    species), so one call takes at most ~32 MiB / (8 (2N + 3)) states
  *    (about 38 000 for 53 species); larger n returns PYRO_EINVAL with a message
  *    giving the limit.
- *  - The first call on a device looks up the scratch address on that device
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - pyro_mech_load also looks up the scratch's device address on its device
+ *    (cudaGetSymbolAddress), so no call of this entry point does any set-up;
+ *    call it only on the device the handle was loaded on.
  *  - Every call on a device shares the one scratch array, which keeps the
  *    previous call's contents (the failure counter is cleared by each call):
  *    calls that overlap on the GPU (other streams, other host threads) race.
+ *  - It runs the same kernel as pyro_net_production_rates on this handle (one
+ *    thread or one warp per state, see variant=).  With the thread kernel and
+ *    the species arrays in the handle's global scratch (store=global, e.g. 160
+ *    species) it also uses that scratch, so it must not overlap on the GPU with
+ *    a pyro_net_production_rates call on the same handle either.
  *  - The call is synchronous (returns after the results are copied out) and
  *    returns PYRO_ENOCONV if a Newton solve failed (input_is_energy != 0). */
 #define PYRO_NOALLOC_SCRATCH_BYTES (32u << 20)

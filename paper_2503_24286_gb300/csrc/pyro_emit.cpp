@@ -327,7 +327,7 @@ void emit_arg(Src& s, const Mechanism& m, const Reaction& r, double A, double b,
   s << "      double " << var << " = fma(" << lit(b) << ", lnT, " << lit((double)lnA) << ");";
   s << " " << var << " = fma(" << lit(-theta) << ", invT, " << var << ");";
   s.fma(2);
-  if (g_fold) { s << " " << var << " -= nuL;\n"; return; }
+  if (g_fold) { s << " " << var << " -= nuL;\n"; s.add(); return; }
   for (auto& p : r.reactants) {
     if (p.second == 1) { s << " " << var << " -= sL" << sidx(p.first) << ";"; s.add(); }
     else { s << " " << var << " = fma(" << lit(-(double)p.second) << ", sL" << sidx(p.first) << ", " << var << ");"; s.fma(); }
@@ -371,13 +371,14 @@ void emit_plog_arg(Src& s, const Mechanism& m, const Reaction& r, const std::str
        "      const double pf = fmin(fmax(pfu, 0.0), 1.0);\n"
        "      double " << var << " = fma(pf, pxb - pxa, pxa);";
   s.fma(5); s.add(3); s.mul(1); s.add(2 + (n > 2 ? n - 2 : 0));
-  if (g_fold) s << " " << var << " -= nuL;";
+  if (g_fold) { s << " " << var << " -= nuL;"; s.add(); }
   else for (auto& p : r.reactants) {
     if (p.second == 1) { s << " " << var << " -= sL" << sidx(p.first) << ";"; s.add(); }
     else { s << " " << var << " = fma(" << lit(-(double)p.second) << ", sL" << sidx(p.first) << ", " << var << ");"; s.fma(); }
   }
   s << "\n";
   if (deriv) {
+    s.add(2); s.mul(3); s.fma(4);
     s << "      const double pdx = (pfu > 0.0 && pfu < 1.0) ? (pxb - pxa) * pinv : 0.0;\n"
          "      const double pta_ = fma(pba, invT, pta * invT2), ptb_ = fma(pbb, invT, ptb * invT2);\n"
          "      const double " << var << "_tau = fma(pdx, invT, fma(pf, ptb_ - pta_, pta_));\n"
@@ -408,6 +409,7 @@ void emit_sri(Src& s, const Reaction& r, bool deriv) {
     << ")), s_exp);\n";
   s.mul(); s.exp_(); s.add(); s.log_(); s.fma(2); s.exp_();
   if (deriv) {
+    s.mul(9); s.fma(2); s.rcp_();
     s << "      const double dlnF_dlnPr = slS * (-2.0 * su * sX * sX * " << lit(inv_ln10) << ");\n"
          "      const double dlnF_dT = fma(sX * fma(sea, " << lit(b) << " * invT2, seb * " << lit(-1.0 / c)
       << "), pdm::rcp(sS), " << lit(e) << " * invT);\n";
@@ -604,15 +606,19 @@ void emit_species_deriv(Src& s, const Mechanism& m, const std::vector<SpeciesCoe
     s << "      const double Lp = fma(-hr, invT, invT);\n";
     s << "      const double E = PEXP(q, s_exp);\n";
     s << "      const double a = E * (rho * y);\n";
-    if (mode == DMode::JAC) s << "      (void)Lp; sA" << sidx(k) << " = a; sE" << sidx(k) << " = E * rho;";
+    s.fma(6); s.exp_(); s.mul(2);                      // L_k polynomial, exp, a_k
+    if (mode != DMode::JAC) s.fma(6);                   // h_k/RT and L'_k (dead code in JAC mode)
+    if (mode == DMode::JAC) { s << "      (void)Lp; sA" << sidx(k) << " = a; sE" << sidx(k) << " = E * rho;"; s.mul(); }
     else s << "      sL" << sidx(k) << " = q; sA" << sidx(k) << " = a;";
     if (mode == DMode::VJP) s << " sLp" << sidx(k) << " = Lp; sC" << sidx(k) << " = 0.0;";
     if (mode == DMode::JVP) {
       s << "\n      const double dy = __ldg(dYp + (i64)" << k << " * n);\n";
       s << "      sdA" << sidx(k) << " = fma(a, fma(Lp, dT, drr), E * (rho * dy)); sdL" << sidx(k) << " = Lp * dT;";
       s << " dysum = fma(dy, " << lit(1.0 / m.species[k].W) << ", dysum);";
+      s.fma(3); s.mul(3);
     }
     s << "\n      ysum = fma(y, " << lit(1.0 / m.species[k].W) << ", ysum); }\n";
+    s.fma();
   }
 }
 
@@ -644,16 +650,25 @@ std::string dprod(const std::vector<int>& f, const char* arr, const char* darr) 
   return "(" + e + ")";
 }
 
+// FP64 operations of dprod over nf factors: nf terms of (nf - 1) products, nf - 1 sums
+void count_dprod(Src& s, int nf) {
+  if (nf <= 1) return;
+  s.mul(nf * (nf - 1));
+  s.add(nf - 1);
+}
+
 // emits, inside a reaction block: x, kt, tau, [mS, M, kM], kk, Pf, Pr, D, R
 void emit_reaction_core(Src& s, const Mechanism& m, const Reaction& r) {
   if (r.kind == RX_PLOG) {
     emit_plog_arg(s, m, r, "x", true);
     s << "      const double kt = PEXP(x, s_exp);\n";
     s << "      double tau = x_tau;\n";
+    s.exp_();
   } else {
     emit_arg(s, m, r, r.A, r.b, r.theta, "x");
     s << "      const double kt = PEXP(x, s_exp);\n";
     s << "      double tau = fma(" << lit(r.b) << ", invT, " << lit(r.theta) << " * invT2);\n";
+    s.exp_(); s.fma(); s.mul();
   }
   if (r.kind == RX_ARRHENIUS) {
     s << "      const double kk = kt;\n";
@@ -661,40 +676,55 @@ void emit_reaction_core(Src& s, const Mechanism& m, const Reaction& r) {
     // k depends on the total concentration M = rho sum Y/W through ln p = ln(R T M)
     s << "      const double mS = ysum;\n      const double M = rho * mS;\n"
          "      const double kk = kt; const double kM = kt * x_pm * pdm::rcp(M);\n";
+    s.mul(3); s.rcp_();
   } else {
     s << "      double mS = ysum;";
     for (auto& e : r.efficiencies) {
       double c = (e.second - 1.0) / m.species[e.first].W;
-      if (c != 0.0) s << " mS = fma(__ldg(Yp + (i64)" << e.first << " * opq(n)), " << lit(c) << ", mS);";
+      if (c != 0.0) { s << " mS = fma(__ldg(Yp + (i64)" << e.first << " * opq(n)), " << lit(c) << ", mS);"; s.fma(); }
     }
     s << "\n      const double M = rho * mS;\n";
+    s.mul();
     if (r.kind == RX_THREEBODY) {
       s << "      const double kk = kt * M; const double kM = kt;\n";
+      s.mul();
     } else {
       const double inv_ln10 = (double)(1.0L / logl(10.0L));
       s << "      const double lnPr = fma(" << lit(r.b0 - r.b) << ", lnT, " << lit((double)(logl(r.A0) - logl(r.A)))
         << ") + fma(" << lit(-(r.theta0 - r.theta)) << ", invT, pdm::log(M, s_log));\n";
       s << "      const double pT = fma(" << lit(r.b0 - r.b) << ", invT, " << lit(r.theta0 - r.theta) << " * invT2);\n";
       s << "      const double fpr = pdm::rcp(1.0 + PEXP(-lnPr, s_exp));\n";
+      s.fma(3); s.add(2); s.mul(); s.log_(); s.exp_(); s.rcp_();   // lnPr, pT, fpr
       if (r.n_sri >= 3) {
         emit_sri(s, r, true);
         s << "      const double sPr = (1.0 - fpr) + dlnF_dlnPr;\n";
         s << "      tau += fma(sPr, pT, dlnF_dT);\n";
         s << "      const double kk = kt * fpr * F;\n";
+        s.add(3); s.fma(); s.mul(2);
       } else if (r.n_troe >= 3) {
         double a = r.troe[0], T3 = r.troe[1], T1 = r.troe[2];
-        if (a < 1.0)
+        if (a < 1.0) {
           s << "      const double t1 = PEXP(fma(T, " << lit(-1.0 / T3) << ", " << lit((double)logl(1.0L - a)) << "), s_exp);\n";
-        else
+          s.fma(); s.exp_();
+        } else {
           s << "      const double t1 = " << lit(1.0 - a) << " * PEXP(T * " << lit(-1.0 / T3) << ", s_exp);\n";
-        if (a > 0.0)
+          s.mul(2); s.exp_();
+        }
+        if (a > 0.0) {
           s << "      const double t2 = PEXP(fma(T, " << lit(-1.0 / T1) << ", " << lit((double)logl((long double)a)) << "), s_exp);\n";
-        else
+          s.fma(); s.exp_();
+        } else {
           s << "      const double t2 = 0.0;\n";
-        if (r.n_troe == 4)
+        }
+        if (r.n_troe == 4) {
           s << "      const double t3 = PEXP(" << lit(-r.troe[3]) << " * invT, s_exp);\n";
-        else
+          s.mul(); s.exp_();
+        } else {
           s << "      const double t3 = 0.0;\n";
+        }
+        // fc, dfc, lfc, cc, nn, xx, den, den2, rD, f, F, rD2, Axx, Aden, sPr, sfc, tau, kk
+        s.add(2); s.fma(2); s.mul(2); s.log_(); s.mul(); s.fma(4); s.mul(); s.fma(); s.rcp_(); s.mul(3); s.exp_();
+        s.mul(1 + 4 + 5); s.fma(1); s.add(2); s.fma(2); s.fma(); s.mul(2); s.rcp_(); s.add(); s.mul(2);
         s << "      const double fc = t1 + t2 + t3;\n";
         s << "      const double dfc = fma(t1, " << lit(-1.0 / T3) << ", fma(t2, " << lit(-1.0 / T1) << ", t3 * "
           << lit(r.n_troe == 4 ? r.troe[3] : 0.0) << " * invT2));\n";
@@ -711,16 +741,22 @@ void emit_reaction_core(Src& s, const Mechanism& m, const Reaction& r) {
         s << "      const double kk = kt * fpr * F;\n";
       } else {
         s << "      const double sPr = 1.0 - fpr;\n      tau += sPr * pT;\n      const double kk = kt * fpr;\n";
+        s.add(2); s.mul(2);
       }
       s << "      const double kM = kk * sPr * pdm::rcp(M);\n";
+      s.mul(2); s.rcp_();
     }
   }
   s << "      const double Pf = " << prod_of(side_factors(r.reactants), "sA") << ";\n";
-  if (r.reversible)
+  s.mul((int)side_factors(r.reactants).size() - 1);
+  if (r.reversible) {
     s << "      const double Pr = " << prod_of(side_factors(r.products), "sA") << ";\n";
-  else
+    s.mul((int)side_factors(r.products).size() - 1); s.add();
+  } else {
     s << "      const double Pr = 0.0;\n";
+  }
   s << "      const double D = Pf - Pr;\n      const double R = kk * D;\n";
+  s.mul();
 }
 
 // net (nu'' - nu') over species of a reaction, and the set of species
@@ -752,9 +788,12 @@ void emit_jvp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
        "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
        "    const double drr = drho * pdm::rcp(rho);\n"
        "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
+  s.log_(); s.rcp_(); s.mul(); s.rcp_(); s.mul();
   emit_species_deriv(s, m, C, DMode::JVP);
-  if (has_plog(m))
+  if (has_plog(m)) {
     s << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lit((double)logl(R_GAS)) << ";\n";
+    s.log_(); s.mul(); s.add(2);
+  }
   g_acc.mem = opt.acc_mem;
   g_acc.base = "Wp";
   if (opt.acc_mem) s << "    double* Wp = g_dw + p;\n";
@@ -764,23 +803,33 @@ void emit_jvp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
     s << "    { // reaction " << j << "\n";
     emit_reaction_core(s, m, r);
     s << "      double dx = tau * dT;";
-    for (auto& p : r.reactants) s << " dx = fma(" << lit(-(double)p.second) << ", sdL" << sidx(p.first) << ", dx);";
+    s.mul();
+    for (auto& p : r.reactants) { s << " dx = fma(" << lit(-(double)p.second) << ", sdL" << sidx(p.first) << ", dx);"; s.fma(); }
     s << "\n";
     if (r.kind == RX_ARRHENIUS) {
       s << "      const double dkk = kk * dx;\n";
+      s.mul();
     } else {
       s << "      double dmS = dysum;";
       for (auto& e : r.efficiencies) {
         double c = (e.second - 1.0) / m.species[e.first].W;
-        if (c != 0.0) s << " dmS = fma(__ldg(dYp + (i64)" << e.first << " * opq(n)), " << lit(c) << ", dmS);";
+        if (c != 0.0) { s << " dmS = fma(__ldg(dYp + (i64)" << e.first << " * opq(n)), " << lit(c) << ", dmS);"; s.fma(); }
       }
       s << "\n      const double dM = fma(drho, mS, rho * dmS);\n";
       s << "      const double dkk = fma(kk, dx, kM * dM);\n";
+      s.fma(2); s.mul(2);
     }
     s << "      const double dPf = " << dprod(side_factors(r.reactants), "sA", "sdA") << ";\n";
-    if (r.reversible) s << "      const double dPr = " << dprod(side_factors(r.products), "sA", "sdA") << ";\n";
-    else s << "      const double dPr = 0.0;\n";
+    count_dprod(s, (int)side_factors(r.reactants).size());
+    if (r.reversible) {
+      s << "      const double dPr = " << dprod(side_factors(r.products), "sA", "sdA") << ";\n";
+      count_dprod(s, (int)side_factors(r.products).size());
+      s.add();
+    } else {
+      s << "      const double dPr = 0.0;\n";
+    }
     s << "      const double dR = fma(dkk, D, kk * (dPf - dPr));\n     ";
+    s.fma(); s.mul();
     emit_omega_update(s, r, "dR");
     s << "    }\n";
   }
@@ -806,9 +855,12 @@ void emit_vjp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
        "    const double rho = g_rho[p], T = g_T[p];\n"
        "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
        "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
+  s.log_(); s.rcp_(); s.mul();
   emit_species_deriv(s, m, C, DMode::VJP);
-  if (has_plog(m))
+  if (has_plog(m)) {
     s << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lit((double)logl(R_GAS)) << ";\n";
+    s.log_(); s.mul(); s.add(2);
+  }
   s << "    double Tb = 0.0, Mtot = 0.0, rhobM = 0.0;\n";
   g_acc.mem = opt.acc_mem;
   g_acc.base = "Ab";
@@ -822,25 +874,36 @@ void emit_vjp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
     for (auto& q : net_nu(r)) {
       if (q.second == 0) continue;
       s << " Rb = fma(" << lit((double)q.second) << ", __ldg(Wb + (i64)" << q.first << " * opq(n)), Rb);";
+      s.fma();
     }
     s << "\n";
     emit_reaction_core(s, m, r);
     s << "      const double xb = Rb * R;\n      Tb = fma(xb, tau, Tb);";
-    for (auto& p : r.reactants) s << " Tb = fma(" << lit(-(double)p.second) << " * xb, sLp" << sidx(p.first) << ", Tb);";
+    s.mul(); s.fma();
+    for (auto& p : r.reactants) {
+      s << " Tb = fma(" << lit(-(double)p.second) << " * xb, sLp" << sidx(p.first) << ", Tb);";
+      s.fma(); if (p.second != 1) s.mul();
+    }
     s << "\n      const double Db = Rb * kk;\n";
+    s.mul();
     auto fr = side_factors(r.reactants);
-    for (int q = 0; q < (int)fr.size(); ++q)
+    for (int q = 0; q < (int)fr.size(); ++q) {
       s << "      " << acc("ab", fr[q]) << " = fma(Db, " << prod_of(fr, "sA", q) << ", " << acc("ab", fr[q]) << ");\n";
+      s.fma(); s.mul(std::max(0, (int)fr.size() - 2));
+    }
     if (r.reversible) {
       auto fp = side_factors(r.products);
-      for (int q = 0; q < (int)fp.size(); ++q)
+      for (int q = 0; q < (int)fp.size(); ++q) {
         s << "      " << acc("ab", fp[q]) << " = fma(-Db, " << prod_of(fp, "sA", q) << ", " << acc("ab", fp[q]) << ");\n";
+        s.fma(); s.mul(std::max(0, (int)fp.size() - 2));
+      }
     }
     if (r.kind != RX_ARRHENIUS) {
       s << "      const double Mb = Rb * kM * D; Mtot += Mb; rhobM = fma(Mb, mS, rhobM);\n";
+      s.mul(2); s.add(); s.fma();
       for (auto& e : r.efficiencies) {
         double c = (e.second - 1.0) / m.species[e.first].W;
-        if (c != 0.0) s << "      sC" << sidx(e.first) << " = fma(Mb, " << lit(c) << ", sC" << sidx(e.first) << ");\n";
+        if (c != 0.0) { s << "      sC" << sidx(e.first) << " = fma(Mb, " << lit(c) << ", sC" << sidx(e.first) << ");\n"; s.fma(); }
       }
     }
     s << "    }\n";
@@ -851,9 +914,11 @@ void emit_vjp_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>&
       << "; Tb = fma(ta, sLp" << sidx(k) << ", Tb); rhob += ta;\n";
     s << "      g_Yb[(i64)" << k << " * n + p] = fma(abk, PEXP(sL" << sidx(k) << ", s_exp) * rho, rho * fma(Mtot, "
       << lit(1.0 / m.species[k].W) << ", sC" << sidx(k) << ")); }\n";
+    s.mul(3); s.fma(3); s.add(); s.exp_();
   }
   g_acc.mem = false;
   s << "    g_Tb[p] = Tb;\n    g_rhob[p] = fma(rhob, pdm::rcp(rho), rhobM);\n  }\n}\n";
+  s.rcp_(); s.fma();
 }
 
 struct JacSlots {
@@ -967,6 +1032,31 @@ std::string jac_table_row_terms(const std::string& sfx, const std::string& add) 
          "          }\n"
          "        }\n"
          "      }\n";
+}
+
+// FP64 operations of the table-driven row assembly (per state): per row the sums
+// over its reactions, the species energy (ty: (T, Y) Jacobian with the Tdot
+// column accumulators) or the row factor, the dense rank-1 fill and the species
+// terms of every reaction of the row.
+void count_table_rows(Src& s, const Mechanism& m, const JacSlots& sl, bool ty) {
+  const int N = m.n_species();
+  for (int k = 0; k < N; ++k) {
+    for (int j = 0; j < m.n_reactions(); ++j) {
+      int nu = 0;
+      for (auto& q : net_nu(m.reactions[j])) if (q.first == k) nu = q.second;
+      if (!nu) continue;
+      s.fma(2 + (sl.RM[j] >= 0 ? 1 : 0));                          // w, jt, u sums
+      const int nq = (int)sl.Q[j].size();
+      if (ty) { s.mul(nq); s.add(nq); s.fma(nq); } else { s.mul(nq); s.fma(nq); }
+      if (sl.RM[j] >= 0) {
+        s.mul();                                                     // ru
+        for (auto& e : m.reactions[j].efficiencies)
+          if (e.second != 1.0) { s.mul(2); if (ty) { s.add(); s.fma(); } else s.fma(); }
+      }
+    }
+    if (ty) { s.fma(5 + 4 + 1 + 4); s.add(); s.mul(1 + N); }          // h/RT, cp/R, e_k, 4 sums, cpm, dense fill
+    else { s.mul(2); s.fma(N); s.mul(N); }                           // fu, fj, dense fill
+  }
 }
 
 void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesCoef>& C, int blk, int* nslots,
@@ -1094,9 +1184,12 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
   }
   s << "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
        "    const bool hi = pdm::to_float_trunc(T) >= (float)TMID;\n";
+  s.log_(); s.rcp_(); s.mul();
   emit_species_deriv(s, m, C, DMode::JAC);
-  if (has_plog(m))
+  if (has_plog(m)) {
     s << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lit((double)logl(R_GAS)) << ";\n";
+    s.log_(); s.mul(); s.add(2);
+  }
   // ---- phase 1
   s << "    const int fr = hi ? 13 : 0;\n";
   for (int j = 0; j < M; ++j) {
@@ -1105,6 +1198,7 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
     s << "      const double* fj = " << ftab << " + " << 26 * j << " + fr;\n"
          "      const double nuL = fma(__ldg(fj), lnT, fma(__ldg(fj + 1), invT, fma(T, fma(T, fma(T, fma(T, __ldg(fj + 6), "
          "__ldg(fj + 5)), __ldg(fj + 4)), __ldg(fj + 3)), __ldg(fj + 2))));\n";
+    s.fma(6);
     g_fold = true;
     emit_reaction_core(s, m, r);
     g_fold = false;
@@ -1116,7 +1210,8 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
          "__ldg(fj + 9)), __ldg(fj + 8)), __ldg(fj + 7)));\n"
          "      const double dS = (" << lit((double)fold_c[j]) << " - Hj) * invT;\n";
     s << "      " << slot(sl.R[j]) << " = R; " << slot(sl.Rt[j]) << " = kk * fma(D, tau, Pr * dS);\n";
-    if (sl.RM[j] >= 0) s << "      " << slot(sl.RM[j]) << " = kM * D;\n";
+    s.fma(5); s.add(); s.mul(); s.mul(2); s.fma();
+    if (sl.RM[j] >= 0) { s << "      " << slot(sl.RM[j]) << " = kM * D;\n"; s.mul(); }
     auto fr = side_factors(r.reactants);
     auto fp = side_factors(r.products);
     for (int i : sp) {
@@ -1131,6 +1226,11 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
           if (fp[q] == i) { termr = "(" + lit((double)nu_of(r.products, i)) + " * " + prod_of(fp, "sA", q) + ")"; break; }
       std::string diff = termf.empty() ? "-" + termr : termr.empty() ? termf : termf + " - " + termr;
       s << "      " << slot(sl.Q[j][i]) << " = kk * sE" << sidx(i) << " * (" << diff << ");\n";
+      // kk * sE * (.), the products of the other factors, nu * product (nu != 1), the difference
+      s.mul(2);
+      if (!termf.empty()) { s.mul(std::max(0, (int)fr.size() - 2)); if (nr_ != 1) s.mul(); }
+      if (!termr.empty()) { s.mul(std::max(0, (int)fp.size() - 2)); if (nu_of(r.products, i) != 1) s.mul(); }
+      if (!termf.empty() && !termr.empty()) s.add();
     }
     s << "    }\n";
   }
@@ -1154,14 +1254,17 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
       s << "      sA" << sidx(i) << " = fma(RT, hr, -RT) * " << lit(1.0 / m.species[i].W) << ";\n";
       s << "      cv = fma(y * " << lit((double)R_GAS / m.species[i].W) << ", cp - 1.0, cv);\n";
       s << "      sE" << sidx(i) << " = rho * " << lit(1.0 / m.species[i].W) << "; }\n";
+      s.fma(5 + 4 + 1 + 1); s.mul(3); s.add();   // h/RT, cp/R, e_i, c_v term, rho/W_i
     }
     s << "    const double mrcv = -pdm::rcp(cv);\n";
     s << "    #pragma unroll 1\n    for (int i = 0; i < NSP; ++i) sA[i * BLKD + t] *= mrcv;\n";
+    s.mul(1 + N); s.rcp_();
     if (mode == JacMode::CN) {
       s << "    const double hh = 0.5 * dt * pdm::rcp(rho);\n";
       s << "    const i64 nr = CN_G;\n";
     }
     if (table) {
+      count_table_rows(s, m, sl, false);
       // rows by loops over the tables; the entries of row k accumulate in place
       s << "    #pragma unroll 1\n    for (int k = 0; k < NSP; ++k) {\n"
            "      const int re0 = __ldg(pyro_jr_ptr" << sfx << " + k), re1 = __ldg(pyro_jr_ptr" << sfx << " + k + 1);\n"
@@ -1212,6 +1315,13 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
           }
         }
       }
+      for (auto& jn : rows[k]) {
+        const int j = jn.first;
+        s.fma(2 + (sl.RM[j] >= 0 ? 1 : 0) + (int)sl.Q[j].size());
+        if (sl.RM[j] >= 0)
+          for (auto& e : m.reactions[j].efficiencies) if (e.second != 1.0) s.fma();
+      }
+      s.mul(2); s.fma(N); s.mul(N);                  // fu, fj, dense fill
       // row factor: W_k (Jacobian of S = W omega), or -dt/(2 rho) W_k (Newton matrix)
       if (mode == JacMode::CN) s << "      const double F = -hh * " << lit(m.species[k].W) << ";\n";
       else s << "      const double F = " << lit(m.species[k].W) << ";\n";
@@ -1225,6 +1335,8 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
         std::string dst = "Jr[(i64)" + std::to_string(i) + " * nr]";
         bool hs = acc.count(i), hc = cr.count(i), diag = mode == JacMode::CN && i == k;
         if (hs || hc) {
+          if (hc) s.fma();
+          s.fma(2); s.mul();
           std::string tv = hc ? "fma(" + si + ", " + cr[i] + ", " + (hs ? acc[i] : std::string("0.0")) + ")" : acc[i];
           std::string base = diag ? "fma(F, " + tv + ", 1.0)" : "F * " + tv;
           s << "      " << dst << " = fma(" << si << ", fu, fma(fj, " << ti << ", " << base << "));\n";
@@ -1251,12 +1363,14 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
   for (int i = 0; i < N; ++i)
     s << "    sE" << sidx(i) << " = rho * " << lit(1.0 / m.species[i].W) << "; sA" << sidx(i) << " = 0.0;\n";
   s << "    const double RT = " << lit((double)R_GAS) << " * T;\n";
+  s.mul(N + 1);
   s << "    double sum_ew = 0.0, sum_cpw = 0.0, sum_ejt = 0.0, U = 0.0;\n";
   // per-species row lists
   std::vector<std::vector<std::pair<int, int>>> rows(N);
   for (int j = 0; j < M; ++j)
     for (auto& q : net_nu(m.reactions[j])) if (q.second) rows[q.first].push_back({j, q.second});
   if (table) {
+    count_table_rows(s, m, sl, true);
     // rows by loops over the tables; the entries of row k accumulate in place and
     // each species term also feeds the Tdot column accumulator sA_i (weight e_k)
     s << "    #pragma unroll 1\n    for (int k = 0; k < NSP; ++k) {\n"
@@ -1277,6 +1391,13 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
   }
   for (int k = 0; k < (table ? 0 : N); ++k) {
     const SpeciesCoef& c = C[k];
+    for (auto& jn : rows[k]) {
+      const int j = jn.first;
+      s.fma(2 + (sl.RM[j] >= 0 ? 1 : 0) + (int)sl.Q[j].size());
+      if (sl.RM[j] >= 0)
+        for (auto& e : m.reactions[j].efficiencies) if (e.second != 1.0) s.fma();
+    }
+    s.fma(5 + 4 + 1 + 4); s.add(); s.mul(1 + N);   // h/RT, cp/R, e_k, 4 sums, cpm, dense fill
     s << "    { // row of species " << k << "\n      double w = 0.0, jt = 0.0, u = 0.0;\n";
     std::map<int, std::string> acc, cr;
     for (auto& jn : rows[k]) {
@@ -1316,6 +1437,7 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
       std::string dst = "Jr[(i64)" + std::to_string(1 + i) + " * nr]";
       bool hs = acc.count(i), hc = cr.count(i);
       if (hs || hc) {
+        s.fma(2 + (hc ? 1 : 0));
         std::string tv = hc ? "fma(" + si + ", " + cr[i] + ", " + (hs ? acc[i] : std::string("0.0")) + ")" : acc[i];
         s << "      { const double tv = " << tv << "; " << dst << " = fma(" << si << ", u, tv); sA" << sidx(i)
           << " = fma(eh, tv, sA" << sidx(i) << "); }\n";
@@ -1336,10 +1458,12 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
       << "); cp = fma(T, cp, " << sel(p1) << "); cp = fma(T, cp, " << sel(p0) << ");\n";
     s << "      double cd = fma(T, " << sel(q3) << ", " << sel(q2) << "); cd = fma(T, cd, " << sel(q1) << "); cd = fma(T, cd, " << sel(q0) << ");\n";
     s << "      cv = fma(yw, cp - 1.0, cv); cvT = fma(yw, cd, cvT); }\n";
+    s.mul(); s.fma(4 + 3 + 2); s.add();
   }
   s << "    const double rcv = pdm::rcp(rho * cv);\n    const double Tdot = -sum_ew * rcv;\n"
        "    const double tcv = Tdot * pdm::rcp(cv);\n"
        "    Jp[0] = fma(-(sum_cpw + sum_ejt), rcv, -tcv * cvT);\n";
+  s.mul(4); s.rcp_(); s.rcp_(); s.add(); s.fma();
   // Tdot row: d c_v/dY_i = (cp_i/R - 1) R/W_i recomputed per entry
   for (int k = 0; k < N; ++k) {
     const SpeciesCoef& c = C[k];
@@ -1349,6 +1473,7 @@ void emit_jacobian_kernel(Src& s, const Mechanism& m, const std::vector<SpeciesC
       << "); cp = fma(T, cp, " << sel(p1) << "); cp = fma(T, cp, " << sel(p0) << ");\n"
       << "      Jp[(i64)" << 1 + k << " * opq(n)] = fma(-fma(sE" << sidx(k) << ", U, sA" << sidx(k) << "), rcv, -tcv * ((cp - 1.0) * "
       << lit((double)R_GAS / m.species[k].W) << ")); }\n";
+    s.fma(4 + 2); s.add(); s.mul(2);
   }
   s << "  }\n}\n";
 }
@@ -2191,15 +2316,21 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, cons
   pre << "#define BLKD " << opt.deriv_block << "\n";
   {
     Src d; d << pre.o.str(); emit_jvp_kernel(d, m, C, opt.deriv_block, opt); out.group_sources["jvp"] = d.o.str();
+    out.stats["jvp_fp64_flops_per_point"] = d.flops();
+    out.stats["jvp_fp64_ops_per_point"] = d.ops();
   }
   {
     Src d; d << pre.o.str(); emit_vjp_kernel(d, m, C, opt.deriv_block, opt); out.group_sources["vjp"] = d.o.str();
+    out.stats["vjp_fp64_flops_per_point"] = d.flops();
+    out.stats["vjp_fp64_ops_per_point"] = d.ops();
   }
   int nslots = 0;
   {
     Src d; d << pre.o.str();
     emit_jacobian_kernel(d, m, C, opt.deriv_block, &nslots, JacMode::TY, opt.dgstore, opt.jac_table);
     out.group_sources["jac"] = d.o.str();
+    out.stats["jacobian_fp64_flops_per_point"] = d.flops();
+    out.stats["jacobian_fp64_ops_per_point"] = d.ops();
   }
   // Jacobian-type kernels: two per-state species arrays, in shared memory or (large
   // mechanisms) after the slots in the per-block global scratch
@@ -2212,6 +2343,8 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, cons
     Src d; d << pre.o.str();
     emit_jacobian_kernel(d, m, C, opt.deriv_block, &ns2, JacMode::ADIA, opt.dgstore, opt.jac_table);
     out.group_sources["jad"] = d.o.str();
+    out.stats["jacobian_adiabatic_fp64_flops_per_point"] = d.flops();
+    out.stats["jacobian_adiabatic_fp64_ops_per_point"] = d.ops();
   }
   if (m.has_transport) {
     Src d;
@@ -2251,6 +2384,7 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, cons
   }
   out.smem_dyn_bytes_deriv = opt.dgstore ? 0 : 4 * N * opt.deriv_block * (int)sizeof(double);
   out.stats["jacobian_scratch_doubles_per_point"] = nslots;
+  out.stats["deriv_warp_per_state"] = 0;
   out.stats["deriv_block"] = opt.deriv_block;
 
   out.stats["omega_fp64_ops_per_point"] = r.ops();

@@ -27,6 +27,12 @@ int internal_launch_omega(const pyro_mech* h, int64_t n, const void* rho, const 
                           int input_is_energy, const void* Y, void* T_out, void* omega,
                           unsigned long long* fail, void* stream);
 
+// Look up, on the current device, the address of the static scratch of
+// pyro_net_production_rates_noalloc (pyro_noalloc.cu) and keep it.  Called by
+// pyro_mech_load, so the scratch's module is loaded and its memory taken while
+// loading a handle rather than inside a no-allocation call.
+int noalloc_prepare_device();
+
 // ---- learned initial guess (pyro_mlp.cu) ----
 struct MlpState;
 int mlp_n_params(int D);

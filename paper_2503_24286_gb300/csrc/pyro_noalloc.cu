@@ -6,9 +6,11 @@
 // must not take cudaMalloc's implicit device-wide synchronisation.  For them,
 // this entry point stages the caller's arrays and the Newton failure counter
 // through one fixed scratch array that lives in this file as a static device
-// variable; it is created when the library is loaded onto a GPU and held by
-// every GPU that loads the library until the process exits.  Nothing here calls
-// cudaMalloc, cudaFree or any allocating routine.
+// variable.  Its module is loaded, and its memory taken, when the first
+// mechanism handle is loaded on a GPU (pyro_mech_load calls
+// noalloc_prepare_device, which also looks up the array's device address), and
+// every GPU that loads a handle keeps it until the process exits.  The entry
+// point itself calls no cudaMalloc, cudaFree or any other allocating routine.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -53,6 +55,13 @@ int scratch_address(void** out) {
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 }  // namespace
+
+namespace pyro {
+int noalloc_prepare_device() {
+  void* p = nullptr;
+  return scratch_address(&p);
+}
+}  // namespace pyro
 
 extern "C" int pyro_net_production_rates_noalloc(const pyro_mech* mech, int64_t n, const double* rho,
                                                  const double* T_or_e, int input_is_energy,

@@ -711,6 +711,9 @@ int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) 
     pyro_mech_free(h);
     return fail(PYRO_ECUDA, "failure counter allocation");
   }
+  // the no-allocation entry point's static scratch: its module is loaded (and its
+  // device memory taken) here, where allocating is allowed, not in its first call
+  if (int rc = pyro::noalloc_prepare_device()) { pyro_mech_free(h); return rc; }
   *out = h;
   return PYRO_OK;
 }
@@ -1310,6 +1313,10 @@ int internal_launch_omega(const pyro_mech* h, int64_t n, const void* rho, const 
   int em = input_is_energy ? 1 : 0;
   double Tg = 1200.0, tol = 1e-10;
   int max_iter = 50;
+  // the same kernel choice as pyro_net_production_rates (thread or warp per state)
+  if (h->warp)
+    return pyro::warp_launch_omega(h->warp, h->num_sms, n, (const double*)rho, (const double*)T_or_e, em,
+                                   (const double*)Y, (double*)T_out, (double*)omega, fail_ctr, (cudaStream_t)stream);
   void* store = h->d_store;
   void* params[] = {&nn, &rho, &T_or_e, &em, &Y, &T_out, &omega, &Tg, &max_iter, &tol, &fail_ctr, &store};
   return launch(h, h->f_omega, n, h->omega_blocks_per_sm, h->emitted.smem_dyn_bytes_omega, stream, params);

@@ -15,7 +15,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL_W = 1e-11
-TOL_D = 1e-9
+TOL_D = 1e-11   # of each derivative entry's gross scale (the oracle's GJ)
 
 
 @pytest.fixture(scope="module")
@@ -71,26 +71,20 @@ def test_large_jvp_vjp_parity(large, dev):
     u = rng.standard_normal((160, n))
     g = m.jvp(*[_t(a, dev) for a in (rho, st.T, st.Y, dr, dT, dY)]).cpu().numpy()
     rb, Tb, Yb = (x.cpu().numpy() for x in m.vjp(_t(rho, dev), _t(st.T, dev), _t(st.Y, dev), _t(u, dev)))
-    # oracle d omega/d(rho, T, Y) by complex-step JVPs along unit directions
-    J = np.zeros((160, 162, n))
-    for c in range(162):
-        e_ = np.zeros((162, n))
-        e_[c] = 1.0
-        J[:, c] = orc.jvp(rho, st.T, st.Y, e_[0], e_[1], e_[2:])
-    v = np.concatenate([dr[None], dT[None], dY], axis=0)
-    ref = np.einsum("kcn,cn->kn", J, v)
-    assert np.all(np.abs(g - ref) <= TOL_D * np.einsum("kcn,cn->kn", np.abs(J), np.abs(v)) + 1e-300)
-    refb = np.einsum("kcn,kn->cn", J, u)
-    sc = np.einsum("kcn,kn->cn", np.abs(J), np.abs(u))
-    assert np.all(np.abs(rb - refb[0]) <= TOL_D * sc[0] + 1e-300)
-    assert np.all(np.abs(Tb - refb[1]) <= TOL_D * sc[1] + 1e-300)
-    assert np.all(np.abs(Yb - refb[2:]) <= TOL_D * sc[2:] + 1e-300)
+    ref = orc.jvp(rho, st.T, st.Y, dr, dT, dY)
+    sc = orc.jvp_scale(rho, st.T, st.Y, dr, dT, dY)
+    assert np.all(np.abs(g - ref) <= TOL_D * sc + 1e-300)
+    orb, oTb, oYb = orc.vjp(rho, st.T, st.Y, u)
+    sc = orc.vjp_scale(rho, st.T, st.Y, u)
+    assert np.all(np.abs(rb - orb) <= TOL_D * sc[0] + 1e-300)
+    assert np.all(np.abs(Tb - oTb) <= TOL_D * sc[1] + 1e-300)
+    assert np.all(np.abs(Yb - oYb) <= TOL_D * sc[2:] + 1e-300)
 
 
 def test_large_jacobian_matches_oracle(large, dev):
     """Dense d(Tdot, omega)/d(T, Y), 161 x 161 per state, rows from tables, species
-    arrays in the global scratch: against the oracle's complex-step Jacobian, with
-    the column scales and row-relative bound of the 53-species test."""
+    arrays in the global scratch: against the oracle's complex-step Jacobian, each
+    entry within 1e-11 of its gross scale."""
     m, orc = large
     assert m.stat("jacobian_rows_from_tables") == 1 and m.stat("deriv_store_global") == 1
     n, NP = 12, 161
@@ -98,10 +92,9 @@ def test_large_jacobian_matches_oracle(large, dev):
     rho = orc.density(st.p, st.T, st.Y)
     J = m.jacobian(_t(rho, dev), _t(st.T, dev), _t(st.Y, dev)).cpu().numpy().reshape(NP, NP, n)
     Jo = orc.jacobian(rho, st.T, st.Y).reshape(NP, NP, n)
-    xs = np.concatenate([st.T[None], np.maximum(st.Y, 1e-3)], axis=0)
-    row = np.max(np.abs(Jo) * xs[None], axis=1, keepdims=True) + 1e-300
+    G = orc.jacobian_gross(rho, st.T, st.Y)[:, 1:]
     assert np.all(np.isfinite(J))
-    assert np.max(np.abs(J - Jo) * xs[None] / row) <= TOL_D
+    assert np.all(np.abs(J - Jo) <= TOL_D * G + 1e-300)
 
 
 def test_large_adiabatic_jacobian_oracle_chain_rule_and_columns(large, dev):
@@ -115,9 +108,8 @@ def test_large_adiabatic_jacobian_oracle_chain_rule_and_columns(large, dev):
     rho = orc.density(st.p, st.T, st.Y)
     J = m.jacobian_adiabatic(_t(rho, dev), _t(st.T, dev), _t(st.Y, dev)).cpu().numpy().reshape(N, N, 8)
     Jo = orc.jacobian_adiabatic(rho, st.T, st.Y).reshape(N, N, 8)
-    xs = np.maximum(st.Y, 1e-3)[None]
-    row = np.max(np.abs(Jo) * xs, axis=1, keepdims=True) + 1e-300
-    assert np.max(np.abs(J - Jo) * xs / row) <= TOL_D
+    G = orc.jacobian_adiabatic_gross(rho, st.T, st.Y).reshape(N, N, 8)
+    assert np.all(np.abs(J - Jo) <= TOL_D * G + 1e-300)
     n = 193
     st = synth.config_states(4, n=n, offset_seed=52)
     rho = orc.density(st.p, st.T, st.Y)

@@ -7,7 +7,10 @@ synchronisation).  It stages the arrays through one fixed scratch array held by
 the library, so this test calls it twice in a row -- the second call finds the
 first call's contents in the scratch -- and compares both with
 pyro_net_production_rates on the same inputs, within the parity tolerance of the
-forward tests.  It also checks that a call larger than the scratch is refused.
+forward tests.  It also checks that a call larger than the scratch is refused,
+that a call leaves the device's free memory unchanged (nothing allocated), and
+that it runs the handle's own kernel for the warp-per-state variant and for the
+160-species mechanism (species arrays in the handle's global scratch).
 
 This file is collected last so that a run that stops at the first failure has
 already run every other test; it also passes on its own in a fresh process.
@@ -73,3 +76,48 @@ def test_noalloc_rejects_calls_beyond_the_scratch(setup):
         mech.net_production_rates_noalloc(rho, Y, T=np.full(n, 1000.0))
     assert ei.value.code == B.PYRO_EINVAL
     assert "scratch" in str(ei.value)
+
+
+def test_noalloc_allocates_no_device_memory(setup):
+    """After a warm-up call, a call on host arrays leaves the driver's free device
+    memory exactly as it was."""
+    B, mech, orc = setup
+    st, rho, e = _case(orc, 2048, 43)
+    Y = np.ascontiguousarray(st.Y)
+    mech.net_production_rates_noalloc(rho, Y, e=e)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    w, T = mech.net_production_rates_noalloc(rho, Y, e=e)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert np.all(np.isfinite(w))
+
+
+@pytest.mark.parametrize("idx,opts", [(1, "variant=warp"), (4, None)])
+def test_noalloc_runs_the_handles_kernel(mech_files, idx, opts):
+    """The warp-per-state handle and the 160-species handle (store=global): two calls
+    in a row against the regular entry point on the same handle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_24286_gb300 import binding as B
+    from paper_2503_24286_gb300 import build as BLD
+    BLD.build()
+    paths, _ = mech_files
+    m = B.Mechanism(paths[idx], opts)
+    orc = O.Oracle(paths[idx])
+    if idx == 4:
+        assert m.stat("omega_store_global") == 1
+    else:
+        assert m.stat("variant_warp") == 1
+    dev = torch.device("cuda:0")
+    for call, (n, seed) in enumerate([(517, 44), (301, 45)]):
+        st = synth.config_states(idx, n=n, offset_seed=seed)
+        rho = orc.density(st.p, st.T, st.Y)
+        e = orc.internal_energy(st.T, st.Y)
+        w_ref, T_ref = m.net_production_rates(torch.tensor(rho, device=dev), torch.tensor(st.Y, device=dev),
+                                              e=torch.tensor(e, device=dev))
+        w, T = m.net_production_rates_noalloc(rho, np.ascontiguousarray(st.Y), e=e)
+        T_ref = T_ref.cpu().numpy()
+        _, G = orc.net_production_rates(rho, T_ref, st.Y, with_gross=True)
+        assert np.max(np.abs(T - T_ref) / T_ref) <= 1e-10, call
+        assert np.all(np.abs(w - w_ref.cpu().numpy()) <= TOL_W * G + 1e-300), call
