@@ -162,7 +162,8 @@ int pyro_net_production_rates(const pyro_mech* mech, int64_t n, const double* rh
 
 /* Compile and load derivative kernels ahead of their first use.  kernels:
  * NULL or "all" (jvp, vjp, jacobian), or a comma list of "jvp", "vjp",
- * "jacobian", "jacobian_adiabatic", "cn", "transport".  The groups are
+ * "jacobian", "jacobian_adiabatic", "cn", "transport", "warp" (the
+ * warp-per-state forward kernel).  The groups are
  * compiled in parallel host threads with NVRTC (cached on disk); without this
  * call each group is compiled on the first call that needs it. */
 int pyro_mech_prepare(const pyro_mech* mech, const char* kernels);

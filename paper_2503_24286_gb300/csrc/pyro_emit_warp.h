@@ -1,0 +1,27 @@
+// Emitter of the warp-per-state kernels (one warp per state, lanes splitting the
+// species and the reactions) for large mechanisms.
+#pragma once
+
+#include <map>
+#include <string>
+
+#include "pyro_emit.h"
+#include "pyro_mech.h"
+
+namespace pyro {
+
+struct WarpEmit {
+  std::map<std::string, std::string> sources;   // "wfwd": pyro_omega_warp
+  std::map<std::string, double> stats;
+  int warps_per_block = 8;                      // states per block
+  int smem_bytes = 0;                           // dynamic shared memory per block
+};
+
+// Limits of the emitted tables (packed indices): species, reactions, and the
+// production-rate segments (species + 32).
+constexpr int kWarpMaxSpecies = 1022;
+constexpr int kWarpMaxReactions = 65535;
+
+WarpEmit emit_warp_units(const Mechanism& m, const EmitOptions& opt);
+
+}  // namespace pyro

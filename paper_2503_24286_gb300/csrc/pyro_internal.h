@@ -51,13 +51,4 @@ const float* mlp_device_params(const MlpState* s);
 const float* mlp_host_norm(const MlpState* s);
 bool mlp_ready(const MlpState* s);
 
-// ---- warp-per-point table-driven net production rates (pyro_warp.cu) ----
-struct Mechanism;
-struct WarpTables;
-int warp_build(const Mechanism& m, int num_sms, WarpTables** out);
-void warp_free(WarpTables* w);
-int warp_launch_omega(const WarpTables* w, int num_sms, int64_t n, const double* rho, const double* T_or_e,
-                      int energy, const double* Y, double* T_out, double* omega, unsigned long long* fail,
-                      cudaStream_t st);
-
 }  // namespace pyro

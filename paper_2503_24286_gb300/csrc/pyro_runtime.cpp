@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "pyro_emit.h"
+#include "pyro_emit_warp.h"
 #include "pyro_internal.h"
 #include "pyro_mech.h"
 
@@ -259,7 +260,6 @@ struct pyro_mech {
   double* d_store = nullptr;       // per-block species arrays when they do not fit in shared memory
   size_t store_bytes = 0;
   // learned initial guess
-  pyro::WarpTables* warp = nullptr;
   pyro::MlpState* mlp = nullptr;
   float* mlp_norm_dev = nullptr;   // device copy of (e_mean, e_std, T_mean, T_std)
   CUfunction f_mlp_guess = nullptr, f_temperature_mlp = nullptr;
@@ -494,7 +494,8 @@ int ensure_store(pyro_mech* h, size_t bytes) {
 
 const char* group_kernel(const std::string& g) {
   return g == "jvp" ? "pyro_jvp" : g == "vjp" ? "pyro_vjp" : g == "jad" ? "pyro_jacobian_adiabatic"
-       : g == "cn" ? "pyro_cn_assemble" : g == "tr" ? "pyro_transport" : "pyro_jacobian";
+       : g == "cn" ? "pyro_cn_assemble" : g == "tr" ? "pyro_transport" : g == "wfwd" ? "pyro_omega_warp"
+       : "pyro_jacobian";
 }
 
 // Compile (in parallel threads, cached on disk) and load the named derivative
@@ -537,6 +538,7 @@ int ensure_groups(pyro_mech* h, const std::vector<std::string>& names) {
     r = d.ModuleGetFunction(&G.f, G.module, group_kernel(todo[i]));
     if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, std::string("missing kernel ") + group_kernel(todo[i]));
     if (todo[i] == "tr") { G.block = pyro::kTransportBlock; G.smem = h->emitted.smem_dyn_bytes_transport; }
+    if (todo[i][0] == 'w') { G.block = 32 * h->emitted.warp_wpb; G.smem = h->emitted.smem_dyn_bytes_warp; }
     if (todo[i] == "jac" || todo[i] == "jad" || todo[i] == "cn") G.smem = h->emitted.smem_dyn_bytes_jac;
     const int smem = G.smem >= 0 ? G.smem : h->emitted.smem_dyn_bytes_deriv;
     const int blk = G.block > 0 ? G.block : h->opt.deriv_block;
@@ -547,7 +549,8 @@ int ensure_groups(pyro_mech* h, const std::vector<std::string>& names) {
     if (r != CUDA_SUCCESS || nb < 1) return fail(PYRO_ECUDA, std::string(group_kernel(todo[i])) + " does not fit on an SM");
     G.blocks_per_sm = nb;
     h->emitted.stats[todo[i] + "_blocks_per_sm"] = nb;
-    if (h->emitted.stats["deriv_store_global"] > 0 && todo[i] != "jac" && todo[i] != "jad" && todo[i] != "cn") {
+    if (h->emitted.stats["deriv_store_global"] > 0 && todo[i] != "jac" && todo[i] != "jad" && todo[i] != "cn" &&
+        todo[i][0] != 'w') {
       size_t bytes = (size_t)h->num_sms * nb * 4 * h->m.n_species() * h->opt.deriv_block * sizeof(double);
       cudaError_t e = cudaMalloc(&G.store, bytes);
       if (e != cudaSuccess) return fail(PYRO_ECUDA, std::string("species-array store allocation: ") + cudaGetErrorString(e));
@@ -600,6 +603,18 @@ int ensure_jac_scratch(pyro_mech* h, const pyro_mech::Group& G, int64_t n) {
   return PYRO_OK;
 }
 
+// warp-per-state kernels: one state per warp, a persistent grid of the resident blocks
+int launch_warp(const pyro_mech* h, const pyro_mech::Group& G, int64_t n, void* stream, void** params) {
+  const int wpb = G.block / 32;
+  int64_t need = (n + wpb - 1) / wpb;
+  int64_t cap = (int64_t)h->num_sms * G.blocks_per_sm;
+  unsigned grid = (unsigned)(need < cap ? need : cap);
+  if (grid == 0) return PYRO_OK;
+  CUresult r = driver().LaunchKernel(G.f, grid, 1, 1, G.block, 1, 1, G.smem, as_stream(stream), params, nullptr);
+  if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
+  return PYRO_OK;
+}
+
 int launch_deriv(const pyro_mech* h, const pyro_mech::Group& G, int64_t n, void* stream, void** params) {
   const int blk = G.block > 0 ? G.block : h->opt.deriv_block;
   const int smem = G.smem >= 0 ? G.smem : h->emitted.smem_dyn_bytes_deriv;
@@ -627,13 +642,11 @@ int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) 
   if (!parse_options(options, h->opt, err)) { delete h; return fail(PYRO_EINVAL, err); }
   if (!parse_mechanism_file(mech_path, h->m, err)) { delete h; return fail(PYRO_EMECH, err); }
   if (!validate_mechanism(h->m, err)) { delete h; return fail(PYRO_EMECH, err); }
-  if (h->opt.warp)
-    for (auto& r : h->m.reactions)
-      if (r.kind == RX_PLOG || r.n_sri) {
-        delete h;
-        return fail(PYRO_EINVAL, "variant=warp supports Arrhenius, third-body and Troe/Lindemann falloff "
-                                 "reactions only (this mechanism has SRI or PLOG reactions)");
-      }
+  if (h->opt.warp && (h->m.n_species() > pyro::kWarpMaxSpecies || h->m.n_reactions() > pyro::kWarpMaxReactions)) {
+    delete h;
+    return fail(PYRO_EINVAL, "variant=warp supports up to " + std::to_string(pyro::kWarpMaxSpecies) + " species and " +
+                                 std::to_string(pyro::kWarpMaxReactions) + " reactions");
+  }
   for (auto& s : h->m.species) h->W.push_back(s.W);
   EmitOptions eo;
   eo.block = h->opt.block;
@@ -703,7 +716,8 @@ int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) 
     if (int rc = ensure_store(h, bytes)) { pyro_mech_free(h); return rc; }
   }
   if (h->opt.warp) {
-    if (int rc = pyro::warp_build(h->m, h->num_sms, &h->warp)) { pyro_mech_free(h); return rc; }
+    // the emitted warp-per-state forward kernel (compiled now, cached on disk)
+    if (int rc = ensure_groups(h, {"wfwd"})) { pyro_mech_free(h); return rc; }
     h->emitted.stats["variant_warp"] = 1;
   }
   if (cudaMalloc(&h->d_fail, sizeof(unsigned long long)) != cudaSuccess ||
@@ -726,7 +740,6 @@ void pyro_mech_free(pyro_mech* h) {
   if (h->d_cn) cudaFree(h->d_cn);
   if (h->d_store) cudaFree(h->d_store);
   if (h->mlp) pyro::mlp_free(h->mlp);
-  if (h->warp) pyro::warp_free(h->warp);
   if (h->mlp_norm_dev) cudaFree(h->mlp_norm_dev);
   for (auto& g : h->groups) {
     if (g.second.module && driver().ModuleUnload) driver().ModuleUnload(g.second.module);
@@ -871,15 +884,12 @@ int pyro_net_production_rates(const pyro_mech* hc, int64_t n, const double* rho,
                        int em = input_is_energy ? 1 : 0;
                        double Tg = 1200.0, tol = 1e-10;
                        int max_iter = 50;
-                       if (h->warp)
-                         return pyro::warp_launch_omega(h->warp, h->num_sms, nc, (const double*)d[0], (const double*)d[1],
-                                                        em, (const double*)d[2], (double*)d[3], (double*)d[4],
-                                                        h->d_fail, (cudaStream_t)st);
                        void* params[] = {&nn, &d[0], &d[1], &em, &d[2], &d[3], &d[4], &Tg, &max_iter, &tol, &h->d_fail,
                                          &h->d_store};
+                       if (h->opt.warp) return launch_warp(h, h->groups["wfwd"], nc, st, params);
                        return launch(h, h->f_omega, nc, h->omega_blocks_per_sm, h->emitted.smem_dyn_bytes_omega,
                                      st, params);
-                     }, !h->warp && h->emitted.stats["omega_store_global"] <= 0);   // shared-memory variant: no scratch
+                     }, h->opt.warp || h->emitted.stats["omega_store_global"] <= 0);   // no per-block global scratch
   if (rc) return rc;
   return input_is_energy ? maybe_checked(h, stream) : PYRO_OK;
 }
@@ -901,6 +911,7 @@ int pyro_mech_prepare(const pyro_mech* hc, const char* kernels) {
       else if (item == "jacobian" || item == "jac") names.push_back("jac");
       else if (item == "jacobian_adiabatic" || item == "jad") names.push_back("jad");
       else if (item == "cn" || item == "crank_nicolson") names.push_back("cn");
+      else if (item == "warp" || item == "wfwd") names.push_back("wfwd");
       else if (item == "transport" || item == "tr") {
         if (h->emitted.stats["has_transport"] <= 0) return fail(PYRO_EMECH, "the mechanism has no transport section");
         names.push_back("tr");
@@ -1313,12 +1324,14 @@ int internal_launch_omega(const pyro_mech* h, int64_t n, const void* rho, const 
   int em = input_is_energy ? 1 : 0;
   double Tg = 1200.0, tol = 1e-10;
   int max_iter = 50;
-  // the same kernel choice as pyro_net_production_rates (thread or warp per state)
-  if (h->warp)
-    return pyro::warp_launch_omega(h->warp, h->num_sms, n, (const double*)rho, (const double*)T_or_e, em,
-                                   (const double*)Y, (double*)T_out, (double*)omega, fail_ctr, (cudaStream_t)stream);
   void* store = h->d_store;
   void* params[] = {&nn, &rho, &T_or_e, &em, &Y, &T_out, &omega, &Tg, &max_iter, &tol, &fail_ctr, &store};
+  // the same kernel choice as pyro_net_production_rates (thread or warp per state)
+  if (h->opt.warp) {
+    auto it = h->groups.find("wfwd");
+    if (it == h->groups.end() || !it->second.f) return fail(PYRO_ECUDA, "warp-per-state kernel not loaded");
+    return launch_warp(h, it->second, n, stream, params);
+  }
   return launch(h, h->f_omega, n, h->omega_blocks_per_sm, h->emitted.smem_dyn_bytes_omega, stream, params);
 }
 

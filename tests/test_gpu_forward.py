@@ -255,11 +255,13 @@ def test_full_size_workload_sampled(mechs, dev):
     assert np.all(np.abs(w[:, ii].cpu().numpy() - ow) <= TOL_W * G + 1e-300)
 
 
-@pytest.mark.parametrize("idx", [0, 1])
+@pytest.mark.parametrize("idx", [0, 1, 7])
 def test_warp_variant_parity(mechs, dev, mech_files, idx):
-    """One warp per state (table-driven) gives the oracle's results as well."""
+    """One warp per state (the emitted warp-per-state kernel, lanes splitting the
+    species and the reactions) gives the oracle's results as well, including the
+    SRI and PLOG reactions of the pressure-dependent variant."""
     from paper_2503_24286_gb300 import binding as B
-    _, orc = mechs[idx]
+    orc = mechs[idx][1] if idx in mechs else O.Oracle(mech_files[0][idx])
     m = B.Mechanism(mech_files[0][idx], "variant=warp")
     assert m.stat("variant_warp") == 1
     st, rho, e = _inputs(idx, 777, orc, seed_offset=11)

@@ -122,9 +122,10 @@ def test_pressure_dependent_forms_parse_validate_and_compile(mech_files, tmp_pat
     assert m.stat("omega_fp64_flops_per_point") > 0
     src = m.source()
     assert "(plog)" in src and "lnp" in src
-    with pytest.raises(B.PyroError) as ei:                 # the table-driven variant has no SRI/PLOG
-        B.Mechanism(mech_files[0][7], "device=0;variant=warp")
-    assert ei.value.code == B.PYRO_EINVAL
+    # the warp-per-state kernel is emitted for SRI and PLOG reactions too, and compiles
+    mw = B.Mechanism(mech_files[0][7], "device=0;variant=warp;cache=0")
+    mw.prepare("warp")
+    assert mw.stat("wfwd_cubin_bytes") > 0 and mw.stat("warp_chunks") >= 325 / 32
     mech = handmech.abcd_mechanism(kind="falloff", low=(1e16, -1.0, 1000.0))
     mech.reactions[0].sri = (0.5, 100.0, -3.0)                # c must be positive
     with pytest.raises(B.PyroError) as ei:
