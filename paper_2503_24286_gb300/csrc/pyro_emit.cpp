@@ -2288,8 +2288,9 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, cons
     WarpEmit w = emit_warp_units(m, opt);
     for (auto& kv : w.sources) out.group_sources[kv.first] = kv.second;
     for (auto& kv : w.stats) out.stats[kv.first] = kv.second;
-    out.warp_wpb = w.warps_per_block;
-    out.smem_dyn_bytes_warp = w.smem_bytes;
+    out.warp_wpb = w.wpb;
+    out.smem_dyn_bytes_warp = w.smem;
+    out.stats["deriv_warp_per_state"] = 1;
   }
   out.stats["deriv_block"] = opt.deriv_block;
 

@@ -40,8 +40,9 @@ struct EmitResult {
   int smem_dyn_bytes_transport = 0;       // dynamic shared memory of the transport kernel
   int smem_dyn_bytes_jac = 0;             // dynamic shared memory of the Jacobian-type kernels
   int cn_solve_warps = 4;                 // states (warps) per block of the Crank-Nicolson solve kernel
-  int warp_wpb = 8;                       // states (warps) per block of the warp-per-state kernels
-  int smem_dyn_bytes_warp = 0;            // dynamic shared memory of the warp-per-state kernels
+  // warp-per-state kernels ("wfwd", "wjvp", "wvjp"): states (warps) per block and
+  // dynamic shared memory per block
+  std::map<std::string, int> warp_wpb, smem_dyn_bytes_warp;
 };
 
 // Threads per block of the transport kernel (3 per-state arrays of N doubles in

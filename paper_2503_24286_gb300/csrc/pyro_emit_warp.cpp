@@ -58,7 +58,8 @@ struct WChunk {
   bool rev = true;          // any reversible reaction in the chunk
   int neff = 0;             // largest number of efficiency terms (eps != 1)
   int nodes = 0;            // PLOG: largest node count
-  int eoff = 0, foff = 0;   // offsets into the efficiency / falloff-constant tables
+  int nrb = 0;              // largest number of species with nu != 0 (adjoint gather of the VJP)
+  int eoff = 0, foff = 0, roff = 0;   // offsets into the efficiency / falloff / nu-list tables
 };
 
 struct WPlan {
@@ -66,10 +67,7 @@ struct WPlan {
   std::vector<int> order;   // slot -> reaction
   std::vector<int> slot;    // reaction -> slot
   std::vector<WChunk> chunks;
-  // production-rate gather: [steps][32] packed entries, per species its segments
-  int steps = 0, nseg = 0;
-  std::vector<unsigned> gent;
-  std::vector<int> seg_first, seg_count;
+  int nplain = 0;           // plain reactions occupy slots [0, nplain)
 };
 
 int n_eff(const Reaction& r) {
@@ -103,7 +101,9 @@ WPlan make_plan(const Mechanism& m) {
   P.order = idx;
   P.slot.assign(M, 0);
   for (int s = 0; s < M; ++s) P.slot[P.order[s]] = s;
-  int eoff = 0, foff = 0;
+  P.nplain = 0;
+  for (int j = 0; j < M; ++j) if (wkind(m.reactions[j]) == WK_PLAIN) ++P.nplain;
+  int eoff = 0, foff = 0, roff = 0;
   for (int s = 0; s < M;) {
     const int kind = wkind(m.reactions[P.order[s]]);
     int e = s;
@@ -116,6 +116,9 @@ WPlan make_plan(const Mechanism& m) {
       if (r.reversible) { c.rev = true; c.nr = std::max(c.nr, n_factors(r.products)); }
       c.neff = std::max(c.neff, n_eff(r));
       if (r.kind == RX_PLOG) c.nodes = std::max(c.nodes, (int)r.plog.size());
+      int nnu = 0;
+      for (auto& t : net_nu(r)) if (t.second) ++nnu;
+      c.nrb = std::max(c.nrb, nnu);
     }
     c.eoff = eoff;
     if (kind != WK_PLAIN && kind != WK_PLOG) eoff += 32 * c.neff;
@@ -123,41 +126,69 @@ WPlan make_plan(const Mechanism& m) {
     const int nfo = kind == WK_LIND ? 3 : kind == WK_TROE3 ? 7 : kind == WK_TROE4 ? 8 : kind == WK_SRI ? 8
                   : kind == WK_PLOG ? 4 * c.nodes + (c.nodes - 1) : 0;
     foff += 32 * nfo;
+    c.roff = roff;
+    roff += 32 * c.nrb;
     P.chunks.push_back(c);
     s = e;
   }
-  // gather: nonzero (species, slot, nu) in species order, cut into 32 equal runs
-  std::vector<std::vector<std::pair<int, int>>> rows(P.N);
-  for (int j = 0; j < M; ++j)
-    for (auto& q : net_nu(m.reactions[j]))
-      if (q.second) rows[q.first].push_back({P.slot[j], q.second});
-  for (auto& r : rows) std::sort(r.begin(), r.end());
-  std::vector<std::tuple<int, int, int>> ent;   // (species, slot, nu)
-  for (int k = 0; k < P.N; ++k)
-    for (auto& e : rows[k]) ent.push_back(std::make_tuple(k, e.first, e.second));
-  const int nnz = (int)ent.size();
-  P.steps = std::max(1, (nnz + 31) / 32);
-  P.gent.assign((size_t)P.steps * 32, 0u);
-  P.seg_first.assign(P.N, -1);
-  P.seg_count.assign(P.N, 0);
-  int seg = 0;
-  for (int l = 0; l < 32; ++l) {
-    const int a = l * P.steps, b = std::min(nnz, (l + 1) * P.steps);
-    for (int q = a; q < b; ++q) {
-      const int k = std::get<0>(ent[q]);
-      const bool last = q + 1 == b || std::get<0>(ent[q + 1]) != k;
-      unsigned e = (unsigned)std::get<1>(ent[q]) | ((unsigned)(std::get<2>(ent[q]) + 4) << 16);
-      if (last) {
-        if (P.seg_first[k] < 0) P.seg_first[k] = seg;
-        P.seg_count[k]++;
-        e |= (1u << 19) | ((unsigned)seg << 20);
-        ++seg;
-      }
-      P.gent[(size_t)(q - a) * 32 + l] = e;
-    }
-  }
-  P.nseg = seg;
   return P;
+}
+
+// Balanced gathers sum_{(k, e)} value(e) into per-species sums: every loop's
+// entries (sorted by species) are cut into 32 runs of equal length, lane l
+// walks run l and flushes a partial sum at each species boundary; the species
+// pass then adds the partial sums (segments) of each species.
+struct GItem {
+  int k;          // species
+  unsigned x, y;  // payload (y: bits 0..19)
+  double c;       // payload coefficient (efficiency loops)
+};
+struct GLoop {
+  int steps = 1;
+  std::vector<unsigned> ent;   // [steps][32][2]
+  std::vector<double> coef;    // [steps][32] (efficiency loops)
+};
+struct Gather {
+  std::vector<GLoop> loops;
+  int nseg = 0;
+  std::vector<int> seg_ptr, seg_idx;   // per species: its segments
+  double entries = 0;
+};
+
+Gather build_gather(int N, std::vector<std::vector<GItem>> items) {
+  Gather G;
+  std::vector<std::vector<int>> segs(N);
+  for (auto& its : items) {
+    std::stable_sort(its.begin(), its.end(), [](const GItem& a, const GItem& b) { return a.k < b.k; });
+    GLoop L;
+    const int nnz = (int)its.size();
+    G.entries += nnz;
+    L.steps = std::max(1, (nnz + 31) / 32);
+    L.ent.assign((size_t)L.steps * 64, 0u);
+    L.coef.assign((size_t)L.steps * 32, 0.0);
+    for (int l = 0; l < 32; ++l) {
+      const int a = l * L.steps, b = std::min(nnz, (l + 1) * L.steps);
+      for (int q = a; q < b; ++q) {
+        const GItem& it = its[q];
+        unsigned y = it.y;
+        if (q + 1 == b || its[q + 1].k != it.k) {
+          y |= (1u << 20) | ((unsigned)G.nseg << 21);
+          segs[it.k].push_back(G.nseg++);
+        }
+        const size_t e = (size_t)(q - a) * 32 + l;
+        L.ent[2 * e] = it.x;
+        L.ent[2 * e + 1] = y;
+        L.coef[e] = it.c;
+      }
+    }
+    G.loops.push_back(L);
+  }
+  G.seg_ptr.push_back(0);
+  for (int k = 0; k < N; ++k) {
+    for (int v : segs[k]) G.seg_idx.push_back(v);
+    G.seg_ptr.push_back((int)G.seg_idx.size());
+  }
+  return G;
 }
 
 template <class T>
@@ -177,50 +208,301 @@ void emit_array(std::ostringstream& o, const char* type, const std::string& name
 
 namespace {
 
-// Tables and device code shared by the warp-per-state kernels of one mechanism,
-// and the reaction-phase code: per chunk, R_j (or its tangent) into sR[slot].
-struct WarpCommon {
-  WPlan P;
-  std::string prelude, reaction_code;
+enum WMode { W_FWD = 0, W_JVP = 1, W_VJP = 2 };
+
+std::string gname(const char* base, int g) { return std::string(base) + std::to_string(g); }
+
+// The gather's tables: entries, coefficients (if any), per-species segments.
+void emit_gather_tables(std::ostringstream& o, const Gather& G, int g, bool coef) {
+  for (size_t l = 0; l < G.loops.size(); ++l) {
+    const auto& L = G.loops[l];
+    o << "__device__ const uint2 " << gname("w_ge", g) << "_" << l << "[" << L.steps * 32 << "] = {";
+    for (size_t e = 0; e < L.ent.size() / 2; ++e)
+      o << (e ? "," : "") << "{" << L.ent[2 * e] << "u," << L.ent[2 * e + 1] << "u}";
+    o << "};\n";
+    if (coef) emit_array(o, "double", gname("w_gc", g) + "_" + std::to_string(l), L.coef, true);
+  }
+  emit_array(o, "int", gname("w_sp", g), G.seg_ptr, false);
+  emit_array(o, "int", gname("w_si", g), G.seg_idx, false);
+}
+
+// One gather loop: lane l accumulates its run; `term` is the FP64 update of acc
+// for entry e (uint2) and coefficient c.
+void emit_gather_loop(std::ostringstream& k, const Gather& G, int g, size_t l, const std::string& term, bool coef,
+                      const std::string& sP) {
+  k << "    {\n      double acc = 0.0;\n#pragma unroll 4\n      for (int st = 0; st < " << G.loops[l].steps
+    << "; ++st) {\n        const uint2 e = __ldg(" << gname("w_ge", g) << "_" << l << " + st * 32 + lane);\n";
+  if (coef) k << "        const double c = __ldg(" << gname("w_gc", g) << "_" << l << " + st * 32 + lane);\n";
+  k << "        " << term << "\n"
+    << "        if (e.y & (1u << 20)) { " << sP << "[e.y >> 21] = acc; acc = 0.0; }\n      }\n    }\n";
+}
+
+// Per-species total of gather g (segments in sP): into the double variable `var`.
+std::string gather_total(int g, const std::string& sP, const std::string& var) {
+  return "      double " + var + " = 0.0;\n      for (int q = __ldg(" + gname("w_sp", g) + " + k); q < __ldg(" +
+         gname("w_sp", g) + " + k + 1); ++q) " + var + " += " + sP + "[__ldg(" + gname("w_si", g) + " + q)];\n";
+}
+
+// Shared-memory words of one warp for a kernel mode.
+struct WLayout {
+  std::vector<std::pair<std::string, int>> arrays;   // name, words
+  int words() const {
+    int w = 0;
+    for (auto& a : arrays) w += a.second;
+    return w;
+  }
 };
 
-WarpCommon emit_warp_common(const Mechanism& m, const EmitOptions& opt) {
-  WarpCommon W;
-  W.P = make_plan(m);
-  const WPlan& P = W.P;
-  const int N = P.N, M = P.M;
+// Warps per block: the most resident warps per SM that the shared memory allows
+// (228 KB per SM, 1 KB reserved per block, 227 KB per block, at most 64 warps);
+// registers are checked at load.  Ties go to the smaller block.
+int pick_warps(int words) {
+  int best = 4, best_w = 0;
+  for (int w = 4; w <= 16; ++w) {
+    const long bytes = 8L * (776 + (long)w * words);
+    if (bytes > 227L * 1024) break;
+    const int blocks = (int)std::min<long>(std::min(32, 64 / w), (228L * 1024) / (bytes + 1024));
+    if (blocks * w > best_w) { best_w = blocks * w; best = w; }
+  }
+  return best;
+}
+
+// The reaction phase of one chunk (lane l: slot base + l) in the given mode.
+//   FWD: sR[s] = R;  JVP: sR[s] = dR;  VJP: sDb[s] = Rb kk, sMb[s - NPLAIN] = Rb kM D and the
+//   lane's partial sums of T_bar, the total [M] adjoint and its rho term.
+void emit_chunk(std::ostringstream& rc, const WChunk& c, int mode) {
+  const double inv_ln10 = (double)(1.0L / logl(10.0L));
+  const std::string ln10 = lit((double)logl(10.0L));
+  rc << "    { // reactions " << c.base << ".." << c.base + c.count - 1 << " (class " << c.kind << ", " << c.nf << "x"
+     << c.nr << (c.rev ? "" : " irreversible") << ")\n";
+  rc << "      const int s = " << c.base << " + lane;\n";
+  if (c.count < 32) rc << "      if (lane < " << c.count << ") {\n";
+  rc << "      const unsigned fr = __ldg(w_fr + s);\n";
+  for (int q = 0; q < c.nf; ++q) rc << "      const int i" << q << " = (fr >> " << 10 * q << ") & 1023;\n";
+  if (c.rev) {
+    rc << "      const unsigned fq = __ldg(w_fp + s);\n";
+    for (int q = 0; q < c.nr; ++q) rc << "      const int o" << q << " = (fq >> " << 10 * q << ") & 1023;\n";
+  }
+  auto F = [&](int field) { return "__ldg(w_fo + " + std::to_string(c.foff + field * 32) + " + lane)"; };
+  const bool der = mode != W_FWD;
+  // ---- exponent of k~ (and d/dT)
+  if (c.kind == WK_PLOG) {
+    const int Q = c.nodes;
+    rc << "      int qa = 0;\n";
+    for (int q = 1; q + 1 < Q; ++q) rc << "      if (lnp >= " << F(4 * q + 3) << ") qa = " << q << ";\n";
+    rc << "      const double* nd = w_fo + " << c.foff << " + lane;\n"
+          "      const double pla = __ldg(nd + (4 * qa) * 32), pba = __ldg(nd + (4 * qa + 1) * 32), "
+          "pma = __ldg(nd + (4 * qa + 2) * 32), plp = __ldg(nd + (4 * qa + 3) * 32);\n"
+          "      const double plb = __ldg(nd + (4 * qa + 4) * 32), pbb = __ldg(nd + (4 * qa + 5) * 32), "
+          "pmb = __ldg(nd + (4 * qa + 6) * 32);\n"
+          "      const double pinv = __ldg(nd + (" << 4 * Q << " + qa) * 32);\n"
+          "      const double pxa = fma(pma, invT, fma(pba, lnT, pla));\n"
+          "      const double pxb = fma(pmb, invT, fma(pbb, lnT, plb));\n"
+          "      const double pfu = (lnp - plp) * pinv;\n"
+          "      const double pf = fmin(fmax(pfu, 0.0), 1.0);\n"
+          "      double x = fma(pf, pxb - pxa, pxa);\n";
+    if (der)
+      rc << "      const double pdx = (pfu > 0.0 && pfu < 1.0) ? (pxb - pxa) * pinv : 0.0;\n"
+            "      const double pta_ = fma(pba, invT, -pma * invT2), ptb_ = fma(pbb, invT, -pmb * invT2);\n"
+            "      double tau = fma(pdx, invT, fma(pf, ptb_ - pta_, pta_));\n";
+  } else {
+    rc << "      double x = fma(__ldg(w_b + s), lnT, __ldg(w_lnA + s));\n"
+          "      x = fma(__ldg(w_mth + s), invT, x);\n";
+    if (der) rc << "      double tau = fma(__ldg(w_b + s), invT, -__ldg(w_mth + s) * invT2);\n";
+  }
+  for (int q = 0; q < c.nf; ++q) rc << "      x -= sL[i" << q << "];\n";
+  rc << "      const double kt = PEXP(x, s_exp);\n";
+  // ---- [M] and the rate-constant factor
+  const bool tb = c.kind != WK_PLAIN && c.kind != WK_PLOG;
+  if (tb) {
+    rc << "      double mS = ysum;\n";
+    for (int q = 0; q < c.neff; ++q)
+      rc << "      mS = fma(sY[__ldg(w_ei + " << c.eoff + q * 32 << " + lane)], __ldg(w_ec + " << c.eoff + q * 32
+         << " + lane), mS);\n";
+    rc << "      const double M = rho * mS;\n";
+  } else if (c.kind == WK_PLOG && der) {
+    rc << "      const double mS = ysum;\n      const double M = rho * mS;\n";
+  }
+  if (c.kind == WK_PLAIN) {
+    rc << "      const double kk = kt;\n";
+  } else if (c.kind == WK_PLOG) {
+    rc << "      const double kk = kt;\n";
+    if (der) rc << "      const double kM = kt * pdx * pdm::rcp(M);\n";
+  } else if (c.kind == WK_TB) {
+    rc << "      const double kk = kt * M;\n";
+    if (der) rc << "      const double kM = kt;\n";
+  } else {
+    rc << "      const double lnPr = fma(" << F(1) << ", lnT, " << F(0) << ") + fma(" << F(2)
+       << ", invT, pdm::log(M, s_log));\n"
+          "      const double fpr = pdm::rcp(1.0 + PEXP(-lnPr, s_exp));\n";
+    if (der) rc << "      const double pT = fma(" << F(1) << ", invT, -" << F(2) << " * invT2);\n";
+    if (c.kind == WK_TROE3 || c.kind == WK_TROE4) {
+      rc << "      const double t1 = " << F(3) << " * PEXP(T * " << F(4) << ", s_exp);\n"
+            "      const double t2 = " << F(5) << " * PEXP(T * " << F(6) << ", s_exp);\n";
+      if (c.kind == WK_TROE4) rc << "      const double t3 = PEXP(" << F(7) << " * invT, s_exp);\n";
+      else rc << "      const double t3 = 0.0;\n";
+      rc << "      const double fc = t1 + t2 + t3;\n"
+            "      const double lfc = pdm::log(fc, s_log) * " << lit(inv_ln10) << ";\n"
+            "      const double cc = fma(-0.67, lfc, -0.4), nn = fma(-1.27, lfc, 0.75);\n"
+            "      const double xx = fma(lnPr, " << lit(inv_ln10) << ", cc), den = fma(-0.14, xx, nn);\n"
+            "      const double den2 = den * den;\n";
+      if (!der) {
+        rc << "      const double lf = lfc * den2 * pdm::rcp(fma(xx, xx, den2));\n"
+              "      const double kk = kt * (fpr * PEXP(lf * " << ln10 << ", s_exp));\n";
+      } else {
+        rc << "      const double rD = pdm::rcp(fma(xx, xx, den2));\n"
+              "      const double f = den2 * rD;\n"
+              "      const double Fb = PEXP(lfc * f * " << ln10 << ", s_exp);\n"
+              "      const double rD2 = rD * rD;\n"
+              "      const double Axx = lfc * (-2.0 * den2 * xx * rD2), Aden = lfc * (2.0 * den * xx * xx * rD2);\n"
+              "      const double sPr = (1.0 - fpr) + fma(-0.14, Aden, Axx);\n"
+              "      const double sfc = fma(-0.67, Axx, fma(-1.1762, Aden, f));\n";
+        if (c.kind == WK_TROE4)
+          rc << "      const double dfc = fma(t1, " << F(4) << ", fma(t2, " << F(6) << ", -(t3 * " << F(7) << ") * invT2));\n";
+        else
+          rc << "      const double dfc = fma(t1, " << F(4) << ", t2 * " << F(6) << ");\n";
+        rc << "      tau += fma(sPr, pT, sfc * dfc * pdm::rcp(fc));\n"
+              "      const double kk = kt * fpr * Fb;\n";
+      }
+    } else if (c.kind == WK_SRI) {
+      rc << "      const double su = lnPr * " << lit(inv_ln10) << ";\n"
+            "      const double sX = pdm::rcp(fma(su, su, 1.0));\n"
+            "      const double sea = " << F(3) << " * PEXP(" << F(4) << " * invT, s_exp);\n"
+            "      const double seb = PEXP(T * " << F(5) << ", s_exp);\n"
+            "      const double sS = sea + seb;\n"
+            "      const double slS = pdm::log(sS, s_log);\n"
+            "      const double Fb = PEXP(fma(sX, slS, fma(" << F(7) << ", lnT, " << F(6) << ")), s_exp);\n";
+      if (der)
+        rc << "      const double dlnF_dlnPr = slS * (-2.0 * su * sX * sX * " << lit(inv_ln10) << ");\n"
+              "      const double dlnF_dT = fma(sX * fma(sea, -" << F(4) << " * invT2, seb * " << F(5)
+           << "), pdm::rcp(sS), " << F(7) << " * invT);\n"
+              "      const double sPr = (1.0 - fpr) + dlnF_dlnPr;\n"
+              "      tau += fma(sPr, pT, dlnF_dT);\n";
+      rc << "      const double kk = kt * fpr * Fb;\n";
+    } else {   // Lindemann
+      if (der) rc << "      const double sPr = 1.0 - fpr;\n      tau += sPr * pT;\n";
+      rc << "      const double kk = kt * fpr;\n";
+    }
+    if (der) rc << "      const double kM = kk * sPr * pdm::rcp(M);\n";
+  }
+  // ---- activity products
+  rc << "      const double Pf = sA[i0]";
+  for (int q = 1; q < c.nf; ++q) rc << " * sA[i" << q << "]";
+  rc << ";\n";
+  if (c.rev) {
+    rc << "      const double Pr = sA[o0]";
+    for (int q = 1; q < c.nr; ++q) rc << " * sA[o" << q << "]";
+    rc << ";\n      const double D = Pf - Pr;\n";
+  } else {
+    rc << "      const double D = Pf;\n";
+  }
+  auto dprod = [&](const char* v, int nfac, const char* da) {
+    std::string e;
+    for (int q = 0; q < nfac; ++q) {
+      std::string t = std::string(da) + "[" + v + std::to_string(q) + "]";
+      for (int r = 0; r < nfac; ++r) if (r != q) t += " * sA[" + std::string(v) + std::to_string(r) + "]";
+      e += (q ? " + " : "") + t;
+    }
+    return e;
+  };
+  if (mode == W_FWD) {
+    rc << "      sR[s] = kk * D;\n";
+  } else if (mode == W_JVP) {
+    rc << "      double dx = tau * dT;\n";
+    for (int q = 0; q < c.nf; ++q) rc << "      dx -= sdL[i" << q << "];\n";
+    if (c.kind == WK_PLAIN) {
+      rc << "      const double dkk = kk * dx;\n";
+    } else {
+      rc << "      double dmS = dysum;\n";
+      if (tb)
+        for (int q = 0; q < c.neff; ++q)
+          rc << "      dmS = fma(sdY[__ldg(w_ei + " << c.eoff + q * 32 << " + lane)], __ldg(w_ec + " << c.eoff + q * 32
+             << " + lane), dmS);\n";
+      rc << "      const double dM = fma(drho, mS, rho * dmS);\n"
+            "      const double dkk = fma(kk, dx, kM * dM);\n";
+    }
+    rc << "      const double dPf = " << dprod("i", c.nf, "sdA") << ";\n";
+    if (c.rev) rc << "      const double dPr = " << dprod("o", c.nr, "sdA") << ";\n";
+    rc << "      sR[s] = fma(dkk, D, kk * " << (c.rev ? "(dPf - dPr)" : "dPf") << ");\n";
+  } else {
+    rc << "      double Rb = 0.0;\n";
+    for (int q = 0; q < c.nrb; ++q)
+      rc << "      { const unsigned short b = __ldg(w_rb + " << c.roff + q * 32
+         << " + lane); Rb = fma(s_nu[b >> 10], sWb[b & 1023], Rb); }\n";
+    rc << "      const double xb = Rb * (kk * D);\n      Tbp = fma(xb, tau, Tbp);\n";
+    for (int q = 0; q < c.nf; ++q) rc << "      Tbp = fma(-xb, sLp[i" << q << "], Tbp);\n";
+    rc << "      sDb[s] = Rb * kk;\n";
+    if (c.kind != WK_PLAIN)
+      rc << "      const double Mb = Rb * kM * D;\n      sMb[s - NPLAIN] = Mb;\n      Mtp += Mb;\n"
+            "      rMp = fma(Mb, mS, rMp);\n";
+  }
+  if (c.count < 32) rc << "      }\n";
+  rc << "    }\n";
+}
+
+}  // namespace
+
+WarpEmit emit_warp_units(const Mechanism& m, const EmitOptions& opt) {
+  WarpEmit out;
+  const WPlan P = make_plan(m);
+  const int N = P.N, M = P.M, N1 = N + 1;
   std::vector<SpeciesCoef> C;
   for (auto& sp : m.species) C.push_back(species_coef(sp));
+  // ---- gathers: production rates (forward, JVP) and the VJP's adjoints
+  std::vector<GItem> fw;
+  std::vector<GItem> adj1, adj2, effl;
+  for (int j = 0; j < M; ++j) {
+    const Reaction& r = m.reactions[j];
+    const unsigned sl = (unsigned)P.slot[j];
+    for (auto& q : net_nu(r))
+      if (q.second) fw.push_back({q.first, sl | ((unsigned)(q.second + 4) << 16), 0u, 0.0});
+    // d(prod a^nu)/d a_i: one entry per factor occurrence, with the other factors
+    for (int side = 0; side < (r.reversible ? 2 : 1); ++side) {
+      std::vector<int> f = side_factors(side == 0 ? r.reactants : r.products);
+      for (size_t q = 0; q < f.size(); ++q) {
+        std::vector<int> oth;
+        for (size_t t = 0; t < f.size(); ++t) if (t != q) oth.push_back(f[t]);
+        const unsigned x = sl | ((unsigned)side << 16);
+        if (oth.size() <= 1) adj1.push_back({f[q], x, (unsigned)(oth.empty() ? N : oth[0]), 0.0});
+        else adj2.push_back({f[q], x, (unsigned)oth[0] | ((unsigned)oth[1] << 10), 0.0});
+      }
+    }
+    if (wkind(r) != WK_PLAIN && wkind(r) != WK_PLOG)
+      for (auto& e : r.efficiencies)
+        if (e.second != 1.0) effl.push_back({e.first, sl - (unsigned)P.nplain, 0u, (e.second - 1.0) / m.species[e.first].W});
+  }
+  const Gather gF = build_gather(N, {fw});
+  const Gather gA = build_gather(N, {adj1, adj2});
+  const Gather gC = build_gather(N, {effl});
+  // ---- shared tables
   std::ostringstream o;
   o << "// Generated for mechanism '" << m.name << "': " << N << " species, " << M
     << " reactions; warp-per-state kernels.\n";
   o << "#include \"pyro_device_math.cuh\"\ntypedef long long i64;\n";
   o << "#define PEXP(x, t) pdm::" << (opt.exp_ops == 4 ? "exp4" : "exp") << "((x), (t))\n";
-  o << "#define NSP " << N << "\n#define NRX " << M << "\n#define TMID " << lit(m.species[0].t_mid) << "\n";
-  o << "#define GSTEPS " << P.steps << "\n#define NSEG " << P.nseg << "\n";
-  // species tables: L_k coefficients [2][7][N+1] (unit slot zero), 1/W, Newton collapse [2][6][N]
-  std::vector<double> Lc(2 * 7 * (N + 1), 0.0), dc(2 * 6 * N), invW(N + 1, 0.0);
+  o << "#define NSP " << N << "\n#define NRX " << M << "\n#define NPLAIN " << P.nplain << "\n#define TMID "
+    << lit(m.species[0].t_mid) << "\n";
+  std::vector<double> Lc(2 * 7 * N1, 0.0), Hc(2 * 6 * N1, 0.0), dc(2 * 6 * N), invW(N1, 0.0);
   std::vector<float> dcf(2 * 6 * N);
   for (int k = 0; k < N; ++k) {
     invW[k] = 1.0 / m.species[k].W;
     for (int r = 0; r < 2; ++r) {
       const double L[7] = {C[k].cl[r], C[k].ci[r], C[k].c0[r], C[k].c1[r], C[k].c2[r], C[k].c3[r], C[k].c4[r]};
-      for (int q = 0; q < 7; ++q) Lc[(r * 7 + q) * (N + 1) + k] = L[q];
+      for (int q = 0; q < 7; ++q) Lc[(r * 7 + q) * N1 + k] = L[q];
       for (int q = 0; q < 6; ++q) {
+        Hc[(r * 6 + q) * N1 + k] = C[k].h[r][q];
         dc[(r * 6 + q) * N + k] = C[k].d[r][q];
         dcf[(r * 6 + q) * N + k] = (float)C[k].d[r][q];
       }
     }
   }
   emit_array(o, "double", "w_Lc", Lc, true);
+  emit_array(o, "double", "w_Hc", Hc, true);
   emit_array(o, "double", "w_dc", dc, true);
-  {
-    o << "__device__ const float w_dcf[" << dcf.size() << "] = {";
-    for (size_t i = 0; i < dcf.size(); ++i) o << (i ? "," : "") << litf(dcf[i]);
-    o << "};\n";
-  }
+  o << "__device__ const float w_dcf[" << dcf.size() << "] = {";
+  for (size_t i = 0; i < dcf.size(); ++i) o << (i ? "," : "") << litf(dcf[i]);
+  o << "};\n";
   emit_array(o, "double", "w_invW", invW, true);
-  // reaction tables in slot order: ln A' (minus the reactants' ln W), b, -theta, packed factor indices
   std::vector<double> ta(M), tb(M), tt(M);
   std::vector<unsigned> tfr(M), tfp(M);
   for (int s = 0; s < M; ++s) {
@@ -241,8 +523,7 @@ WarpCommon emit_warp_common(const Mechanism& m, const EmitOptions& opt) {
   emit_array(o, "double", "w_mth", tt, true);
   emit_array(o, "unsigned", "w_fr", tfr, false);
   emit_array(o, "unsigned", "w_fp", tfp, false);
-  // per-chunk efficiency terms [chunk][q][lane] and falloff / PLOG constants [chunk][field][lane]
-  std::vector<unsigned short> ei;
+  std::vector<unsigned short> ei, rb;
   std::vector<double> ec, fo;
   for (auto& c : P.chunks) {
     if (c.kind != WK_PLAIN && c.kind != WK_PLOG) {
@@ -261,13 +542,23 @@ WarpCommon emit_warp_common(const Mechanism& m, const EmitOptions& opt) {
       ei.insert(ei.end(), bi.begin(), bi.end());
       ec.insert(ec.end(), bc.begin(), bc.end());
     }
+    {
+      // net nu list of each reaction: species (10 bits) | (nu + 4) << 10; padding: the unit slot, nu 0
+      std::vector<unsigned short> br((size_t)32 * c.nrb, (unsigned short)(N | (4 << 10)));
+      for (int l = 0; l < c.count; ++l) {
+        int q = 0;
+        for (auto& t : net_nu(m.reactions[P.order[c.base + l]]))
+          if (t.second) br[(size_t)(q++) * 32 + l] = (unsigned short)(t.first | ((t.second + 4) << 10));
+      }
+      rb.insert(rb.end(), br.begin(), br.end());
+    }
     int nfo = 0;
     std::vector<double> f;
     if (c.kind == WK_LIND || c.kind == WK_TROE3 || c.kind == WK_TROE4 || c.kind == WK_SRI) {
       nfo = c.kind == WK_LIND ? 3 : c.kind == WK_TROE3 ? 7 : 8;
       f.assign((size_t)32 * nfo, 0.0);
-      for (int l = 0; l < c.count; ++l) {
-        const Reaction& r = m.reactions[P.order[c.base + l]];
+      for (int l = 0; l < 32; ++l) {
+        const Reaction& r = m.reactions[P.order[c.base + std::min(l, c.count - 1)]];
         double v[8] = {(double)(logl((long double)r.A0) - logl((long double)r.A)), r.b0 - r.b, -(r.theta0 - r.theta),
                        0, 0, 0, 0, 0};
         if (c.kind == WK_TROE3 || c.kind == WK_TROE4) {
@@ -280,11 +571,8 @@ WarpCommon emit_warp_common(const Mechanism& m, const EmitOptions& opt) {
         }
         for (int q = 0; q < nfo; ++q) f[(size_t)q * 32 + l] = v[q];
       }
-      // unused lanes of a partial chunk: finite constants (their results are not stored)
-      for (int l = c.count; l < 32; ++l)
-        for (int q = 0; q < nfo; ++q) f[(size_t)q * 32 + l] = f[(size_t)q * 32];
     } else if (c.kind == WK_PLOG) {
-      // per node q: lnA'_q, b_q, -theta_q, ln p_q (nodes beyond a reaction's own: ln p = +huge);
+      // per node q: lnA'_q, b_q, -theta_q, ln p_q (nodes past a reaction's own: ln p = 1e300);
       // then per segment q: 1/(ln p_{q+1} - ln p_q)
       const int Q = c.nodes;
       nfo = 4 * Q + (Q - 1);
@@ -308,17 +596,16 @@ WarpCommon emit_warp_common(const Mechanism& m, const EmitOptions& opt) {
     }
     fo.insert(fo.end(), f.begin(), f.end());
   }
-  {
-    o << "__device__ const unsigned short w_ei[" << std::max<size_t>(ei.size(), 1) << "] = {";
-    if (ei.empty()) o << "0";
-    for (size_t i = 0; i < ei.size(); ++i) o << (i ? "," : "") << ei[i];
-    o << "};\n";
-  }
+  o << "__device__ const unsigned short w_ei[" << std::max<size_t>(ei.size(), 1) << "] = {";
+  if (ei.empty()) o << "0";
+  for (size_t i = 0; i < ei.size(); ++i) o << (i ? "," : "") << ei[i];
+  o << "};\n";
+  o << "__device__ const unsigned short w_rb[" << std::max<size_t>(rb.size(), 1) << "] = {";
+  if (rb.empty()) o << "0";
+  for (size_t i = 0; i < rb.size(); ++i) o << (i ? "," : "") << rb[i];
+  o << "};\n";
   emit_array(o, "double", "w_ec", ec, true);
   emit_array(o, "double", "w_fo", fo, true);
-  emit_array(o, "unsigned", "w_gent", P.gent, false);
-  emit_array(o, "int", "w_segf", P.seg_first, false);
-  emit_array(o, "int", "w_segc", P.seg_count, false);
   o << "__constant__ double pyro_tab_exp[512] = {";
   for (int j = 0; j < 512; ++j) o << (j ? "," : "") << lit((double)exp2l((j + 0.5L) / 512.0L));
   o << "};\n__constant__ double pyro_tab_log[256] = {";
@@ -338,7 +625,17 @@ __device__ __forceinline__ float warp_sumf(float v) {
   for (int q = 16; q > 0; q >>= 1) v += __shfl_xor_sync(0xffffffffu, v, q);
   return v;
 }
-
+// the block's exp/log tables and the stoichiometric coefficients -4..3 (index nu + 4;
+// index 0 is the gather's padding and holds 0)
+__device__ __forceinline__ void wload_tables(double* s_exp, double* s_log, double* s_nu) {
+  for (int i = threadIdx.x; i < 512; i += blockDim.x) s_exp[i] = pyro_tab_exp[i];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) s_log[i] = pyro_tab_log[i];
+  if (threadIdx.x < 8) s_nu[threadIdx.x] = threadIdx.x == 0 ? 0.0 : (double)((int)threadIdx.x - 4);
+}
+)";
+  // Newton temperature solve (forward kernel only)
+  std::ostringstream nw;
+  nw << R"(
 // Newton inversion of e(T) = sum_k Y_k e_k(T) for the warp's state (Sec. A.3.1,
 // Eq. delta_temp): the mixture polynomial's coefficients are warp sums over the
 // lanes' species; every lane then iterates identically -- FP32 to |dT| <= 1e-5 T,
@@ -415,237 +712,195 @@ __device__ double wtsolve(const double* sY, double e, double T0, int max_iter, f
   return T;
 }
 )";
-  W.prelude = o.str();
-  // chunk code: one block per chunk of 32 reactions, lane l on slot base + l
-  std::ostringstream rc;
-  Src cnt;   // tally only (the algorithmic counts are the thread-per-state kernel's)
-  for (auto& c : P.chunks) {
-    rc << "    { // reactions " << c.base << ".." << c.base + c.count - 1 << " (class " << c.kind << ", " << c.nf
-       << "x" << c.nr << (c.rev ? "" : " irreversible") << ")\n";
-    rc << "      const int s = " << c.base << " + lane;\n";
-    if (c.count < 32) rc << "      if (lane < " << c.count << ") {\n";
-    rc << "      const unsigned fr = __ldg(w_fr + s);\n";
-    for (int q = 0; q < c.nf; ++q) rc << "      const int i" << q << " = (fr >> " << 10 * q << ") & 1023;\n";
-    if (c.rev) {
-      rc << "      const unsigned fq = __ldg(w_fp + s);\n";
-      for (int q = 0; q < c.nr; ++q) rc << "      const int o" << q << " = (fq >> " << 10 * q << ") & 1023;\n";
-    }
-    // ---- exponent (the shared ln k~ form)
-    if (c.kind == WK_PLOG) {
-      const int Q = c.nodes;
-      auto F = [&](int field) { return "__ldg(w_fo + " + std::to_string(c.foff) + " + " + std::to_string(field * 32) + " + lane)"; };
-      rc << "      int qa = 0;\n";
-      for (int q = 1; q + 1 < Q; ++q) rc << "      if (lnp >= " << F(4 * q + 3) << ") qa = " << q << ";\n";
-      rc << "      const double* nd = w_fo + " << c.foff << " + lane;\n"
-            "      const double pla = __ldg(nd + (4 * qa) * 32), pba = __ldg(nd + (4 * qa + 1) * 32), "
-            "pta = __ldg(nd + (4 * qa + 2) * 32), plp = __ldg(nd + (4 * qa + 3) * 32);\n"
-            "      const double plb = __ldg(nd + (4 * qa + 4) * 32), pbb = __ldg(nd + (4 * qa + 5) * 32), "
-            "ptb = __ldg(nd + (4 * qa + 6) * 32);\n"
-            "      const double pinv = __ldg(nd + (" << 4 * Q << " + qa) * 32);\n"
-            "      const double pxa = fma(pta, invT, fma(pba, lnT, pla));\n"
-            "      const double pxb = fma(ptb, invT, fma(pbb, lnT, plb));\n"
-            "      const double pf = fmin(fmax((lnp - plp) * pinv, 0.0), 1.0);\n"
-            "      double x = fma(pf, pxb - pxa, pxa);\n";
-      cnt.fma(5); cnt.add(4 + std::max(0, Q - 2)); cnt.mul();   // as the thread kernel's PLOG count
-    } else {
-      rc << "      double x = fma(__ldg(w_b + s), lnT, __ldg(w_lnA + s));\n"
-            "      x = fma(__ldg(w_mth + s), invT, x);\n";
-      cnt.fma(2);
-    }
-    for (int q = 0; q < c.nf; ++q) rc << "      x -= sL[i" << q << "];\n";
-    cnt.add(c.nf);
-    rc << "      double kt = PEXP(x, s_exp);\n";
-    cnt.exp_();
-    if (c.kind != WK_PLAIN && c.kind != WK_PLOG) {
-      rc << "      double mS = ysum;\n";
-      for (int q = 0; q < c.neff; ++q)
-        rc << "      mS = fma(sY[__ldg(w_ei + " << c.eoff + q * 32 << " + lane)], __ldg(w_ec + " << c.eoff + q * 32
-           << " + lane), mS);\n";
-      rc << "      const double M = rho * mS;\n";
-      cnt.fma(c.neff); cnt.mul();
-    }
-    auto F = [&](int field) { return "__ldg(w_fo + " + std::to_string(c.foff + field * 32) + " + lane)"; };
-    if (c.kind == WK_TB) {
-      rc << "      kt *= M;\n";
-      cnt.mul();
-    } else if (c.kind == WK_LIND || c.kind == WK_TROE3 || c.kind == WK_TROE4 || c.kind == WK_SRI) {
-      rc << "      const double lnPr = fma(" << F(1) << ", lnT, " << F(0) << ") + fma(" << F(2)
-         << ", invT, pdm::log(M, s_log));\n"
-            "      const double fpr = pdm::rcp(1.0 + PEXP(-lnPr, s_exp));\n";
-      cnt.fma(2); cnt.add(2); cnt.log_(); cnt.exp_(); cnt.rcp_();
-      if (c.kind == WK_TROE3 || c.kind == WK_TROE4) {
-        rc << "      double fc = fma(" << F(3) << ", PEXP(T * " << F(4) << ", s_exp), " << F(5) << " * PEXP(T * "
-           << F(6) << ", s_exp));\n";
-        cnt.fma(); cnt.mul(3); cnt.exp_(); cnt.exp_();
-        if (c.kind == WK_TROE4) { rc << "      fc += PEXP(" << F(7) << " * invT, s_exp);\n"; cnt.mul(); cnt.exp_(); cnt.add(); }
-        const double inv_ln10 = (double)(1.0L / logl(10.0L));
-        rc << "      const double lfc = pdm::log(fc, s_log) * " << lit(inv_ln10) << ";\n"
-              "      const double cc = fma(-0.67, lfc, -0.4), nn = fma(-1.27, lfc, 0.75);\n"
-              "      const double xx = fma(lnPr, " << lit(inv_ln10) << ", cc), den = fma(-0.14, xx, nn);\n"
-              "      const double den2 = den * den;\n"
-              "      const double lf = lfc * den2 * pdm::rcp(fma(xx, xx, den2));\n"
-              "      kt *= fpr * PEXP(lf * " << lit((double)logl(10.0L)) << ", s_exp);\n";
-        cnt.log_(); cnt.mul(); cnt.fma(4); cnt.mul(3); cnt.fma(); cnt.rcp_(); cnt.mul(); cnt.exp_(); cnt.mul(2);
-      } else if (c.kind == WK_SRI) {
-        const double inv_ln10 = (double)(1.0L / logl(10.0L));
-        rc << "      const double su = lnPr * " << lit(inv_ln10) << ";\n"
-              "      const double sX = pdm::rcp(fma(su, su, 1.0));\n"
-              "      const double sS = fma(" << F(3) << ", PEXP(" << F(4) << " * invT, s_exp), PEXP(T * " << F(5)
-           << ", s_exp));\n"
-              "      kt *= fpr * PEXP(fma(sX, pdm::log(sS, s_log), fma(" << F(7) << ", lnT, " << F(6)
-           << ")), s_exp);\n";
-        cnt.mul(); cnt.fma(); cnt.rcp_(); cnt.mul(2); cnt.fma(); cnt.exp_(); cnt.exp_(); cnt.log_(); cnt.fma(2);
-        cnt.exp_(); cnt.mul(2);
-      } else {
-        rc << "      kt *= fpr;\n";
-        cnt.mul();
-      }
-    }
-    rc << "      double Pf = sA[i0]";
-    for (int q = 1; q < c.nf; ++q) rc << " * sA[i" << q << "]";
-    rc << ";\n";
-    cnt.mul(c.nf - 1);
-    if (c.rev) {
-      rc << "      double Pr = sA[o0]";
-      for (int q = 1; q < c.nr; ++q) rc << " * sA[o" << q << "]";
-      rc << ";\n      sR[s] = kt * (Pf - Pr);\n";
-      cnt.mul(c.nr - 1); cnt.add(); cnt.mul();
-    } else {
-      rc << "      sR[s] = kt * Pf;\n";
-      cnt.mul();
-    }
-    if (c.count < 32) rc << "      }\n";
-    rc << "    }\n";
-    // algorithmic count: the chunk's ops for each of its reactions (not the idle lanes)
-  }
-  W.reaction_code = rc.str();
-  return W;
-}
-
-// Shared-memory words per warp: Y (N+1), L then the partial sums (max(N+1, NSEG)),
-// a (N+1), one value per reaction.
-int warp_words(const WPlan& P) { return (P.N + 1) + std::max(P.N + 1, P.nseg) + (P.N + 1) + P.M; }
-
-// Warps per block: the most resident warps per SM that 227 KB of shared memory
-// allows (registers are checked at load); ties go to the smaller block.
-int pick_warps(int words) {
-  int best = 4, best_w = 0;
-  for (int w = 4; w <= 16; ++w) {
-    const long bytes = 8L * (776 + (long)w * words);
-    if (bytes > 227L * 1024) break;
-    // 228 KB of shared memory per SM, 1 KB of it reserved per resident block
-    const int blocks = (int)std::min<long>(std::min(32, 64 / w), (228L * 1024) / (bytes + 1024));
-    if (blocks * w > best_w) { best_w = blocks * w; best = w; }
-  }
-  return best;
-}
-
-}  // namespace
-
-WarpEmit emit_warp_units(const Mechanism& m, const EmitOptions& opt) {
-  WarpEmit out;
-  WarpCommon W = emit_warp_common(m, opt);
-  const WPlan& P = W.P;
-  const int N = P.N;
-  const int words = warp_words(P);
-  const int wpb = pick_warps(words);
-  out.warps_per_block = wpb;
-  out.smem_bytes = 8 * (776 + wpb * words);
-  out.stats["warp_chunks"] = (double)P.chunks.size();
-  out.stats["warp_gather_steps"] = P.steps;
-  out.stats["warp_segments"] = P.nseg;
-  out.stats["warp_warps_per_block"] = wpb;
-  out.stats["warp_smem_bytes"] = out.smem_bytes;
-  std::ostringstream k;
-  k << W.prelude;
-  k << "#define WPB " << wpb << "\n#define WWORDS " << words << "\n#define LSTRIDE " << std::max(N + 1, P.nseg) << "\n";
   const bool plog = has_plog(m);
-  k << R"(
-// Net production rates, one warp per state (see the emitter for the work split).
-// Same arguments as pyro_omega; g_store is unused.
-extern "C" __global__ void __launch_bounds__(WPB * 32) pyro_omega_warp(i64 n, const double* __restrict__ g_rho,
-    const double* __restrict__ g_Tin, int energy_mode, const double* __restrict__ g_Y,
-    double* __restrict__ g_Tout, double* __restrict__ g_omega, double T_guess, int max_iter, double tol,
-    unsigned long long* __restrict__ g_fail, double* __restrict__ g_store) {
-  extern __shared__ double smem[];
-  double* s_exp = smem;
-  double* s_log = s_exp + 512;
-  double* s_nu = s_log + 256;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* sY = s_nu + 8 + warp * WWORDS;
-  double* sL = sY + (NSP + 1);
-  double* sP = sL;                      // partial sums of the production rates (after the reactions)
-  double* sA = sL + LSTRIDE;
-  double* sR = sA + (NSP + 1);
-  for (int i = threadIdx.x; i < 512; i += blockDim.x) s_exp[i] = pyro_tab_exp[i];
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) s_log[i] = pyro_tab_log[i];
-  if (threadIdx.x < 8) s_nu[threadIdx.x] = threadIdx.x == 0 ? 0.0 : (double)((int)threadIdx.x - 4);
-  __syncthreads();
-  (void)g_store;
-  const float tolf = (float)tol;
-  for (i64 base = (i64)blockIdx.x * WPB; base < n; base += (i64)gridDim.x * WPB) {
-    const i64 p = base + warp;
-    if (p >= n) break;                  // warp-uniform; no block barrier below
-    const double rho = g_rho[p];
-    double ys = 0.0;
-    for (int k = lane; k < NSP; k += 32) {
-      const double y = g_Y[(i64)k * n + p];
-      sY[k] = y;
-      ys = fma(y, __ldg(w_invW + k), ys);
+  const std::string lnR = lit((double)logl(R_GAS));
+  // species thermo of lane k: q = L_k; with H: hr = h_k/RT and Lp = L'_k = (1 - h_k/RT)/T
+  auto species_L = [&](bool H) {
+    std::string t =
+        "      const double* Lc = w_Lc + hi * 7 * (NSP + 1);\n"
+        "      double q = fma(T, __ldg(Lc + 6 * (NSP + 1) + k), __ldg(Lc + 5 * (NSP + 1) + k));\n"
+        "      q = fma(T, q, __ldg(Lc + 4 * (NSP + 1) + k));\n"
+        "      q = fma(T, q, __ldg(Lc + 3 * (NSP + 1) + k));\n"
+        "      q = fma(T, q, __ldg(Lc + 2 * (NSP + 1) + k));\n"
+        "      q = fma(__ldg(Lc + k), lnT, q);\n"
+        "      q = fma(__ldg(Lc + (NSP + 1) + k), invT, q);\n";
+    if (H)
+      t += "      const double* Hc = w_Hc + hi * 6 * (NSP + 1);\n"
+           "      double hr = fma(T, __ldg(Hc + 4 * (NSP + 1) + k), __ldg(Hc + 3 * (NSP + 1) + k));\n"
+           "      hr = fma(T, hr, __ldg(Hc + 2 * (NSP + 1) + k));\n"
+           "      hr = fma(T, hr, __ldg(Hc + (NSP + 1) + k));\n"
+           "      hr = fma(T, hr, __ldg(Hc + k));\n"
+           "      hr = fma(__ldg(Hc + 5 * (NSP + 1) + k), invT, hr);\n"
+           "      const double Lp = fma(-hr, invT, invT);\n";
+    return t;
+  };
+  auto kernel_head = [&](std::ostringstream& k, const WLayout& L, const char* sig) {
+    int words = L.words();
+    const int wpb = pick_warps(words);
+    k << "\n#undef WPB\n#define WPB " << wpb << "\n" << sig << " {\n"
+      << "  extern __shared__ double smem[];\n  double* s_exp = smem;\n  double* s_log = s_exp + 512;\n"
+      << "  double* s_nu = s_log + 256;\n  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;\n"
+      << "  double* wbase = s_nu + 8 + warp * " << words << ";\n";
+    int off = 0;
+    for (auto& a : L.arrays) {
+      k << "  double* " << a.first << " = wbase + " << off << ";\n";
+      off += a.second;
     }
-    if (lane == 0) sY[NSP] = 0.0;
-    const double ysum = warp_sum(ys);
-    __syncwarp();
-    double T;
-    if (energy_mode) {
-      int it;
-      T = wtsolve(sY, g_Tin[p], T_guess, max_iter, tolf, &it, lane);
-      if (lane == 0) {
-        if (it < 0) atomicAdd(g_fail, 1ull);
-        if (g_Tout) g_Tout[p] = T;
-      }
-    } else {
-      T = g_Tin[p];
-    }
-    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T);
-    const int hi = pdm::to_float_trunc(T) >= (float)TMID;
-    const double* Lc = w_Lc + hi * 7 * (NSP + 1);
-    for (int k = lane; k < NSP; k += 32) {
-      double q = fma(T, __ldg(Lc + 6 * (NSP + 1) + k), __ldg(Lc + 5 * (NSP + 1) + k));
-      q = fma(T, q, __ldg(Lc + 4 * (NSP + 1) + k));
-      q = fma(T, q, __ldg(Lc + 3 * (NSP + 1) + k));
-      q = fma(T, q, __ldg(Lc + 2 * (NSP + 1) + k));
-      q = fma(__ldg(Lc + k), lnT, q);
-      q = fma(__ldg(Lc + (NSP + 1) + k), invT, q);
-      sL[k] = q;
-      sA[k] = PEXP(q, s_exp) * (rho * sY[k]);
-    }
-    if (lane == 0) { sL[NSP] = 0.0; sA[NSP] = 1.0; }
-)";
-  if (plog)
-    k << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lit((double)logl(R_GAS)) << ";\n";
-  k << "    __syncwarp();\n";
-  k << W.reaction_code;
-  k << R"(    __syncwarp();
-    double acc = 0.0;
-#pragma unroll 4
-    for (int st = 0; st < GSTEPS; ++st) {
-      const unsigned e = __ldg(w_gent + st * 32 + lane);
-      acc = fma(s_nu[(e >> 16) & 7u], sR[e & 0xffffu], acc);
-      if (e & (1u << 19)) { sP[e >> 20] = acc; acc = 0.0; }
-    }
-    __syncwarp();
-    for (int k = lane; k < NSP; k += 32) {
-      const int f = __ldg(w_segf + k), c = __ldg(w_segc + k);
-      double w = c > 0 ? sP[f] : 0.0;
-      for (int q = 1; q < c; ++q) w += sP[f + q];
-      g_omega[(i64)k * n + p] = w;
-    }
-    __syncwarp();
+    k << "  wload_tables(s_exp, s_log, s_nu);\n  __syncthreads();\n";
+    return std::make_pair(wpb, 8 * (776 + wpb * words));
+  };
+  // ===================== forward =====================
+  {
+    WLayout L;
+    L.arrays = {{"sY", N1}, {"sL", std::max(N1, gF.nseg)}, {"sA", N1}, {"sR", M}};
+    std::ostringstream k;
+    k << o.str() << nw.str();
+    emit_gather_tables(k, gF, 0, false);
+    auto wp = kernel_head(k, L,
+        "// Net production rates, one warp per state (Eq. production_rates); arguments as pyro_omega.\n"
+        "extern \"C\" __global__ void __launch_bounds__(WPB * 32) pyro_omega_warp(i64 n, const double* __restrict__ g_rho,\n"
+        "    const double* __restrict__ g_Tin, int energy_mode, const double* __restrict__ g_Y,\n"
+        "    double* __restrict__ g_Tout, double* __restrict__ g_omega, double T_guess, int max_iter, double tol,\n"
+        "    unsigned long long* __restrict__ g_fail, double* __restrict__ g_store)");
+    k << "  double* sP = sL;   // partial sums of the production rates (after the reactions)\n"
+         "  (void)g_store;\n  const float tolf = (float)tol;\n"
+         "  for (i64 base = (i64)blockIdx.x * WPB; base < n; base += (i64)gridDim.x * WPB) {\n"
+         "    const i64 p = base + warp;\n    if (p >= n) break;   // warp-uniform; no block barrier below\n"
+         "    const double rho = g_rho[p];\n    double ys = 0.0;\n"
+         "    for (int k = lane; k < NSP; k += 32) {\n      const double y = g_Y[(i64)k * n + p];\n"
+         "      sY[k] = y;\n      ys = fma(y, __ldg(w_invW + k), ys);\n    }\n"
+         "    if (lane == 0) sY[NSP] = 0.0;\n    const double ysum = warp_sum(ys);\n    __syncwarp();\n"
+         "    double T;\n    if (energy_mode) {\n      int it;\n"
+         "      T = wtsolve(sY, g_Tin[p], T_guess, max_iter, tolf, &it, lane);\n"
+         "      if (lane == 0) {\n        if (it < 0) atomicAdd(g_fail, 1ull);\n        if (g_Tout) g_Tout[p] = T;\n      }\n"
+         "    } else {\n      T = g_Tin[p];\n    }\n"
+         "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T);\n"
+         "    const int hi = pdm::to_float_trunc(T) >= (float)TMID;\n"
+         "    for (int k = lane; k < NSP; k += 32) {\n" << species_L(false) <<
+         "      sL[k] = q;\n      sA[k] = PEXP(q, s_exp) * (rho * sY[k]);\n    }\n"
+         "    if (lane == 0) { sL[NSP] = 0.0; sA[NSP] = 1.0; }\n";
+    if (plog) k << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lnR << ";\n";
+    k << "    __syncwarp();\n";
+    for (auto& c : P.chunks) emit_chunk(k, c, W_FWD);
+    k << "    __syncwarp();\n";
+    emit_gather_loop(k, gF, 0, 0, "acc = fma(s_nu[(e.x >> 16) & 7u], sR[e.x & 0xffffu], acc);", false, "sP");
+    k << "    __syncwarp();\n    for (int k = lane; k < NSP; k += 32) {\n" << gather_total(0, "sP", "w")
+      << "      g_omega[(i64)k * n + p] = w;\n    }\n    __syncwarp();\n  }\n}\n";
+    out.sources["wfwd"] = k.str();
+    out.stats["warp_fwd_warps_per_block"] = wp.first;
+    out.smem["wfwd"] = wp.second;
+    out.wpb["wfwd"] = wp.first;
   }
-}
-)";
-  out.sources["wfwd"] = k.str();
+  // ===================== JVP =====================
+  {
+    WLayout L;
+    L.arrays = {{"sY", N1}, {"sdY", N1}, {"sL", std::max(N1, gF.nseg)}, {"sA", N1}, {"sdA", N1}, {"sdL", N1}, {"sR", M}};
+    std::ostringstream k;
+    k << o.str();
+    emit_gather_tables(k, gF, 0, false);
+    auto wp = kernel_head(k, L,
+        "// JVP of the net production rates, one warp per state; arguments as pyro_jvp.  Per reaction the\n"
+        "// tangent dR = dkk D + kk (dP' - dP'') of the forward kernel's expression, intermediates recomputed.\n"
+        "extern \"C\" __global__ void __launch_bounds__(WPB * 32) pyro_jvp_warp(i64 n, const double* __restrict__ g_rho,\n"
+        "    const double* __restrict__ g_T, const double* __restrict__ g_Y, const double* __restrict__ g_drho,\n"
+        "    const double* __restrict__ g_dT, const double* __restrict__ g_dY, double* __restrict__ g_dw,\n"
+        "    double* __restrict__ g_store)");
+    k << "  double* sP = sL;\n  (void)g_store;\n"
+         "  for (i64 base = (i64)blockIdx.x * WPB; base < n; base += (i64)gridDim.x * WPB) {\n"
+         "    const i64 p = base + warp;\n    if (p >= n) break;\n"
+         "    const double rho = g_rho[p], T = g_T[p], drho = g_drho[p], dT = g_dT[p];\n"
+         "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
+         "    const double drr = drho * pdm::rcp(rho);\n"
+         "    const int hi = pdm::to_float_trunc(T) >= (float)TMID;\n"
+         "    double ys = 0.0, dys = 0.0;\n"
+         "    for (int k = lane; k < NSP; k += 32) {\n"
+         "      const double y = g_Y[(i64)k * n + p], dy = g_dY[(i64)k * n + p];\n"
+         "      sY[k] = y; sdY[k] = dy;\n"
+         "      ys = fma(y, __ldg(w_invW + k), ys); dys = fma(dy, __ldg(w_invW + k), dys);\n"
+      << species_L(true) <<
+         "      const double E = PEXP(q, s_exp);\n      const double a = E * (rho * y);\n"
+         "      sL[k] = q; sA[k] = a;\n"
+         "      sdA[k] = fma(a, fma(Lp, dT, drr), E * (rho * dy)); sdL[k] = Lp * dT;\n    }\n"
+         "    if (lane == 0) { sY[NSP] = 0.0; sdY[NSP] = 0.0; sL[NSP] = 0.0; sA[NSP] = 1.0; sdA[NSP] = 0.0; sdL[NSP] = 0.0; }\n"
+         "    const double ysum = warp_sum(ys), dysum = warp_sum(dys);\n";
+    if (plog) k << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lnR << ";\n";
+    k << "    __syncwarp();\n";
+    for (auto& c : P.chunks) emit_chunk(k, c, W_JVP);
+    k << "    __syncwarp();\n";
+    emit_gather_loop(k, gF, 0, 0, "acc = fma(s_nu[(e.x >> 16) & 7u], sR[e.x & 0xffffu], acc);", false, "sP");
+    k << "    __syncwarp();\n    for (int k = lane; k < NSP; k += 32) {\n" << gather_total(0, "sP", "w")
+      << "      g_dw[(i64)k * n + p] = w;\n    }\n    __syncwarp();\n  }\n}\n";
+    out.sources["wjvp"] = k.str();
+    out.stats["warp_jvp_warps_per_block"] = wp.first;
+    out.smem["wjvp"] = wp.second;
+    out.wpb["wjvp"] = wp.first;
+  }
+  // ===================== VJP =====================
+  {
+    WLayout L;
+    L.arrays = {{"sY", std::max(N1, gA.nseg)}, {"sWb", std::max(N1, gC.nseg)}, {"sL", N1}, {"sA", N1}, {"sLp", N1},
+                {"sDb", M}, {"sMb", std::max(1, M - P.nplain)}};
+    std::ostringstream k;
+    k << o.str();
+    emit_gather_tables(k, gA, 1, false);
+    emit_gather_tables(k, gC, 2, true);
+    auto wp = kernel_head(k, L,
+        "// VJP (reverse mode) of the net production rates, one warp per state; arguments as pyro_vjp.\n"
+        "// Per reaction the adjoint R_bar = sum_k nu_kj omega_bar_k; the species adjoints of the\n"
+        "// activity products and of [M] are gathered per species afterwards (nothing stored\n"
+        "// between calls; the per-reaction intermediates are recomputed).\n"
+        "extern \"C\" __global__ void __launch_bounds__(WPB * 32) pyro_vjp_warp(i64 n, const double* __restrict__ g_rho,\n"
+        "    const double* __restrict__ g_T, const double* __restrict__ g_Y, const double* __restrict__ g_wb,\n"
+        "    double* __restrict__ g_rhob, double* __restrict__ g_Tb, double* __restrict__ g_Yb,\n"
+        "    double* __restrict__ g_store)");
+    k << "  double* sPa = sY;    // partial sums of the activity adjoints (after the reactions)\n"
+         "  double* sPc = sWb;   // partial sums of the efficiency adjoints\n  (void)g_store;\n"
+         "  for (i64 base = (i64)blockIdx.x * WPB; base < n; base += (i64)gridDim.x * WPB) {\n"
+         "    const i64 p = base + warp;\n    if (p >= n) break;\n"
+         "    const double rho = g_rho[p], T = g_T[p];\n"
+         "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
+         "    const int hi = pdm::to_float_trunc(T) >= (float)TMID;\n"
+         "    double ys = 0.0;\n"
+         "    for (int k = lane; k < NSP; k += 32) {\n"
+         "      const double y = g_Y[(i64)k * n + p];\n"
+         "      sY[k] = y; sWb[k] = g_wb[(i64)k * n + p];\n"
+         "      ys = fma(y, __ldg(w_invW + k), ys);\n"
+      << species_L(true) <<
+         "      sL[k] = q; sA[k] = PEXP(q, s_exp) * (rho * y); sLp[k] = Lp;\n    }\n"
+         "    if (lane == 0) { sY[NSP] = 0.0; sWb[NSP] = 0.0; sL[NSP] = 0.0; sA[NSP] = 1.0; sLp[NSP] = 0.0; }\n"
+         "    const double ysum = warp_sum(ys);\n";
+    if (plog) k << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lnR << ";\n";
+    k << "    double Tbp = 0.0, Mtp = 0.0, rMp = 0.0;\n    __syncwarp();\n";
+    for (auto& c : P.chunks) emit_chunk(k, c, W_VJP);
+    k << "    __syncwarp();\n    const double Mtot = warp_sum(Mtp);\n";
+    // activity adjoints: entries with one other factor, then with two (sign bit 16 of x: product side)
+    emit_gather_loop(k, gA, 1, 0,
+        "const double db = sDb[e.x & 0xffffu]; acc = (e.x >> 16) & 1u ? fma(-db, sA[e.y & 1023u], acc) : "
+        "fma(db, sA[e.y & 1023u], acc);", false, "sPa");
+    emit_gather_loop(k, gA, 1, 1,
+        "const double db = sDb[e.x & 0xffffu]; const double pa = sA[e.y & 1023u] * sA[(e.y >> 10) & 1023u]; "
+        "acc = (e.x >> 16) & 1u ? fma(-db, pa, acc) : fma(db, pa, acc);", false, "sPa");
+    emit_gather_loop(k, gC, 2, 0, "acc = fma(sMb[e.x & 0xffffu], c, acc);", true, "sPc");
+    k << "    __syncwarp();\n    double rbp = 0.0;\n"
+         "    for (int k = lane; k < NSP; k += 32) {\n" << gather_total(1, "sPa", "ab") << gather_total(2, "sPc", "sc") <<
+         "      const double ta = ab * sA[k];\n      Tbp = fma(ta, sLp[k], Tbp);\n      rbp += ta;\n"
+         "      g_Yb[(i64)k * n + p] = fma(ab, PEXP(sL[k], s_exp) * rho, rho * fma(Mtot, __ldg(w_invW + k), sc));\n"
+         "    }\n"
+         "    const double Tb = warp_sum(Tbp), rhob = warp_sum(rbp), rhobM = warp_sum(rMp);\n"
+         "    if (lane == 0) { g_Tb[p] = Tb; g_rhob[p] = fma(rhob, pdm::rcp(rho), rhobM); }\n"
+         "    __syncwarp();\n  }\n}\n";
+    out.sources["wvjp"] = k.str();
+    out.stats["warp_vjp_warps_per_block"] = wp.first;
+    out.smem["wvjp"] = wp.second;
+    out.wpb["wvjp"] = wp.first;
+  }
+  out.stats["warp_chunks"] = (double)P.chunks.size();
+  out.stats["warp_gather_steps"] = gF.loops[0].steps;
+  out.stats["warp_segments"] = gF.nseg;
+  out.stats["warp_warps_per_block"] = out.wpb["wfwd"];
+  out.stats["warp_smem_bytes"] = out.smem["wfwd"];
+  out.warps_per_block = out.wpb["wfwd"];
+  out.smem_bytes = out.smem["wfwd"];
   return out;
 }
 

@@ -11,10 +11,13 @@
 namespace pyro {
 
 struct WarpEmit {
-  std::map<std::string, std::string> sources;   // "wfwd": pyro_omega_warp
+  // "wfwd": pyro_omega_warp, "wjvp": pyro_jvp_warp, "wvjp": pyro_vjp_warp
+  std::map<std::string, std::string> sources;
   std::map<std::string, double> stats;
-  int warps_per_block = 8;                      // states per block
-  int smem_bytes = 0;                           // dynamic shared memory per block
+  std::map<std::string, int> wpb;               // warps (states) per block of each kernel
+  std::map<std::string, int> smem;              // dynamic shared memory per block of each kernel
+  int warps_per_block = 8;                      // of the forward kernel
+  int smem_bytes = 0;
 };
 
 // Limits of the emitted tables (packed indices): species, reactions, and the

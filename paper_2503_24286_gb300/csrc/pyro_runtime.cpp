@@ -495,7 +495,7 @@ int ensure_store(pyro_mech* h, size_t bytes) {
 const char* group_kernel(const std::string& g) {
   return g == "jvp" ? "pyro_jvp" : g == "vjp" ? "pyro_vjp" : g == "jad" ? "pyro_jacobian_adiabatic"
        : g == "cn" ? "pyro_cn_assemble" : g == "tr" ? "pyro_transport" : g == "wfwd" ? "pyro_omega_warp"
-       : "pyro_jacobian";
+       : g == "wjvp" ? "pyro_jvp_warp" : g == "wvjp" ? "pyro_vjp_warp" : "pyro_jacobian";
 }
 
 // Compile (in parallel threads, cached on disk) and load the named derivative
@@ -538,7 +538,10 @@ int ensure_groups(pyro_mech* h, const std::vector<std::string>& names) {
     r = d.ModuleGetFunction(&G.f, G.module, group_kernel(todo[i]));
     if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, std::string("missing kernel ") + group_kernel(todo[i]));
     if (todo[i] == "tr") { G.block = pyro::kTransportBlock; G.smem = h->emitted.smem_dyn_bytes_transport; }
-    if (todo[i][0] == 'w') { G.block = 32 * h->emitted.warp_wpb; G.smem = h->emitted.smem_dyn_bytes_warp; }
+    if (todo[i][0] == 'w') {
+      G.block = 32 * h->emitted.warp_wpb.at(todo[i]);
+      G.smem = h->emitted.smem_dyn_bytes_warp.at(todo[i]);
+    }
     if (todo[i] == "jac" || todo[i] == "jad" || todo[i] == "cn") G.smem = h->emitted.smem_dyn_bytes_jac;
     const int smem = G.smem >= 0 ? G.smem : h->emitted.smem_dyn_bytes_deriv;
     const int blk = G.block > 0 ? G.block : h->opt.deriv_block;
@@ -901,13 +904,13 @@ int pyro_mech_prepare(const pyro_mech* hc, const char* kernels) {
   std::string k = kernels ? kernels : "all";
   std::vector<std::string> names;
   if (k == "all") {
-    names = {"jvp", "vjp", "jac"};
+    names = {h->opt.warp ? "wjvp" : "jvp", h->opt.warp ? "wvjp" : "vjp", "jac"};
   }
   else {
     std::string item;
     std::stringstream ss(k);
     while (std::getline(ss, item, ',')) {
-      if (item == "jvp" || item == "vjp") names.push_back(item);
+      if (item == "jvp" || item == "vjp") names.push_back(h->opt.warp ? "w" + item : item);
       else if (item == "jacobian" || item == "jac") names.push_back("jac");
       else if (item == "jacobian_adiabatic" || item == "jad") names.push_back("jad");
       else if (item == "cn" || item == "crank_nicolson") names.push_back("cn");
@@ -929,15 +932,17 @@ int pyro_jvp(const pyro_mech* hc, int64_t n, const double* rho, const double* T,
     return fail(PYRO_EINVAL, "pyro_jvp: bad arguments");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
-  if (int rc = ensure_groups(h, {"jvp"})) return rc;
+  const std::string g = h->opt.warp ? "wjvp" : "jvp";   // one warp or one thread per state
+  if (int rc = ensure_groups(h, {g})) return rc;
   const int64_t NS = h->m.n_species();
   return with_args(h, n, {{rho, 1, 8, true, false}, {T, 1, 8, true, false}, {Y, NS, 8, true, false}, {d_rho, 1, 8, true, false},
                        {d_T, 1, 8, true, false}, {d_Y, NS, 8, true, false}, {d_omega, NS, 8, false, true}},
                    stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
                      long long nn = nc;
-                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &d[4], &d[5], &d[6], &h->groups["jvp"].store};
-                     return launch_deriv(h, h->groups["jvp"], nc, st, params);
-                   });
+                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &d[4], &d[5], &d[6], &h->groups[g].store};
+                     if (h->opt.warp) return launch_warp(h, h->groups[g], nc, st, params);
+                     return launch_deriv(h, h->groups[g], nc, st, params);
+                   }, h->opt.warp);
 }
 
 int pyro_vjp(const pyro_mech* hc, int64_t n, const double* rho, const double* T, const double* Y,
@@ -947,15 +952,17 @@ int pyro_vjp(const pyro_mech* hc, int64_t n, const double* rho, const double* T,
     return fail(PYRO_EINVAL, "pyro_vjp: bad arguments");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
-  if (int rc = ensure_groups(h, {"vjp"})) return rc;
+  const std::string g = h->opt.warp ? "wvjp" : "vjp";
+  if (int rc = ensure_groups(h, {g})) return rc;
   const int64_t NS = h->m.n_species();
   return with_args(h, n, {{rho, 1, 8, true, false}, {T, 1, 8, true, false}, {Y, NS, 8, true, false}, {omega_bar, NS, 8, true, false},
                        {rho_bar, 1, 8, false, true}, {T_bar, 1, 8, false, true}, {Y_bar, NS, 8, false, true}},
                    stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
                      long long nn = nc;
-                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &d[4], &d[5], &d[6], &h->groups["vjp"].store};
-                     return launch_deriv(h, h->groups["vjp"], nc, st, params);
-                   });
+                     void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &d[4], &d[5], &d[6], &h->groups[g].store};
+                     if (h->opt.warp) return launch_warp(h, h->groups[g], nc, st, params);
+                     return launch_deriv(h, h->groups[g], nc, st, params);
+                   }, h->opt.warp);
 }
 
 int pyro_jacobian(const pyro_mech* hc, int64_t n, const double* rho, const double* T, const double* Y,

@@ -191,3 +191,40 @@ def test_large_warp_variant(large, dev, mech_files):
     wt = m.net_production_rates(r, Y, T=T0)
     scale = wt.abs().amax(dim=0, keepdim=True) + 1e-300
     assert ((ww - wt).abs() <= 1e-9 * scale).all().item()
+
+
+def test_large_warp_jvp_vjp_parity(large, dev, mech_files):
+    """Warp-per-state JVP and VJP on the 160-species mechanism (the large-mechanism
+    derivative kernels: intermediates recomputed per reaction, nothing stored):
+    against the oracle entry by entry, and against the thread-per-state kernels on
+    2^14 states."""
+    from paper_2503_24286_gb300 import binding as B
+    m, orc = large
+    mw = B.Mechanism(mech_files[0][4], "variant=warp")
+    n = 37
+    st = synth.config_states(4, n=n, offset_seed=9)
+    rho = orc.density(st.p, st.T, st.Y)
+    rng = np.random.default_rng(2)
+    dr, dT, dY = rng.standard_normal(n) * rho * 0.1, rng.standard_normal(n) * 5, rng.standard_normal((160, n)) * 1e-3
+    u = rng.standard_normal((160, n))
+    g = mw.jvp(*[_t(a, dev) for a in (rho, st.T, st.Y, dr, dT, dY)]).cpu().numpy()
+    assert np.all(np.abs(g - orc.jvp(rho, st.T, st.Y, dr, dT, dY)) <=
+                  TOL_D * orc.jvp_scale(rho, st.T, st.Y, dr, dT, dY) + 1e-300)
+    rb, Tb, Yb = (x.cpu().numpy() for x in mw.vjp(_t(rho, dev), _t(st.T, dev), _t(st.Y, dev), _t(u, dev)))
+    orb, oTb, oYb = orc.vjp(rho, st.T, st.Y, u)
+    sc = orc.vjp_scale(rho, st.T, st.Y, u)
+    assert np.all(np.abs(rb - orb) <= TOL_D * sc[0] + 1e-300)
+    assert np.all(np.abs(Tb - oTb) <= TOL_D * sc[1] + 1e-300)
+    assert np.all(np.abs(Yb - oYb) <= TOL_D * sc[2:] + 1e-300)
+    # the two kernel families agree on many states (same inputs, different summation order)
+    n = 2 ** 14
+    cfg = synth.CONFIGS[4]
+    T0, p, Y = synth.generate_states_torch(160, n, cfg["T"], cfg["p_atm"], 98, dev)
+    r = m.density(p, T0, Y)
+    gen = torch.Generator(device=dev).manual_seed(4)
+    v = [torch.randn(n, dtype=torch.float64, device=dev, generator=gen) * r * 1e-3,
+         torch.randn(n, dtype=torch.float64, device=dev, generator=gen),
+         torch.randn((160, n), dtype=torch.float64, device=dev, generator=gen) * 1e-4]
+    jw, jt = mw.jvp(r, T0, Y, *v), m.jvp(r, T0, Y, *v)
+    sc = jt.abs().amax(dim=0, keepdim=True) + 1e-300
+    assert torch.isfinite(jw).all().item() and ((jw - jt).abs() <= 1e-9 * sc).all().item()
