@@ -421,7 +421,9 @@ template <class S> S forward_rate_coefficient(const OMech& m, const OReaction& r
   S k0 = arrhenius(r.A0, r.b0, r.theta0, T);
   S Pr = k0 * third_body(r, C, N) / kinf;
   if (re(Pr) < 1e-300) Pr = Pr - re(Pr) + 1e-300;   // guard log10(0) (reading (c8))
-  return kinf * (Pr / (1.0 + Pr)) * falloff_factor(r, T, Pr);
+  // Pr/(1+Pr) written as 1/(1 + 1/Pr): the same value, but its complex-step
+  // derivative does not subtract two nearly equal numbers when Pr >> 1
+  return kinf / (1.0 + 1.0 / Pr) * falloff_factor(r, T, Pr);
 }
 
 // K_j = (p0/(R T))^{sum_i nu_ij} exp(-sum_i nu_ij g_i/(R T))      (Eq. equil_constants, reading (c1))

@@ -173,3 +173,35 @@ def test_mlp_forward_tiny_network_by_hand():
     Pt = P.copy()
     Pt[0:4] = [W1[0], W1[2], W1[1], W1[3]]
     assert abs(O.mlp_forward(D, H, Pt, x)[0] - g["y"]) > 1e-5
+
+
+@pytest.mark.parametrize("lnPr", [-46.0, 0.0, 46.0, 69.0])
+def test_falloff_blend_derivative_at_extreme_pr(tmp_path, lnPr):
+    """Lindemann falloff H + O2 (+M) <=> OH + O with an inert N2 that enters only
+    [M]: with k = k_inf Pr/(1+Pr), Pr = k0 [M]/k_inf, the derivative of the rate
+    of progress R = k P (P = C_H C_O2 - C_OH C_O/K_c) along Y_N2 is
+    dR/dY_N2 = R/([M] (1 + Pr)) * rho/W_N2 in closed form.  The oracle's complex
+    step must reproduce it from Pr = 1e-20 to Pr = 1e30 (where 1 - Pr/(1+Pr)
+    cancels to nothing in floating point)."""
+    A, b, th, A0, b0, th0 = 1e12, 0.3, 4000.0, 1e16, -1.0, 1000.0
+    m = handmech.abcd_mechanism(kind="falloff", A=A, b=b, theta=th, low=(A0, b0, th0))
+    m.species.append(handmech.const_cp_species("N2", {"N": 2}, 3.5, 0.0, 23.0))
+    m.elements.append(("N", synth.ATOMIC_WEIGHTS["N"]))
+    o = O.Oracle(handmech.write(m, str(tmp_path), "lind_inert.txt"))
+    T = np.array([800.0, 1500.0])
+    Y = np.array([[0.1, 0.2], [0.2, 0.1], [0.15, 0.25], [0.05, 0.15], [0.5, 0.3]])
+    Wm = 1.0 / (Y / o.W[:, None]).sum(axis=0)
+    kinf = A * T ** b * np.exp(-th / T)
+    k0 = A0 * T ** b0 * np.exp(-th0 / T)
+    M = math.exp(lnPr) * kinf / k0              # [M] that puts Pr at e^lnPr
+    rho = M * Wm
+    d = o.reaction_data(rho, T, Y)
+    R_ = d["Rf"][0] - d["Rr"][0]
+    Pr = k0 * M / kinf
+    expect = R_ / (M * (1.0 + Pr)) * rho / o.W[4]
+    e4 = np.zeros((5, 2))
+    e4[4] = 1.0
+    dw = o.jvp(rho, T, Y, np.zeros(2), np.zeros(2), e4)     # d omega / d Y_N2
+    assert np.allclose(dw[0], -expect, rtol=1e-12, atol=0)  # omega_H = -R
+    assert np.allclose(dw[2], expect, rtol=1e-12, atol=0)   # omega_OH = +R
+    assert np.all(dw[4] == 0.0)
