@@ -591,11 +591,14 @@ void emit_reaction_core(Src& s, const Mechanism& m, const Reaction& r) {
       s << "      const double lnPr = fma(" << lit(r.b0 - r.b) << ", lnT, " << lit((double)(logl(r.A0) - logl(r.A)))
         << ") + fma(" << lit(-(r.theta0 - r.theta)) << ", invT, pdm::log(M, s_log));\n";
       s << "      const double pT = fma(" << lit(r.b0 - r.b) << ", invT, " << lit(r.theta0 - r.theta) << " * invT2);\n";
-      s << "      const double fpr = pdm::rcp(1.0 + PEXP(-lnPr, s_exp));\n";
-      s.fma(3); s.add(2); s.mul(); s.log_(); s.exp_(); s.rcp_();   // lnPr, pT, fpr
+      // 1 - Pr/(1+Pr) = q Pr/(1+Pr) with q = 1/Pr: formed as a product (the difference
+      // cancels to nothing for Pr >> 1)
+      s << "      const double qpr = PEXP(-lnPr, s_exp);\n      const double fpr = pdm::rcp(1.0 + qpr);\n"
+           "      const double cpr = qpr * fpr;\n";
+      s.fma(3); s.add(2); s.mul(2); s.log_(); s.exp_(); s.rcp_();   // lnPr, pT, fpr, 1 - fpr
       if (r.n_sri >= 3) {
         emit_sri(s, r, true);
-        s << "      const double sPr = (1.0 - fpr) + dlnF_dlnPr;\n";
+        s << "      const double sPr = cpr + dlnF_dlnPr;\n";
         s << "      tau += fma(sPr, pT, dlnF_dT);\n";
         s << "      const double kk = kt * fpr * F;\n";
         s.add(3); s.fma(); s.mul(2);
@@ -633,12 +636,12 @@ void emit_reaction_core(Src& s, const Mechanism& m, const Reaction& r) {
         s << "      const double f = den2 * rD; const double F = PEXP(lfc * f * " << lit((double)logl(10.0L)) << ", s_exp);\n";
         s << "      const double rD2 = rD * rD;\n";
         s << "      const double Axx = lfc * (-2.0 * den2 * xx * rD2); const double Aden = lfc * (2.0 * den * xx * xx * rD2);\n";
-        s << "      const double sPr = (1.0 - fpr) + fma(-0.14, Aden, Axx);\n";
+        s << "      const double sPr = cpr + fma(-0.14, Aden, Axx);\n";
         s << "      const double sfc = fma(-0.67, Axx, fma(-1.1762, Aden, f));\n";
         s << "      tau += fma(sPr, pT, sfc * dfc * pdm::rcp(fc));\n";
         s << "      const double kk = kt * fpr * F;\n";
       } else {
-        s << "      const double sPr = 1.0 - fpr;\n      tau += sPr * pT;\n      const double kk = kt * fpr;\n";
+        s << "      const double sPr = cpr;\n      tau += sPr * pT;\n      const double kk = kt * fpr;\n";
         s.add(2); s.mul(2);
       }
       s << "      const double kM = kk * sPr * pdm::rcp(M);\n";

@@ -334,8 +334,11 @@ void emit_chunk(std::ostringstream& rc, const WChunk& c, int mode) {
   } else {
     rc << "      const double lnPr = fma(" << F(1) << ", lnT, " << F(0) << ") + fma(" << F(2)
        << ", invT, pdm::log(M, s_log));\n"
-          "      const double fpr = pdm::rcp(1.0 + PEXP(-lnPr, s_exp));\n";
-    if (der) rc << "      const double pT = fma(" << F(1) << ", invT, -" << F(2) << " * invT2);\n";
+          "      const double qpr = PEXP(-lnPr, s_exp);\n"
+          "      const double fpr = pdm::rcp(1.0 + qpr);\n";
+    if (der)
+      rc << "      const double pT = fma(" << F(1) << ", invT, -" << F(2) << " * invT2);\n"
+            "      const double cpr = qpr * fpr;   // 1 - Pr/(1+Pr) without cancellation\n";
     if (c.kind == WK_TROE3 || c.kind == WK_TROE4) {
       rc << "      const double t1 = " << F(3) << " * PEXP(T * " << F(4) << ", s_exp);\n"
             "      const double t2 = " << F(5) << " * PEXP(T * " << F(6) << ", s_exp);\n";
@@ -355,7 +358,7 @@ void emit_chunk(std::ostringstream& rc, const WChunk& c, int mode) {
               "      const double Fb = PEXP(lfc * f * " << ln10 << ", s_exp);\n"
               "      const double rD2 = rD * rD;\n"
               "      const double Axx = lfc * (-2.0 * den2 * xx * rD2), Aden = lfc * (2.0 * den * xx * xx * rD2);\n"
-              "      const double sPr = (1.0 - fpr) + fma(-0.14, Aden, Axx);\n"
+              "      const double sPr = cpr + fma(-0.14, Aden, Axx);\n"
               "      const double sfc = fma(-0.67, Axx, fma(-1.1762, Aden, f));\n";
         if (c.kind == WK_TROE4)
           rc << "      const double dfc = fma(t1, " << F(4) << ", fma(t2, " << F(6) << ", -(t3 * " << F(7) << ") * invT2));\n";
@@ -376,11 +379,11 @@ void emit_chunk(std::ostringstream& rc, const WChunk& c, int mode) {
         rc << "      const double dlnF_dlnPr = slS * (-2.0 * su * sX * sX * " << lit(inv_ln10) << ");\n"
               "      const double dlnF_dT = fma(sX * fma(sea, -" << F(4) << " * invT2, seb * " << F(5)
            << "), pdm::rcp(sS), " << F(7) << " * invT);\n"
-              "      const double sPr = (1.0 - fpr) + dlnF_dlnPr;\n"
+              "      const double sPr = cpr + dlnF_dlnPr;\n"
               "      tau += fma(sPr, pT, dlnF_dT);\n";
       rc << "      const double kk = kt * fpr * Fb;\n";
     } else {   // Lindemann
-      if (der) rc << "      const double sPr = 1.0 - fpr;\n      tau += sPr * pT;\n";
+      if (der) rc << "      const double sPr = cpr;\n      tau += sPr * pT;\n";
       rc << "      const double kk = kt * fpr;\n";
     }
     if (der) rc << "      const double kM = kk * sPr * pdm::rcp(M);\n";

@@ -10,6 +10,13 @@ within 1e-11 of its gross scale (reading c15; for derivatives the oracle's GJ):
   and infinity for every Troe and SRI reaction.
 * Lindemann falloff (falloff data without Troe or SRI constants, F = 1): the
   53-species mechanism with its Troe data removed.
+
+The equilibrium states span mass fractions down to ~1e-230, so some rates and
+their derivatives fall near the bottom of the double range.  The oracle's
+complex-step derivatives (step 1e-30) carry f' h in the imaginary part, which
+loses its relative precision once |f'| drops below ~1e-266; derivative entries
+are therefore compared with an absolute floor of 1e-250 added to 1e-11 of their
+gross scale (DER_FLOOR), far below any entry that matters.
 """
 import math
 
@@ -25,6 +32,7 @@ pytestmark = pytest.mark.gpu
 R = 8314.462618
 P0 = 101325.0
 TOL = 1e-11
+DER_FLOOR = 1e-250
 
 
 @pytest.fixture(scope="module")
@@ -113,20 +121,20 @@ def _check_derivatives(m, o, rho, T, Y, dev, seed):
         rng.standard_normal((o.N, n)) * 1e-3
     tr, tT, tY = _t(rho, dev), _t(T, dev), _t(Y, dev)
     g = m.jvp(tr, tT, tY, _t(dr, dev), _t(dT, dev), _t(dY, dev)).cpu().numpy()
-    assert np.all(np.abs(g - o.jvp(rho, T, Y, dr, dT, dY)) <= TOL * o.jvp_scale(rho, T, Y, dr, dT, dY) + 1e-300)
+    assert np.all(np.abs(g - o.jvp(rho, T, Y, dr, dT, dY)) <= TOL * o.jvp_scale(rho, T, Y, dr, dT, dY) + DER_FLOOR)
     u = rng.standard_normal((o.N, n))
     rb, Tb, Yb = (x.cpu().numpy() for x in m.vjp(tr, tT, tY, _t(u, dev)))
     orb, oTb, oYb = o.vjp(rho, T, Y, u)
     sc = o.vjp_scale(rho, T, Y, u)
-    assert np.all(np.abs(rb - orb) <= TOL * sc[0] + 1e-300)
-    assert np.all(np.abs(Tb - oTb) <= TOL * sc[1] + 1e-300)
-    assert np.all(np.abs(Yb - oYb) <= TOL * sc[2:] + 1e-300)
+    assert np.all(np.abs(rb - orb) <= TOL * sc[0] + DER_FLOOR)
+    assert np.all(np.abs(Tb - oTb) <= TOL * sc[1] + DER_FLOOR)
+    assert np.all(np.abs(Yb - oYb) <= TOL * sc[2:] + DER_FLOOR)
     NP = o.N + 1
     J = m.jacobian(tr, tT, tY).cpu().numpy().reshape(NP, NP, n)
     Jo = o.jacobian(rho, T, Y).reshape(NP, NP, n)
     G = o.jacobian_gross(rho, T, Y)[:, 1:]
     assert np.all(np.isfinite(J))
-    assert np.all(np.abs(J - Jo) <= TOL * G + 1e-300)
+    assert np.all(np.abs(J - Jo) <= TOL * G + DER_FLOOR)
 
 
 @pytest.mark.parametrize("name,n", [("h2", 96), ("gri", 40), ("pdep", 24)])
