@@ -1896,7 +1896,9 @@ __device__ __forceinline__ unsigned pyro_f2bf(float f) {
   return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
 }
 __device__ __forceinline__ float pyro_bf2f(unsigned h) { return __uint_as_float(h << 16); }
-__device__ __forceinline__ float pyro_silu(float z) { return z / (1.0f + expf(-z)); }
+// SiLU z / (1 + e^-z) with the hardware exp2 and reciprocal (a few ulp of FP32):
+// the result is rounded to bf16 (8 significant bits) right after
+__device__ __forceinline__ float pyro_silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 // one 16x8x16 BF16 MMA with FP32 accumulation
 __device__ __forceinline__ void pyro_mma(float* c, unsigned a0, unsigned a1, unsigned a2, unsigned a3,
