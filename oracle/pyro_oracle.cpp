@@ -946,16 +946,27 @@ void orc_jacobian(void* h, int64_t n, const double* rho, const double* T, const 
   }
 }
 
-// JVP of omega(rho, T, Y) along (drho, dT, dY) by complex step: domega [N][n]
+// JVP of omega(rho, T, Y) along v = (drho, dT, dY): domega = sum_c (d omega/d x_c) v_c, [N][n],
+// the columns by complex step one variable at a time.  (A single complex step along
+// v would also carry products of the perturbations of different variables into the
+// imaginary part wherever h |v_c| is not small against |x_c|, e.g. for mass
+// fractions far below the step.)
 void orc_jvp(void* h, int64_t n, const double* rho, const double* T, const double* Y,
              const double* drho, const double* dT, const double* dY, double* domega) {
   OMech* m = (OMech*)h; int N = m->N();
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(dynamic, 4)
   for (int64_t i = 0; i < n; ++i) {
     std::vector<cplx> y(N), w(N);
-    for (int k = 0; k < N; ++k) y[k] = cplx(Y[k * n + i], CS_H * dY[k * n + i]);
-    net_production_rates<cplx>(*m, cplx(rho[i], CS_H * drho[i]), cplx(T[i], CS_H * dT[i]), y.data(), w.data());
-    for (int k = 0; k < N; ++k) domega[k * n + i] = w[k].imag() / CS_H;
+    std::vector<double> acc(N, 0.0);
+    for (int c = 0; c < N + 2; ++c) {
+      const double vc = c == 0 ? drho[i] : c == 1 ? dT[i] : dY[(c - 2) * n + i];
+      if (vc == 0.0) continue;
+      cplx rc(rho[i], c == 0 ? CS_H : 0.0), Tc(T[i], c == 1 ? CS_H : 0.0);
+      for (int k = 0; k < N; ++k) y[k] = cplx(Y[k * n + i], (c == k + 2) ? CS_H : 0.0);
+      net_production_rates<cplx>(*m, rc, Tc, y.data(), w.data());
+      for (int k = 0; k < N; ++k) acc[k] += (w[k].imag() / CS_H) * vc;
+    }
+    for (int k = 0; k < N; ++k) domega[k * n + i] = acc[k];
   }
 }
 

@@ -25,6 +25,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2503_24286_gb300 import synth
+from tests.edge_states import equilibrium_states
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -72,40 +73,6 @@ def _t(a, dev):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
 
 
-def _equilibrium_states(o, mech, n, seed):
-    """n Gibbs-minimised states: T ~ U[600, 2800] K, element potentials
-    lambda_e ~ U[-3, 3] shifted by a common delta (lambda_e + delta is still a set of
-    element potentials) chosen by bisection so that rho = sum_k C_k W_k is
-    log-uniform in [0.05, 20] kg/m^3 (shifting every lambda_e by delta multiplies
-    C_k by exp(delta * atoms_k), so rho grows monotonically with delta)."""
-    els = [e for e, _ in mech.elements]
-    n_ke = np.array([[s.composition.get(e, 0) for e in els] for s in mech.species], dtype=float)
-    atoms = n_ke.sum(axis=1)
-    lnW = np.log(o.W)
-    rng = np.random.default_rng(seed)
-    T = rng.uniform(600.0, 2800.0, n)
-    Y = np.zeros((o.N, n))
-    rho = np.zeros(n)
-    for i in range(n):
-        lam = rng.uniform(-3.0, 3.0, len(els))
-        target = math.log(0.05) + rng.uniform(0.0, 1.0) * math.log(400.0)
-        gRT = np.array([o.species_thermo(k, T[i])[3] for k in range(o.N)])
-        base = math.log(P0 / (R * T[i])) - gRT + n_ke @ lam
-
-        def lnrho(d):
-            v = base + d * atoms + lnW
-            mx = v.max()
-            return mx + math.log(np.exp(v - mx).sum())
-        lo, hi = -200.0, 200.0
-        for _ in range(200):
-            mid = 0.5 * (lo + hi)
-            lo, hi = (mid, hi) if lnrho(mid) < target else (lo, mid)
-        C = np.exp(base + 0.5 * (lo + hi) * atoms)
-        rho[i] = float((C * o.W).sum())
-        Y[:, i] = C * o.W / rho[i]
-    return rho, T, Y
-
-
 def _check_forward(m, o, rho, T, Y, dev):
     w = m.net_production_rates(_t(rho, dev), _t(Y, dev), T=_t(T, dev)).cpu().numpy()
     ow, G = o.net_production_rates(rho, T, Y, with_gross=True)
@@ -140,7 +107,7 @@ def _check_derivatives(m, o, rho, T, Y, dev, seed):
 @pytest.mark.parametrize("name,n", [("h2", 96), ("gri", 40), ("pdep", 24)])
 def test_gibbs_equilibrium_states(mechs, dev, name, n):
     m, o, mech = mechs[name]
-    rho, T, Y = _equilibrium_states(o, mech, n, seed=17)
+    rho, T, Y = equilibrium_states(o, mech, n, seed=17)
     w, G = _check_forward(m, o, rho, T, Y, dev)
     # every rate of progress vanishes: omega is zero to the gross scale on the GPU too
     assert np.all(np.abs(w) <= TOL * G + 1e-300)

@@ -205,3 +205,46 @@ def test_falloff_blend_derivative_at_extreme_pr(tmp_path, lnPr):
     assert np.allclose(dw[0], -expect, rtol=1e-12, atol=0)  # omega_H = -R
     assert np.allclose(dw[2], expect, rtol=1e-12, atol=0)   # omega_OH = +R
     assert np.all(dw[4] == 0.0)
+
+
+def test_jvp_is_linear_at_states_with_tiny_mass_fractions(orc):
+    """The JVP is the linear map J v: at states whose mass fractions reach 1e-200
+    (far below the complex step) it must stay additive in v and reproduce the
+    Jacobian's columns along unit directions."""
+    o, _ = orc[1]
+    st, rho = _states(1, 3, o, seed=35)
+    Y = st.Y.copy()
+    Y[:10] = 10.0 ** -np.arange(150.0, 250.0, 10.0)[:, None]
+    Y /= Y.sum(axis=0, keepdims=True)
+    rng = np.random.default_rng(36)
+    v1 = [rng.standard_normal(3) * rho * 0.1, rng.standard_normal(3) * 10.0, rng.standard_normal((o.N, 3)) * 1e-3]
+    v2 = [rng.standard_normal(3) * rho * 0.1, rng.standard_normal(3) * 10.0, rng.standard_normal((o.N, 3)) * 1e-3]
+    j1, j2 = o.jvp(rho, st.T, Y, *v1), o.jvp(rho, st.T, Y, *v2)
+    j12 = o.jvp(rho, st.T, Y, *[a + b for a, b in zip(v1, v2)])
+    sc = o.jvp_scale(rho, st.T, Y, *[np.abs(a) + np.abs(b) for a, b in zip(v1, v2)])
+    assert np.all(np.abs(j12 - j1 - j2) <= 1e-13 * sc + 1e-300)
+    NP = o.N + 1
+    J = o.jacobian(rho, st.T, Y).reshape(NP, NP, 3)
+    for c in (0, 1, 5, 12):                     # T and three mass fractions (two of them tiny)
+        dT = np.full(3, 1.0 if c == 0 else 0.0)
+        dY = np.zeros((o.N, 3))
+        if c > 0:
+            dY[c - 1] = 1.0
+        assert np.array_equal(o.jvp(rho, st.T, Y, np.zeros(3), dT, dY), J[1:, c])
+
+
+def test_jvp_bounded_by_gross_scale_at_equilibrium_states(orc):
+    """At Gibbs-minimised equilibrium states (mass fractions down to ~1e-230) the
+    JVP obeys the triangle inequality |J v|_k <= sum_c GJ_kc |v_c| entry by entry.
+    (A single complex step along v breaks it there: products of the
+    perturbations of different species, far larger than those species' mass
+    fractions, leak into the imaginary part.)"""
+    from tests.edge_states import equilibrium_states
+    o, mech = orc[1]
+    rho, T, Y = equilibrium_states(o, mech, 40, seed=17)
+    rng = np.random.default_rng(18)
+    n = T.size
+    dr, dT, dY = rng.standard_normal(n) * rho * 0.1, rng.standard_normal(n) * 10.0, rng.standard_normal((o.N, n)) * 1e-3
+    j = o.jvp(rho, T, Y, dr, dT, dY)
+    sc = o.jvp_scale(rho, T, Y, dr, dT, dY)
+    assert np.all(np.abs(j) <= sc * (1 + 1e-12) + 1e-300)
