@@ -608,6 +608,47 @@ def transport_rates(mech, synth, dev, stream, args, rank):
             "fp64_pipe_frac": ops * n / (ms * 1e-3) / (args.fp64_peak * 1e9 / 2)}
 
 
+def run_rows_only(args):
+    """--only ROWS: run just the named secondary rows (for profiling one kernel
+    family under ncu without the headline launches before it) and print one JSON
+    line with those rows; no headline value."""
+    import torch
+    from paper_2503_24286_gb300 import binding as B
+    from paper_2503_24286_gb300 import build as BLD
+    from paper_2503_24286_gb300 import synth
+    rank, _ = rank_world()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    BLD.build()
+    args.fp64_peak = fp64_peak_gflops(torch.cuda.get_device_properties(dev).multi_processor_count,
+                                      sm_max_mhz_of(local))
+    rows = set(args.only.split(","))
+    stream = torch.cuda.current_stream(dev)
+    d = tempfile.mkdtemp()
+    path = os.path.join(d, "mech.txt")
+    synth.write_mechanism(synth.config_mechanism(CONFIG_INDEX), path)
+    out = {}
+    if "large" in rows:
+        path4 = large_mechanism_path(synth)
+        args.large_compile, _ = start_large_compile(path4)
+        out["large_mechanism"] = large_mechanism_rates(path4, synth, dev, stream, args, rank)
+    mech = B.Mechanism(path) if rows & {"derivatives", "learned", "transport"} else None
+    if "derivatives" in rows:
+        out["derivatives"] = derivative_rates(mech, synth, dev, stream, args, rank)
+    if "learned" in rows:
+        out["learned_guess"] = learned_guess_rates(mech, path, synth, dev, stream, args, rank)
+    if "pdep" in rows:
+        out["pressure_dependent"] = pressure_dependent_rates(synth, dev, stream, args, rank)
+    if "transport" in rows:
+        out["transport"] = transport_rates(mech, synth, dev, stream, args, rank)
+    if "cn" in rows:
+        out["crank_nicolson"] = crank_nicolson_rates(synth, dev, stream, args, rank)
+    if rank == 0:
+        print(json.dumps({"rows_only": sorted(rows), **out}), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     from paper_2503_24286_gb300 import binding as B
@@ -817,10 +858,16 @@ def main():
     ap.add_argument("--no-transport", action="store_true")
     ap.add_argument("--pdep-points", type=int, default=2 ** 22)
     ap.add_argument("--no-pdep", action="store_true")
+    ap.add_argument("--only", default=None,
+                    help="profiling: run only these secondary rows (comma list of derivatives, learned, large, pdep, "
+                         "transport, cn) and print them; no headline")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    rc = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        rc = run_reference(args)
+    else:
+        rc = run_rows_only(args) if args.only else run_ours(args)
     dist = _dist()
     if dist is not None:
         dist.barrier()

@@ -70,10 +70,15 @@ typedef struct pyro_mech pyro_mech;
  *   exp=4|2|4call|2call (device exponential: 4 FP64-pipe operations (default)
  *                        or 2 with the second-order terms in FP32 pairs; inlined
  *                        at every use, or one called body)
+ *   warp_exp=2|4        (the exponential of the warp-per-state kernels: 2 FP64-pipe
+ *                        operations (default; their code is compact) or 4)
  *   variant=thread|warp (net production rates: one thread per state with
  *                        mechanism-specialised straight-line code (default),
- *                        or one warp per state, lanes splitting species and
- *                        reactions, driven by tables (no specialisation))
+ *                        or one warp per state (pyro_net_production_rates,
+ *                        pyro_jvp, pyro_vjp): the lanes split the species and
+ *                        the reactions, in chunks of 32 reactions emitted for
+ *                        the mechanism's reaction classes -- the faster form for
+ *                        large mechanisms such as 160 species / 1100 reactions)
  *   store=auto|shared|global  (where each thread keeps its state's species
  *                        arrays: shared memory, or -- automatic when they do
  *                        not fit, e.g. 160 species -- a library-owned global

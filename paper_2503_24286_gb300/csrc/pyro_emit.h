@@ -25,6 +25,8 @@ struct EmitOptions {
   // Crank-Nicolson unit: also emit the right-hand-side-only kernel of the chord iteration
   bool cn_residual = false;
   int exp_ops = 4;            // device exponential: 4 (default) or 2 FP64-pipe operations
+  int warp_exp_ops = 2;       // the same for the warp-per-state kernels (their code is compact, so
+                              // the 2-operation form does not outgrow the instruction cache)
   bool exp_call = false;      // one called body instead of inlining at every use
 };
 

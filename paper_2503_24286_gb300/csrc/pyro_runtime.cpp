@@ -183,6 +183,7 @@ struct Options {
   int store = 0;          // 0 auto, 1 shared memory, 2 global scratch (per-state species arrays)
   bool warp = false;      // net production rates: warp per state (table-driven) instead of thread per state
   int exp_ops = 4;        // exponential flavour (4 or 2 FP64 ops)
+  int warp_exp_ops = 2;   // the warp-per-state kernels' exponential (compact code: 2 FP64 ops by default)
   bool exp_call = false;  // exponential as a called function
   bool cn_chord = false;  // Crank-Nicolson: keep a factorisation for several iterations (chord) instead of full Newton
   int cn_refresh = 4;     // chord: re-assemble and re-factor every cn_refresh-th iteration
@@ -205,6 +206,11 @@ bool parse_options(const char* s, Options& o, std::string& err) {
     else if (k == "cache") o.cache = v != "0";
     else if (k == "checked") o.checked = v != "0";
     else if (k == "device") o.device = v != "0";
+    else if (k == "warp_exp") {
+      if (v == "2") o.warp_exp_ops = 2;
+      else if (v == "4") o.warp_exp_ops = 4;
+      else { err = "warp_exp must be 2 or 4"; return false; }
+    }
     else if (k == "exp") {
       if (v == "2") { o.exp_ops = 2; o.exp_call = false; }
       else if (v == "4") { o.exp_ops = 4; o.exp_call = false; }
@@ -657,6 +663,7 @@ int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) 
   eo.mixed_newton = h->opt.mixed;
   eo.deriv_block = h->opt.deriv_block;
   eo.exp_ops = h->opt.exp_ops;
+  eo.warp_exp_ops = h->opt.warp_exp_ops;
   eo.exp_call = h->opt.exp_call;
   {
     const int N = h->m.n_species();
