@@ -502,18 +502,18 @@ const double CS_H = 1e-30;   // complex-step size (no subtractive cancellation)
 
 // Chemical Jacobian J_jk = dS_j/dY_k of the source S_j = W_j omega_j (Eq. massfrac_ode,
 // Eq. chem_jacobian) at fixed rho and e: T follows Y through the inversion of
-// Eq. int_energy.  Complex step through that inversion: starting from the real
-// root T of e(T, Y) = e, Newton steps in complex arithmetic carry the derivative
-// dT/dY_k into the imaginary part (one step is exact to O(h^2); two are taken).
-// J is row-major [j][k], N x N.
+// Eq. int_energy, and differentiating e = sum_i Y_i e_i(T) at fixed e gives
+// dT/dY_k = -e_k(T)/c_v (Eq. cv).  One complex step per column moves Y_k by ih and
+// T by ih dT/dY_k together, so the imaginary part of omega carries
+// d omega/dY_k + d omega/dT dT/dY_k.  J is row-major [j][k], N x N.
 void source_jacobian_adiabatic(const OMech& m, double rho, double T, const double* Y, double* J) {
   const int N = m.N();
-  const double e = internal_energy(m, T, Y);
+  const double cv = cv_mass(m, T, Y);
   std::vector<cplx> y(N), w(N);
   for (int c = 0; c < N; ++c) {
     for (int k = 0; k < N; ++k) y[k] = cplx(Y[k], k == c ? CS_H : 0.0);
-    cplx Tc(T, 0.0);
-    for (int it = 0; it < 2; ++it) Tc -= (internal_energy<cplx>(m, Tc, y.data()) - e) / cv_mass<cplx>(m, Tc, y.data());
+    const double ec = (R_GAS * T * h_RT(m.sp[c], T) - R_GAS * T) / m.sp[c].W;   // e_c per unit mass
+    cplx Tc(T, CS_H * (-ec / cv));
     net_production_rates<cplx>(m, cplx(rho, 0.0), Tc, y.data(), w.data());
     for (int j = 0; j < N; ++j) J[j * N + c] = m.sp[j].W * w[j].imag() / CS_H;
   }
