@@ -35,6 +35,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 #include <set>
 #include <sstream>
 
@@ -2063,6 +2064,11 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_mlp(i64 n, co
 }  // namespace
 
 EmitResult emit_module(const Mechanism& m, const EmitOptions& opt) {
+  // the emitters keep per-emission state in file-scope variables (accumulator
+  // mode, folded sums, exponential flavour): one emission at a time, so that
+  // handles loaded from several host threads stay independent
+  static std::mutex emit_mu;
+  std::lock_guard<std::mutex> lock(emit_mu);
   EmitResult out;
   g_exp_ops = opt.exp_ops;
   Src s;

@@ -185,3 +185,32 @@ def test_null_and_negative_arguments_rejected(mech_files):
     assert L.pyro_temperature(m.handle, 4, None, None, None, 0, None, None, None) == B.PYRO_EINVAL
     # n == 0 is a no-op even without pointers
     assert L.pyro_net_production_rates(m.handle, 0, None, None, 0, None, None, None, None) == B.PYRO_OK
+
+
+def test_concurrent_loads_emit_the_same_sources(mech_files, tmp_path):
+    """Separate handles are independent: mechanisms loaded from several host
+    threads at once get exactly the sources a single load emits (the emitters'
+    per-emission settings -- e.g. the accumulators-in-memory mode of mechanisms
+    above 64 species -- must not leak between concurrent loads)."""
+    import threading
+    from paper_2503_24286_gb300 import synth
+    paths, _ = mech_files
+    big = synth.generate_mechanism("big70", ["C", "H", "O", "N"], 70, 60, 6, 4, 0, [], seed=11)
+    paths = {1: paths[1], 4: str(tmp_path / "big70.txt")}
+    synth.write_mechanism(big, paths[4])
+    ref = {i: B.Mechanism(paths[i], "device=0").source() for i in (1, 4)}
+    assert "Wp[" in ref[4] and "Wp[" not in ref[1]      # accumulators in memory only above 64 species
+    got, errs = [], []
+
+    def load(i):
+        try:
+            got.append((i, B.Mechanism(paths[i], "device=0").source()))
+        except Exception as e:          # pragma: no cover - reported below
+            errs.append(repr(e))
+    th = [threading.Thread(target=load, args=(i,)) for i in (1, 4, 1, 4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs
+    assert len(got) == 4 and all(src == ref[i] for i, src in got)
