@@ -11,7 +11,12 @@
 // templated on the scalar type so that the same definitions run in
 //   double                -- the oracle proper,
 //   long double           -- a rounding-error envelope for the oracle itself,
-//   std::complex<double>  -- complex-step derivatives (Jacobian, JVP, VJP).
+//   Dual (below)          -- forward-mode derivatives (Jacobian, JVP, VJP, gross
+//                            scales): value and first derivative carried together,
+//                            exact up to rounding, with no step size.  (A complex
+//                            step h is exact only to O(h^2 f'''/f'): where a
+//                            variable is far below h -- mass fractions of 1e-75 at
+//                            equilibrium states -- that term dominates.)
 //
 // Readings of passages that the paper leaves silent, ambiguous or garbled are
 // marked "reading (cN)"; each states the interpretation taken and why.
@@ -34,6 +39,14 @@
 #endif
 
 namespace {
+
+// math functions by unqualified name: the std overloads for double, long double and
+// std::complex, and (found by argument-dependent lookup) those of Dual
+using std::exp;
+using std::log;
+using std::log10;
+using std::pow;
+using std::sqrt;
 
 const double R_GAS = 8314.462618;   // J/(kmol K)
 const double P_ATM = 101325.0;      // Pa
@@ -211,12 +224,57 @@ bool parse_mech(const char* path, OMech& m) {
 }
 
 // ---------------------------------------------------------------------------
-// Scalar helpers (real part for comparisons, so complex steps pass through)
+// Scalar helpers (real part for comparisons, so derivative carriers pass through)
 // ---------------------------------------------------------------------------
 
 inline double re(double x) { return x; }
 inline long double re(long double x) { return x; }
 inline double re(const std::complex<double>& x) { return x.real(); }
+
+// ---------------------------------------------------------------------------
+// Dual numbers v + d eps with eps^2 = 0: every operation carries the value and its
+// derivative along one direction (the chain rule of each elementary function), so
+// a definition evaluated on Dual inputs with d = 1 in one variable returns that
+// partial derivative exactly up to rounding.
+// ---------------------------------------------------------------------------
+namespace dualnum {
+struct Dual {
+  double v = 0.0, d = 0.0;
+  Dual() {}
+  Dual(double x) : v(x) {}
+  Dual(double x, double dx) : v(x), d(dx) {}
+  Dual& operator+=(const Dual& b) { v += b.v; d += b.d; return *this; }
+  Dual& operator-=(const Dual& b) { v -= b.v; d -= b.d; return *this; }
+  Dual& operator*=(const Dual& b) { d = d * b.v + v * b.d; v *= b.v; return *this; }
+  Dual& operator/=(const Dual& b) { d = (d * b.v - v * b.d) / (b.v * b.v); v /= b.v; return *this; }
+};
+inline Dual operator+(Dual a, const Dual& b) { return a += b; }
+inline Dual operator-(Dual a, const Dual& b) { return a -= b; }
+inline Dual operator*(Dual a, const Dual& b) { return a *= b; }
+inline Dual operator/(Dual a, const Dual& b) { return a /= b; }
+inline Dual operator+(Dual a, double b) { a.v += b; return a; }
+inline Dual operator+(double a, Dual b) { b.v += a; return b; }
+inline Dual operator-(Dual a, double b) { a.v -= b; return a; }
+inline Dual operator-(double a, const Dual& b) { return Dual(a - b.v, -b.d); }
+inline Dual operator*(const Dual& a, double b) { return Dual(a.v * b, a.d * b); }
+inline Dual operator*(double a, const Dual& b) { return Dual(a * b.v, a * b.d); }
+inline Dual operator/(const Dual& a, double b) { return Dual(a.v / b, a.d / b); }
+inline Dual operator/(double a, const Dual& b) { return Dual(a / b.v, -a * b.d / (b.v * b.v)); }
+inline Dual operator-(const Dual& a) { return Dual(-a.v, -a.d); }
+inline Dual exp(const Dual& a) { const double e = std::exp(a.v); return Dual(e, a.d * e); }
+inline Dual log(const Dual& a) { return Dual(std::log(a.v), a.d / a.v); }
+inline Dual log10(const Dual& a) { return Dual(std::log10(a.v), a.d / (a.v * std::log(10.0))); }
+inline Dual sqrt(const Dual& a) { const double r = std::sqrt(a.v); return Dual(r, a.d / (2.0 * r)); }
+// x^p, constant p: d(x^p) = p x^(p-1) dx (x^0 = 1 with derivative 0)
+inline Dual pow(const Dual& a, double p) {
+  if (p == 0.0) return Dual(1.0, 0.0);
+  return Dual(std::pow(a.v, p), p * std::pow(a.v, p - 1.0) * a.d);
+}
+// x^y for x > 0: exp(y ln x)
+inline Dual pow(const Dual& a, const Dual& b) { return exp(b * log(a)); }
+}  // namespace dualnum
+using dualnum::Dual;
+inline double re(const Dual& x) { return x.v; }
 
 // ---------------------------------------------------------------------------
 // Thermodynamics: NASA-7 polynomials (Sec. A.1, Eq. nasa_poly, Eq. nasa_poly_c)
@@ -231,7 +289,7 @@ inline const double* nasa_coeffs(const OSpecies& s, double T) {
 template <class S> S cp_R(const OSpecies& s, S T) {
   const double* a = nasa_coeffs(s, re(T));
   S v = 0;
-  for (int m = 1; m <= 5; ++m) v += a[m - 1] * std::pow(T, (double)(m - 1));
+  for (int m = 1; m <= 5; ++m) v += a[m - 1] * pow(T, (double)(m - 1));
   return v;
 }
 
@@ -239,15 +297,15 @@ template <class S> S cp_R(const OSpecies& s, S T) {
 template <class S> S h_RT(const OSpecies& s, S T) {
   const double* a = nasa_coeffs(s, re(T));
   S v = a[5] / T;
-  for (int m = 1; m <= 5; ++m) v += a[m - 1] * std::pow(T, (double)(m - 1)) / (double)m;
+  for (int m = 1; m <= 5; ++m) v += a[m - 1] * pow(T, (double)(m - 1)) / (double)m;
   return v;
 }
 
 // s/R = a1 ln T + sum_{m=2}^{5} a_m T^{m-1}/(m-1) + a7    (Eq. nasa_poly, second line; reading (c2))
 template <class S> S s_R(const OSpecies& s, S T) {
   const double* a = nasa_coeffs(s, re(T));
-  S v = a[0] * std::log(T) + a[6];
-  for (int m = 2; m <= 5; ++m) v += a[m - 1] * std::pow(T, (double)(m - 1)) / (double)(m - 1);
+  S v = a[0] * log(T) + a[6];
+  for (int m = 2; m <= 5; ++m) v += a[m - 1] * pow(T, (double)(m - 1)) / (double)(m - 1);
   return v;
 }
 
@@ -352,7 +410,7 @@ double temperature_bisect(const OMech& m, double e, const double* Y, double lo, 
 
 // k = A T^b exp(-theta/T)      (Eq. rate_coeff)
 template <class S> S arrhenius(double A, double b, double theta, S T) {
-  return A * std::pow(T, b) * std::exp(-theta / T);
+  return A * pow(T, b) * exp(-theta / T);
 }
 
 // [M]_j = sum_k eps_kj C_k, eps default 1      (reading (c9))
@@ -371,23 +429,23 @@ template <class S> S third_body(const OReaction& r, const S* C, int N) {
 template <class S> S falloff_factor(const OReaction& r, S T, S Pr) {
   if (r.n_sri >= 3) {
     // SRI form (reading (p1)): F = d [a exp(-b/T) + exp(-T/c)]^X T^e,  X = 1/(1 + (log10 Pr)^2)
-    S lPr = std::log10(Pr);
+    S lPr = log10(Pr);
     S X = 1.0 / (1.0 + lPr * lPr);
-    S base = r.sri[0] * std::exp(-r.sri[1] / T) + std::exp(-T / r.sri[2]);
-    return r.sri[3] * std::pow(base, X) * std::pow(T, r.sri[4]);
+    S base = r.sri[0] * exp(-r.sri[1] / T) + exp(-T / r.sri[2]);
+    return r.sri[3] * pow(base, X) * pow(T, r.sri[4]);
   }
   if (r.n_troe < 3) return S(1.0);
   double a = r.troe[0], T3 = r.troe[1], T1 = r.troe[2];
-  S Fcent = (1.0 - a) * std::exp(-T / T3) + a * std::exp(-T / T1);
-  if (r.n_troe >= 4) Fcent += std::exp(-r.troe[3] / T);
-  S lFc = std::log10(Fcent);
+  S Fcent = (1.0 - a) * exp(-T / T3) + a * exp(-T / T1);
+  if (r.n_troe >= 4) Fcent += exp(-r.troe[3] / T);
+  S lFc = log10(Fcent);
   S c = -0.4 - 0.67 * lFc;
   S n = 0.75 - 1.27 * lFc;
   const double d = 0.14;
-  S lPr = std::log10(Pr);
+  S lPr = log10(Pr);
   S f = (lPr + c) / (n - d * (lPr + c));
   S lF = lFc / (1.0 + f * f);
-  return std::pow(S(10.0), lF);
+  return pow(S(10.0), lF);
 }
 
 // forward rate coefficient k_f,j (includes [M] for third-body reactions, reading (c14))
@@ -405,10 +463,10 @@ template <class S> S plog_rate(const OReaction& r, S T, const S* C, int N) {
   if (re(p) >= nd[n - 1][0]) return arrhenius(nd[n - 1][1], nd[n - 1][2], nd[n - 1][3], T);
   int i = 0;
   while (!(re(p) < nd[i + 1][0])) ++i;
-  S lk0 = std::log(arrhenius(nd[i][1], nd[i][2], nd[i][3], T));
-  S lk1 = std::log(arrhenius(nd[i + 1][1], nd[i + 1][2], nd[i + 1][3], T));
-  S w = (std::log(p) - std::log(nd[i][0])) / (std::log(nd[i + 1][0]) - std::log(nd[i][0]));
-  return std::exp(lk0 + (lk1 - lk0) * w);
+  S lk0 = log(arrhenius(nd[i][1], nd[i][2], nd[i][3], T));
+  S lk1 = log(arrhenius(nd[i + 1][1], nd[i + 1][2], nd[i + 1][3], T));
+  S w = (log(p) - log(nd[i][0])) / (log(nd[i + 1][0]) - log(nd[i][0]));
+  return exp(lk0 + (lk1 - lk0) * w);
 }
 
 template <class S> S forward_rate_coefficient(const OMech& m, const OReaction& r, S T, const S* C) {
@@ -421,8 +479,8 @@ template <class S> S forward_rate_coefficient(const OMech& m, const OReaction& r
   S k0 = arrhenius(r.A0, r.b0, r.theta0, T);
   S Pr = k0 * third_body(r, C, N) / kinf;
   if (re(Pr) < 1e-300) Pr = Pr - re(Pr) + 1e-300;   // guard log10(0) (reading (c8))
-  // Pr/(1+Pr) written as 1/(1 + 1/Pr): the same value, but its complex-step
-  // derivative does not subtract two nearly equal numbers when Pr >> 1
+  // Pr/(1+Pr) written as 1/(1 + 1/Pr): the same value, but its derivative does
+  // not subtract two nearly equal numbers when Pr >> 1
   return kinf / (1.0 + 1.0 / Pr) * falloff_factor(r, T, Pr);
 }
 
@@ -432,7 +490,7 @@ template <class S> S equilibrium_constant(const OMech& m, const OReaction& r, S 
   S dg = 0;
   for (auto& p : r.prod) { dnu += p.second; dg += (double)p.second * g_RT(m.sp[p.first], T); }
   for (auto& p : r.reac) { dnu -= p.second; dg -= (double)p.second * g_RT(m.sp[p.first], T); }
-  return std::pow(P_ATM / (R_GAS * T), dnu) * std::exp(-dg);
+  return pow(P_ATM / (R_GAS * T), dnu) * exp(-dg);
 }
 
 template <class S> S conc_product(const std::vector<std::pair<int, int>>& side, const S* C) {
@@ -498,24 +556,24 @@ template <class S> S temperature_rate(const OMech& m, S rho, S T, const S* Y, co
 }
 
 typedef std::complex<double> cplx;
-const double CS_H = 1e-30;   // complex-step size (no subtractive cancellation)
+const double CS_H = 1e-30;   // complex-step size (the learned guess's loss derivative only)
 
 // Chemical Jacobian J_jk = dS_j/dY_k of the source S_j = W_j omega_j (Eq. massfrac_ode,
 // Eq. chem_jacobian) at fixed rho and e: T follows Y through the inversion of
 // Eq. int_energy, and differentiating e = sum_i Y_i e_i(T) at fixed e gives
-// dT/dY_k = -e_k(T)/c_v (Eq. cv).  One complex step per column moves Y_k by ih and
-// T by ih dT/dY_k together, so the imaginary part of omega carries
-// d omega/dY_k + d omega/dT dT/dY_k.  J is row-major [j][k], N x N.
+// dT/dY_k = -e_k(T)/c_v (Eq. cv).  One dual evaluation per column moves Y_k with
+// derivative 1 and T with derivative dT/dY_k together, so the derivative part of
+// omega carries d omega/dY_k + d omega/dT dT/dY_k.  J is row-major [j][k], N x N.
 void source_jacobian_adiabatic(const OMech& m, double rho, double T, const double* Y, double* J) {
   const int N = m.N();
   const double cv = cv_mass(m, T, Y);
-  std::vector<cplx> y(N), w(N);
+  std::vector<Dual> y(N), w(N);
   for (int c = 0; c < N; ++c) {
-    for (int k = 0; k < N; ++k) y[k] = cplx(Y[k], k == c ? CS_H : 0.0);
+    for (int k = 0; k < N; ++k) y[k] = Dual(Y[k], k == c ? 1.0 : 0.0);
     const double ec = (R_GAS * T * h_RT(m.sp[c], T) - R_GAS * T) / m.sp[c].W;   // e_c per unit mass
-    cplx Tc(T, CS_H * (-ec / cv));
-    net_production_rates<cplx>(m, cplx(rho, 0.0), Tc, y.data(), w.data());
-    for (int j = 0; j < N; ++j) J[j * N + c] = m.sp[j].W * w[j].imag() / CS_H;
+    Dual Tc(T, -ec / cv);
+    net_production_rates<Dual>(m, Dual(rho), Tc, y.data(), w.data());
+    for (int j = 0; j < N; ++j) J[j * N + c] = m.sp[j].W * w[j].d;
   }
 }
 
@@ -599,23 +657,23 @@ int cn_step(const OMech& m, double rho, double dt, const double* Ym, double Tm, 
 // ---------------------------------------------------------------------------
 
 template <class S> S poly_logT(const std::vector<double>& c, S T) {
-  S lt = std::log(T), v = 0;
-  for (int m = 0; m <= 4; ++m) v += c[m] * std::pow(lt, (double)m);
+  S lt = log(T), v = 0;
+  for (int m = 0; m <= 4; ++m) v += c[m] * pow(lt, (double)m);
   return v;
 }
 
 // mu_i = sqrt(T) [sum_m b_im (log T)^m]^2
 template <class S> S species_viscosity(const OMech& m, int k, S T) {
   S b = poly_logT(m.visc[k], T);
-  return std::sqrt(T) * b * b;
+  return sqrt(T) * b * b;
 }
 // kappa_i = sqrt(T) sum_m c_im (log T)^m      (Eq. species_cond)
 template <class S> S species_conductivity(const OMech& m, int k, S T) {
-  return std::sqrt(T) * poly_logT(m.cond[k], T);
+  return sqrt(T) * poly_logT(m.cond[k], T);
 }
 // D_ij = sqrt(T) sum_m a_ijm (log T)^m
 template <class S> S binary_diffusivity(const OMech& m, int k, int j, S T) {
-  return std::sqrt(T) * poly_logT(m.bdiff[k][j], T);
+  return sqrt(T) * poly_logT(m.bdiff[k][j], T);
 }
 
 // mole fractions X_k = W Y_k / W_k with W = (sum_k Y_k/W_k)^-1 (Eq. eos)
@@ -630,8 +688,8 @@ template <class S> S mole_fractions(const OMech& m, const S* Y, S* X) {
 // Wilke's Phi_kj = [1 + sqrt((mu_k/mu_j) sqrt(W_j/W_k))]^2 / sqrt(8 (1 + W_k/W_j))
 template <class S> S wilke_phi(const OMech& m, int k, int j, S mu_k, S mu_j) {
   double Wk = m.sp[k].W, Wj = m.sp[j].W;
-  S t = 1.0 + std::sqrt((mu_k / mu_j) * std::sqrt(Wj / Wk));
-  return t * t / std::sqrt(8.0 * (1.0 + Wk / Wj));
+  S t = 1.0 + sqrt((mu_k / mu_j) * sqrt(Wj / Wk));
+  return t * t / sqrt(8.0 * (1.0 + Wk / Wj));
 }
 
 // mu = sum_k X_k mu_k / sum_j Phi_kj X_j      (Eq. mixavg_viscosity)
@@ -693,7 +751,7 @@ double round_bf16(double x) {
   return f;
 }
 
-template <class S> S silu(S x) { return x / (1.0 + std::exp(-x)); }
+template <class S> S silu(S x) { return x / (1.0 + exp(-x)); }
 template <class S> S rbf(S x) { return x - re(x) + round_bf16(re(x)); }   // straight-through rounding
 
 
@@ -768,13 +826,13 @@ void orc_species_thermo(void* h, int k, double T, double* out) {
   out[2] = s_R(m->sp[k], T);  out[3] = g_RT(m->sp[k], T);
 }
 
-// complex-step temperature derivatives: out[0] = d(h/R)/dT, out[1] = d(s/R)/dT, out[2] = d(cp/R)/dT
+// temperature derivatives (dual numbers): out[0] = d(h/R)/dT, out[1] = d(s/R)/dT, out[2] = d(cp/R)/dT
 void orc_species_thermo_dT(void* h, int k, double T, double* out) {
   OMech* m = (OMech*)h;
-  cplx Tc(T, CS_H);
-  out[0] = (Tc * h_RT(m->sp[k], Tc)).imag() / CS_H;
-  out[1] = s_R(m->sp[k], Tc).imag() / CS_H;
-  out[2] = cp_R(m->sp[k], Tc).imag() / CS_H;
+  Dual Tc(T, 1.0);
+  out[0] = (Tc * h_RT(m->sp[k], Tc)).d;
+  out[1] = s_R(m->sp[k], Tc).d;
+  out[2] = cp_R(m->sp[k], Tc).d;
 }
 
 void orc_density(void* h, int64_t n, const double* p, const double* T, const double* Y, double* rho) {
@@ -927,63 +985,61 @@ void orc_temperature_rate(void* h, int64_t n, const double* rho, const double* T
   }
 }
 
-// Dense Jacobian d(Tdot, omega)/d(T, Y) at fixed rho by complex step, reading (c13).
+// Dense Jacobian d(Tdot, omega)/d(T, Y) at fixed rho, one dual evaluation per column,
+// reading (c13).
 // J[(r*(N+1) + c)*n + p]; row 0 = Tdot, rows 1..N = omega; column 0 = T, columns 1..N = Y.
 void orc_jacobian(void* h, int64_t n, const double* rho, const double* T, const double* Y, double* J) {
   OMech* m = (OMech*)h; int N = m->N(); int NP = N + 1;
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t i = 0; i < n; ++i) {
-    std::vector<cplx> y(N), w(N);
+    std::vector<Dual> y(N), w(N);
     for (int c = 0; c < NP; ++c) {
-      cplx Tc(T[i], c == 0 ? CS_H : 0.0);
-      for (int k = 0; k < N; ++k) y[k] = cplx(Y[k * n + i], (c == k + 1) ? CS_H : 0.0);
-      cplx rc(rho[i], 0.0);
-      net_production_rates<cplx>(*m, rc, Tc, y.data(), w.data());
-      cplx td = temperature_rate<cplx>(*m, rc, Tc, y.data(), w.data());
-      J[(0 * NP + c) * n + i] = td.imag() / CS_H;
-      for (int k = 0; k < N; ++k) J[((k + 1) * NP + c) * n + i] = w[k].imag() / CS_H;
+      Dual Tc(T[i], c == 0 ? 1.0 : 0.0);
+      for (int k = 0; k < N; ++k) y[k] = Dual(Y[k * n + i], (c == k + 1) ? 1.0 : 0.0);
+      Dual rc(rho[i]);
+      net_production_rates<Dual>(*m, rc, Tc, y.data(), w.data());
+      Dual td = temperature_rate<Dual>(*m, rc, Tc, y.data(), w.data());
+      J[(0 * NP + c) * n + i] = td.d;
+      for (int k = 0; k < N; ++k) J[((k + 1) * NP + c) * n + i] = w[k].d;
     }
   }
 }
 
 // JVP of omega(rho, T, Y) along v = (drho, dT, dY): domega = sum_c (d omega/d x_c) v_c, [N][n],
-// the columns by complex step one variable at a time.  (A single complex step along
-// v would also carry products of the perturbations of different variables into the
-// imaginary part wherever h |v_c| is not small against |x_c|, e.g. for mass
-// fractions far below the step.)
+// the columns by dual evaluations one variable at a time.
 void orc_jvp(void* h, int64_t n, const double* rho, const double* T, const double* Y,
              const double* drho, const double* dT, const double* dY, double* domega) {
   OMech* m = (OMech*)h; int N = m->N();
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t i = 0; i < n; ++i) {
-    std::vector<cplx> y(N), w(N);
+    std::vector<Dual> y(N), w(N);
     std::vector<double> acc(N, 0.0);
     for (int c = 0; c < N + 2; ++c) {
       const double vc = c == 0 ? drho[i] : c == 1 ? dT[i] : dY[(c - 2) * n + i];
       if (vc == 0.0) continue;
-      cplx rc(rho[i], c == 0 ? CS_H : 0.0), Tc(T[i], c == 1 ? CS_H : 0.0);
-      for (int k = 0; k < N; ++k) y[k] = cplx(Y[k * n + i], (c == k + 2) ? CS_H : 0.0);
-      net_production_rates<cplx>(*m, rc, Tc, y.data(), w.data());
-      for (int k = 0; k < N; ++k) acc[k] += (w[k].imag() / CS_H) * vc;
+      Dual rc(rho[i], c == 0 ? 1.0 : 0.0), Tc(T[i], c == 1 ? 1.0 : 0.0);
+      for (int k = 0; k < N; ++k) y[k] = Dual(Y[k * n + i], (c == k + 2) ? 1.0 : 0.0);
+      net_production_rates<Dual>(*m, rc, Tc, y.data(), w.data());
+      for (int k = 0; k < N; ++k) acc[k] += w[k].d * vc;
     }
     for (int k = 0; k < N; ++k) domega[k * n + i] = acc[k];
   }
 }
 
 // VJP of omega(rho, T, Y): (rho_bar, T_bar, Y_bar) = J^T omega_bar with J = d omega/d(rho, T, Y)
-// formed column by column (complex step).
+// formed column by column (dual numbers).
 void orc_vjp(void* h, int64_t n, const double* rho, const double* T, const double* Y,
              const double* wbar, double* rho_bar, double* T_bar, double* Y_bar) {
   OMech* m = (OMech*)h; int N = m->N();
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t i = 0; i < n; ++i) {
-    std::vector<cplx> y(N), w(N);
+    std::vector<Dual> y(N), w(N);
     for (int c = 0; c < N + 2; ++c) {
-      cplx rc(rho[i], c == 0 ? CS_H : 0.0), Tc(T[i], c == 1 ? CS_H : 0.0);
-      for (int k = 0; k < N; ++k) y[k] = cplx(Y[k * n + i], (c == k + 2) ? CS_H : 0.0);
-      net_production_rates<cplx>(*m, rc, Tc, y.data(), w.data());
+      Dual rc(rho[i], c == 0 ? 1.0 : 0.0), Tc(T[i], c == 1 ? 1.0 : 0.0);
+      for (int k = 0; k < N; ++k) y[k] = Dual(Y[k * n + i], (c == k + 2) ? 1.0 : 0.0);
+      net_production_rates<Dual>(*m, rc, Tc, y.data(), w.data());
       double acc = 0;
-      for (int k = 0; k < N; ++k) acc += wbar[k * n + i] * (w[k].imag() / CS_H);
+      for (int k = 0; k < N; ++k) acc += wbar[k * n + i] * w[k].d;
       if (c == 0) rho_bar[i] = acc;
       else if (c == 1) T_bar[i] = acc;
       else Y_bar[(c - 2) * n + i] = acc;
@@ -996,7 +1052,7 @@ void orc_vjp(void* h, int64_t n, const double* rho, const double* T, const doubl
 // the terms that cancel in it, so for omega_k and a variable x_c
 //   GJ_kc = sum_j |nu_kj| (|d Rf_j/d x_c| + |d Rr_j/d x_c|),
 // the forward and reverse rates of progress (Eq. reaction_rates) differentiated
-// separately by complex step.  For the temperature rate of the adiabatic
+// separately (dual numbers).  For the temperature rate of the adiabatic
 // isochoric reactor, Tdot = -sum_k ehat_k omega_k / (rho c_v) with
 // ehat_k = h_k - R T (reading (c13)), the same magnitudes are carried through
 // its product and quotient rules:
@@ -1010,7 +1066,7 @@ void orc_jacobian_gross(void* h, int64_t n, const double* rho, const double* T, 
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t i = 0; i < n; ++i) {
     std::vector<double> y(N), Rf(M), Rr(M), G(N, 0.0), eh(N), deh(N);
-    std::vector<cplx> yc(N), Rfc(M), Rrc(M);
+    std::vector<Dual> yc(N), Rfc(M), Rrc(M);
     for (int k = 0; k < N; ++k) y[k] = Y[k * n + i];
     rates_of_progress(*m, rho[i], T[i], y.data(), Rf.data(), Rr.data());
     std::vector<std::map<int, int>> nu(M);
@@ -1023,20 +1079,20 @@ void orc_jacobian_gross(void* h, int64_t n, const double* rho, const double* T, 
     double Tg = 0.0;
     for (int k = 0; k < N; ++k) {
       eh[k] = R_GAS * T[i] * h_RT(m->sp[k], T[i]) - R_GAS * T[i];
-      cplx Tc(T[i], CS_H);
-      deh[k] = (R_GAS * Tc * h_RT(m->sp[k], Tc) - R_GAS * Tc).imag() / CS_H;   // cp_k - R
+      Dual Tc(T[i], 1.0);
+      deh[k] = (R_GAS * Tc * h_RT(m->sp[k], Tc) - R_GAS * Tc).d;   // cp_k - R
       Tg += std::fabs(eh[k]) * G[k] / rcv;
     }
     for (int c = 0; c < NC; ++c) {
-      cplx rc(rho[i], c == 0 ? CS_H : 0.0), Tc(T[i], c == 1 ? CS_H : 0.0);
-      for (int k = 0; k < N; ++k) yc[k] = cplx(y[k], (c == k + 2) ? CS_H : 0.0);
-      rates_of_progress<cplx>(*m, rc, Tc, yc.data(), Rfc.data(), Rrc.data());
+      Dual rc(rho[i], c == 0 ? 1.0 : 0.0), Tc(T[i], c == 1 ? 1.0 : 0.0);
+      for (int k = 0; k < N; ++k) yc[k] = Dual(y[k], (c == k + 2) ? 1.0 : 0.0);
+      rates_of_progress<Dual>(*m, rc, Tc, yc.data(), Rfc.data(), Rrc.data());
       std::vector<double> col(N, 0.0);
       for (int j = 0; j < M; ++j) {
-        const double df = std::fabs(Rfc[j].imag() / CS_H), dr = std::fabs(Rrc[j].imag() / CS_H);
+        const double df = std::fabs(Rfc[j].d), dr = std::fabs(Rrc[j].d);
         for (auto& q : nu[j]) col[q.first] += std::abs(q.second) * (df + dr);
       }
-      const double drcv = std::fabs((rc * cv_mass<cplx>(*m, Tc, yc.data())).imag() / CS_H);
+      const double drcv = std::fabs((rc * cv_mass<Dual>(*m, Tc, yc.data())).d);
       double g0 = Tg * drcv / rcv;
       for (int k = 0; k < N; ++k) {
         g0 += ((c == 1 ? std::fabs(deh[k]) * G[k] : 0.0) + std::fabs(eh[k]) * col[k]) / rcv;
@@ -1191,7 +1247,7 @@ double orc_mlp_loss_grad(int D, int H, const double* P, int64_t n, const double*
     gb3[0] += dy;
     for (int i = 0; i < H; ++i) {
       gw3[i] += dy * a2[i];
-      double s = 1.0 / (1.0 + std::exp(-z2[i]));
+      double s = 1.0 / (1.0 + exp(-z2[i]));
       d2[i] = dy * w3[i] * (s * (1.0 + z2[i] * (1.0 - s)));   // d silu/dz
     }
     for (int o = 0; o < H; ++o) {
@@ -1201,7 +1257,7 @@ double orc_mlp_loss_grad(int D, int H, const double* P, int64_t n, const double*
     for (int i = 0; i < H; ++i) {
       double acc = 0;
       for (int o = 0; o < H; ++o) acc += d2[o] * W2[o * H + i];
-      double s = 1.0 / (1.0 + std::exp(-z1[i]));
+      double s = 1.0 / (1.0 + exp(-z1[i]));
       d1[i] = acc * (s * (1.0 + z1[i] * (1.0 - s)));
     }
     for (int o = 0; o < H; ++o) {

@@ -3,7 +3,7 @@
 The derivative scale GJ (reading c15 carried over to derivatives) is the sum,
 over the reactions of a species, of the magnitudes of the forward and reverse
 rates' derivatives.  It is checked three ways, none of which reuses its code:
-it bounds every entry of the complex-step Jacobian (triangle inequality), it
+it bounds every entry of the oracle's Jacobian (triangle inequality), it
 equals the entry's magnitude where only one rate of one reaction moves with the
 variable (a one-reaction mechanism), and it agrees with the same sums assembled
 here from central differences of the forward and reverse rates of progress.
@@ -180,8 +180,8 @@ def test_falloff_blend_derivative_at_extreme_pr(tmp_path, lnPr):
     """Lindemann falloff H + O2 (+M) <=> OH + O with an inert N2 that enters only
     [M]: with k = k_inf Pr/(1+Pr), Pr = k0 [M]/k_inf, the derivative of the rate
     of progress R = k P (P = C_H C_O2 - C_OH C_O/K_c) along Y_N2 is
-    dR/dY_N2 = R/([M] (1 + Pr)) * rho/W_N2 in closed form.  The oracle's complex
-    step must reproduce it from Pr = 1e-20 to Pr = 1e30 (where 1 - Pr/(1+Pr)
+    dR/dY_N2 = R/([M] (1 + Pr)) * rho/W_N2 in closed form.  The oracle's
+    derivatives must reproduce it from Pr = 1e-20 to Pr = 1e30 (where 1 - Pr/(1+Pr)
     cancels to nothing in floating point)."""
     A, b, th, A0, b0, th0 = 1e12, 0.3, 4000.0, 1e16, -1.0, 1000.0
     m = handmech.abcd_mechanism(kind="falloff", A=A, b=b, theta=th, low=(A0, b0, th0))
@@ -207,9 +207,39 @@ def test_falloff_blend_derivative_at_extreme_pr(tmp_path, lnPr):
     assert np.all(dw[4] == 0.0)
 
 
+@pytest.mark.parametrize("Y_O", [1e-75, 1e-100, 1e-200])
+def test_jacobian_entry_closed_form_at_tiny_mass_fractions(tmp_path, Y_O):
+    """Recombination 2 O (+M) <=> O2, Lindemann falloff, with O and O2 both far
+    below any finite-difference or complex step (as at equilibrium states, where
+    mass fractions reach 1e-200).  At fixed (rho, T):
+      d omega_O2/d Y_O = k 2 C_O rho/W_O + dk/d[M] rho/W_O (C_O^2 - C_O2/K_c),
+      dk/d[M] = k0/(1 + Pr)^2  (k = k_inf Pr/(1+Pr), Pr = k0 [M]/k_inf),
+    and d omega_O/d Y_O = -2 of it.  Evaluated here from the Arrhenius constants;
+    the oracle's Jacobian must reproduce it to rounding.  A complex step of 1e-30
+    fails this by many orders of magnitude (its h^2 term dominates)."""
+    A, b, th, A0, b0, th0 = 1e10, 0.5, 5000.0, 1e16, -1.0, 1000.0
+    m = handmech.abcd_mechanism(kind="falloff", A=A, b=b, theta=th, low=(A0, b0, th0))
+    m.reactions[0].reactants = [(3, 2)]
+    m.reactions[0].products = [(1, 1)]
+    o = O.Oracle(handmech.write(m, str(tmp_path), "two_o.txt"))
+    T, rho = np.array([1500.0, 900.0]), np.array([0.8, 3.0])
+    Y = np.array([[0.3, 0.2], [Y_O ** 2, Y_O * 1e-30], [0.7, 0.8], [Y_O, Y_O]])
+    C = rho * Y / o.W[:, None]
+    M = C.sum(axis=0)
+    kinf = A * T ** b * np.exp(-th / T)
+    k0 = A0 * T ** b0 * np.exp(-th0 / T)
+    Pr = k0 * M / kinf
+    k = kinf * Pr / (1.0 + Pr)
+    Kc = o.reaction_data(rho, T, Y)["Kc"][0]
+    expect = (k * 2.0 * C[3] + k0 / (1.0 + Pr) ** 2 * (C[3] ** 2 - C[1] / Kc)) * rho / o.W[3]
+    J = o.jacobian(rho, T, Y).reshape(5, 5, 2)       # rows (Tdot, omega), columns (T, Y)
+    assert np.allclose(J[2, 4], expect, rtol=1e-13, atol=0)
+    assert np.allclose(J[4, 4], -2.0 * expect, rtol=1e-13, atol=0)
+
+
 def test_jvp_is_linear_at_states_with_tiny_mass_fractions(orc):
     """The JVP is the linear map J v: at states whose mass fractions reach 1e-200
-    (far below the complex step) it must stay additive in v and reproduce the
+    it must stay additive in v and reproduce the
     Jacobian's columns along unit directions."""
     o, _ = orc[1]
     st, rho = _states(1, 3, o, seed=35)
