@@ -140,7 +140,7 @@ class Oracle:
         return out
 
     def species_thermo_dT(self, k: int, T: float) -> np.ndarray:
-        """complex-step [d(h/R)/dT, d(s/R)/dT, d(cp/R)/dT]."""
+        """[d(h/R)/dT, d(s/R)/dT, d(cp/R)/dT] (dual numbers)."""
         out = np.zeros(3)
         lib().orc_species_thermo_dT(self._h, k, float(T), _d(out))
         return out

@@ -13,7 +13,9 @@
 //   long double           -- a rounding-error envelope for the oracle itself,
 //   Dual (below)          -- forward-mode derivatives (Jacobian, JVP, VJP, gross
 //                            scales): value and first derivative carried together,
-//                            exact up to rounding, with no step size.  (A complex
+//                            exact up to rounding, with no step size -- automatic
+//                            differentiation through a scalar type with redefined
+//                            operations, as the paper obtains Eq. rate_gradient.  (A complex
 //                            step h is exact only to O(h^2 f'''/f'): where a
 //                            variable is far below h -- mass fractions of 1e-75 at
 //                            equilibrium states -- that term dominates.)

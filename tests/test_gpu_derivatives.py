@@ -1,5 +1,5 @@
 """GPU derivative kernels (JVP, VJP, dense Jacobian) against the CPU oracle's
-complex-step derivatives, against central finite differences, and against each
+dual-number (forward-mode) derivatives, against central finite differences, and against each
 other (u.(J v) = (J^T u).v).  Also the torch.autograd.Function wrapper.
 
 Tolerance: each entry is compared element by element at 1e-11 of its own
@@ -206,17 +206,19 @@ def test_derivatives_full_size_sampled(mechs, dev):
     assert np.all(np.abs(Yb[:, ii].cpu().numpy() - oYb) <= TOL * scale[2:] + 1e-300)
 
 
-@pytest.mark.parametrize("idx", [0, 1, 7])
-def test_warp_per_state_jvp_vjp_match_oracle(mech_files, dev, idx):
+@pytest.mark.parametrize("idx", [0, 1, 7, "7-mixed"])
+def test_warp_per_state_jvp_vjp_match_oracle(mech_files, mixed_reversibility_mech, dev, idx):
     """The warp-per-state JVP and VJP kernels (variant=warp: lanes split the
     reactions, species adjoints gathered per species) against the oracle, every
-    entry within 1e-11 of its gross scale, over several blocks with a ragged tail;
-    and against the thread-per-state kernels on the same inputs."""
+    entry within 1e-11 of its gross scale, over several blocks with a ragged tail
+    (7-mixed: every third reaction irreversible)."""
     from paper_2503_24286_gb300 import binding as B
     paths, _ = mech_files
-    mw = B.Mechanism(paths[idx], "variant=warp")
+    path = mixed_reversibility_mech if idx == "7-mixed" else paths[idx]
+    idx = 7 if idx == "7-mixed" else idx
+    mw = B.Mechanism(path, "variant=warp")
     assert mw.stat("deriv_warp_per_state") == 1
-    orc = O.Oracle(paths[idx])
+    orc = O.Oracle(path)
     n = 203
     st, rho = _state(idx, n, orc, seed=7)
     rng = np.random.default_rng(13)

@@ -83,7 +83,7 @@ def test_large_jvp_vjp_parity(large, dev):
 
 def test_large_jacobian_matches_oracle(large, dev):
     """Dense d(Tdot, omega)/d(T, Y), 161 x 161 per state, rows from tables, species
-    arrays in the global scratch: against the oracle's complex-step Jacobian, each
+    arrays in the global scratch: against the oracle's dual-number Jacobian, each
     entry within 1e-11 of its gross scale."""
     m, orc = large
     assert m.stat("jacobian_rows_from_tables") == 1 and m.stat("deriv_store_global") == 1
@@ -228,3 +228,32 @@ def test_large_warp_jvp_vjp_parity(large, dev, mech_files):
     jw, jt = mw.jvp(r, T0, Y, *v), m.jvp(r, T0, Y, *v)
     sc = jt.abs().amax(dim=0, keepdim=True) + 1e-300
     assert torch.isfinite(jw).all().item() and ((jw - jt).abs() <= 1e-9 * sc).all().item()
+
+
+def test_large_block_per_state_jacobians(large, dev, mech_files):
+    """The dense Jacobians with one block of 8 warps per state (variant=warp: the
+    per-reaction partials in shared memory, rows written once from balanced
+    gathers): d(Tdot, omega)/d(T, Y) and dS/dY at fixed (rho, e) against the
+    oracle entry by entry; on 600 states (more than one resident grid) against
+    the thread-per-state kernels."""
+    from paper_2503_24286_gb300 import binding as B
+    m, orc = large
+    mw = B.Mechanism(mech_files[0][4], "variant=warp")
+    assert mw.stat("jacobian_cta") == 1 and mw.stat("wjac_row_groups") >= 2
+    N, NP, n = 160, 161, 6
+    st = synth.config_states(4, n=n, offset_seed=53)
+    rho = orc.density(st.p, st.T, st.Y)
+    r, T, Y = _t(rho, dev), _t(st.T, dev), _t(st.Y, dev)
+    J = mw.jacobian(r, T, Y).cpu().numpy().reshape(NP, NP, n)
+    assert np.all(np.abs(J - orc.jacobian(rho, st.T, st.Y).reshape(NP, NP, n)) <=
+                  TOL_D * orc.jacobian_gross(rho, st.T, st.Y)[:, 1:] + 1e-300)
+    Ja = mw.jacobian_adiabatic(r, T, Y).cpu().numpy().reshape(N, N, n)
+    assert np.all(np.abs(Ja - orc.jacobian_adiabatic(rho, st.T, st.Y).reshape(N, N, n)) <=
+                  TOL_D * orc.jacobian_adiabatic_gross(rho, st.T, st.Y).reshape(N, N, n) + 1e-300)
+    n = 600
+    cfg = synth.CONFIGS[4]
+    T0, p, Y0 = synth.generate_states_torch(160, n, cfg["T"], cfg["p_atm"], 97, dev)
+    r0 = m.density(p, T0, Y0)
+    Jw, Jt = mw.jacobian(r0, T0, Y0).reshape(NP, NP, n), m.jacobian(r0, T0, Y0).reshape(NP, NP, n)
+    sc = Jt.abs().amax(dim=1, keepdim=True) + 1e-300
+    assert torch.isfinite(Jw).all().item() and ((Jw - Jt).abs() <= 1e-9 * sc).all().item()

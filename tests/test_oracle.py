@@ -2,7 +2,7 @@
 
 Nothing here compares the oracle with itself: each test checks a closed form,
 an identity, a conservation law, a limit, a printed worked example, an
-independent algorithm (bisection, complex step vs finite differences), or the
+independent algorithm (bisection, dual-number derivatives vs finite differences), or the
 data-preparation code that produced the mechanism (NASA anchor values).
 """
 import math
@@ -298,7 +298,7 @@ def _fd_jacobian(o, rho, T, Y, h_rel=1e-7):
 
 
 @pytest.mark.parametrize("idx", [0, 1])
-def test_jacobian_complex_step_vs_central_fd(orc, idx):
+def test_jacobian_vs_central_fd(orc, idx):
     o = orc[0][idx]
     n = 6 if idx == 1 else 24
     st, rho = _states(idx, n, o)

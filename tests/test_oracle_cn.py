@@ -66,7 +66,7 @@ def test_enthalpy_newton_round_trip_and_bisection(orc, idx):
 
 @pytest.mark.parametrize("idx", [0, 1])
 def test_adiabatic_jacobian_vs_central_fd(orc, idx):
-    """dS/dY at fixed (rho, e) by complex step through the T inversion, against
+    """dS/dY at fixed (rho, e) by dual numbers through the T inversion, against
     central differences of S(Y) with T re-solved from e (h_k = 1e-7 max(|Y_k|, 1e-3))."""
     o = orc[idx]
     n = 4 if idx == 1 else 16

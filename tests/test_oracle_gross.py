@@ -57,7 +57,7 @@ def test_gross_bounds_every_derivative_entry(orc, idx):
     J = o.jacobian(rho, st.T, st.Y).reshape(NP, NP, n)           # columns T, Y
     assert np.all(G >= 0)
     assert np.all(np.abs(J) <= G[:, 1:] * (1 + 1e-12) + 1e-300)
-    # rho column of the production rates, by a complex-step JVP along rho
+    # rho column of the production rates, by a JVP along rho
     jr = o.jvp(rho, st.T, st.Y, np.ones(n), np.zeros(n), np.zeros((o.N, n)))
     assert np.all(np.abs(jr) <= G[1:, 0] * (1 + 1e-12) + 1e-300)
     # the bound is not vacuous: for most entries it is within a few orders of |J|
@@ -265,10 +265,7 @@ def test_jvp_is_linear_at_states_with_tiny_mass_fractions(orc):
 
 def test_jvp_bounded_by_gross_scale_at_equilibrium_states(orc):
     """At Gibbs-minimised equilibrium states (mass fractions down to ~1e-230) the
-    JVP obeys the triangle inequality |J v|_k <= sum_c GJ_kc |v_c| entry by entry.
-    (A single complex step along v breaks it there: products of the
-    perturbations of different species, far larger than those species' mass
-    fractions, leak into the imaginary part.)"""
+    JVP obeys the triangle inequality |J v|_k <= sum_c GJ_kc |v_c| entry by entry."""
     from tests.edge_states import equilibrium_states
     o, mech = orc[1]
     rho, T, Y = equilibrium_states(o, mech, 40, seed=17)

@@ -9,7 +9,7 @@ formulas; the standard SRI falloff and PLOG forms are taken, readings p1, p2):
   above the last node it is the end node's; ln k is linear in ln p inside a
   segment and continuous across nodes; identical nodes make k independent of p;
 * the 53-species mechanism with SRI and PLOG reactions conserves mass and
-  elements, vanishes at a Gibbs-minimised equilibrium, and its complex-step
+  elements, vanishes at a Gibbs-minimised equilibrium, and its (dual-number)
   Jacobian agrees with central differences.
 """
 import math
@@ -136,7 +136,7 @@ def test_pdep_mechanism_conservation_and_equilibrium(pdep):
         assert np.all(np.abs(Rf - Rr)[ok] <= 1e-11 * scale[ok])
 
 
-def test_pdep_jacobian_complex_step_vs_central_fd(pdep):
+def test_pdep_jacobian_vs_central_fd(pdep):
     from tests.test_oracle import _fd_jacobian
     o, _ = pdep
     n = 5
