@@ -338,8 +338,8 @@ def start_large_compile(path):
 
     def run():
         try:
-            for opts in ("device=0", "device=0;variant=warp"):
-                B.Mechanism(path, opts).prepare("jvp,vjp")
+            B.Mechanism(path, "device=0").prepare("jvp,vjp")
+            B.Mechanism(path, "device=0;variant=warp").prepare("jvp,vjp,jacobian,jacobian_adiabatic")
         except Exception as e:  # reported by the rows that need the groups
             err.append(repr(e))
     t = threading.Thread(target=run, daemon=True)
@@ -421,6 +421,31 @@ def large_mechanism_rates(path, synth, dev, stream, args, rank):
             r[name + "_frac"] = fl * n / (ms * 1e-3) / peak
         deriv[tag] = r
     res["derivatives"] = deriv
+    # dense Jacobians, one block of 8 warps per state (variant=warp), on --large-jac-points
+    # states; FP64 fraction against the thread-per-state kernel's static count of the same
+    # quantity (the algorithmic operations of the assembly)
+    del d_Y, w_bar, w
+    nj = args.large_jac_points
+    jac = {"states": nj}
+    if mw.stat("jacobian_cta") > 0:
+        rj, Tj, Yj = rho[:nj].contiguous(), T[:nj].contiguous(), Y[:, :nj].contiguous()
+        mw.prepare("jacobian,jacobian_adiabatic")
+        J = torch.empty((161 * 161, nj), dtype=torch.float64, device=dev)
+        ms = timed(lambda: mw.jacobian(rj, Tj, Yj, out=J))
+        fl = mt.stat("jacobian_fp64_flops_per_point")
+        jac.update(jacobian_ms=ms, jacobian_states_per_s=nj / (ms * 1e-3), jacobian_out_GB_per_s=J.numel() * 8 / (ms * 1e6),
+                   jacobian_fp64_flops_per_state_static=fl, jacobian_frac=fl * nj / (ms * 1e-3) / peak)
+        del J
+        Ja = torch.empty((160 * 160, nj), dtype=torch.float64, device=dev)
+        ms = timed(lambda: mw.jacobian_adiabatic(rj, Tj, Yj, out=Ja))
+        fl = mt.stat("jacobian_adiabatic_fp64_flops_per_point")
+        jac.update(jacobian_adiabatic_ms=ms, jacobian_adiabatic_states_per_s=nj / (ms * 1e-3),
+                   jacobian_adiabatic_fp64_flops_per_state_static=fl,
+                   jacobian_adiabatic_frac=fl * nj / (ms * 1e-3) / peak)
+        del Ja
+    else:
+        jac["unavailable"] = "no block-per-state Jacobian kernels for this mechanism"
+    res["jacobian_block_per_state"] = jac
     return res
 
 
@@ -852,6 +877,8 @@ def main():
                     help="also time the Jacobian, dS/dY and Crank-Nicolson kernels on the 160-species "
                          "mechanism (or the comma list given of jacobian, jacobian_adiabatic, cn)")
     ap.add_argument("--large-deriv-points", type=int, default=2 ** 15)
+    ap.add_argument("--large-jac-points", type=int, default=2 ** 15,
+                    help="states of the block-per-state dense Jacobian rows of the large mechanism")
     ap.add_argument("--cn-points", type=int, default=2 ** 18)
     ap.add_argument("--no-cn", action="store_true")
     ap.add_argument("--transport-points", type=int, default=2 ** 20)

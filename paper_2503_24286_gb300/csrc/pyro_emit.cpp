@@ -2294,7 +2294,8 @@ extern "C" __global__ void __launch_bounds__(BLK) pyro_temperature_h(i64 n, cons
   out.smem_dyn_bytes_deriv = opt.dgstore ? 0 : 4 * N * opt.deriv_block * (int)sizeof(double);
   out.stats["jacobian_scratch_doubles_per_point"] = nslots;
   out.stats["deriv_warp_per_state"] = 0;
-  if (m.n_species() <= kWarpMaxSpecies && m.n_reactions() <= kWarpMaxReactions) {
+  std::string warp_why;
+  if (warp_supported(m, &warp_why)) {
     // warp-per-state kernels (compiled on first use: variant=warp)
     WarpEmit w = emit_warp_units(m, opt);
     for (auto& kv : w.sources) out.group_sources[kv.first] = kv.second;

@@ -54,6 +54,7 @@ int wkind(const Reaction& r) {
 
 struct WChunk {
   int kind = 0, base = 0, count = 0;
+  int goff = 0;             // Jacobian kernels: first slot of the chunk's species partials
   int nf = 1, nr = 1;       // largest reactant / product factor counts
   bool rev = true;          // any reversible reaction in the chunk
   int neff = 0;             // largest number of efficiency terms (eps != 1)
@@ -106,8 +107,11 @@ WPlan make_plan(const Mechanism& m) {
   int eoff = 0, foff = 0, roff = 0;
   for (int s = 0; s < M;) {
     const int kind = wkind(m.reactions[P.order[s]]);
+    const bool rev = m.reactions[P.order[s]].reversible;
+    // a chunk holds one class and one direction: the reverse product of an
+    // irreversible reaction must be absent, not the unit slot's 1
     int e = s;
-    while (e < M && e - s < 32 && wkind(m.reactions[P.order[e]]) == kind) ++e;
+    while (e < M && e - s < 32 && wkind(m.reactions[P.order[e]]) == kind && m.reactions[P.order[e]].reversible == rev) ++e;
     WChunk c;
     c.kind = kind; c.base = s; c.count = e - s; c.rev = false; c.nf = 1; c.nr = 1;
     for (int q = s; q < e; ++q) {
@@ -149,24 +153,26 @@ struct GLoop {
   std::vector<double> coef;    // [steps][32] (efficiency loops)
 };
 struct Gather {
+  int lanes = 32;                      // threads that share the gather (a warp or a block)
   std::vector<GLoop> loops;
   int nseg = 0;
   std::vector<int> seg_ptr, seg_idx;   // per species: its segments
   double entries = 0;
 };
 
-Gather build_gather(int N, std::vector<std::vector<GItem>> items) {
+Gather build_gather(int N, std::vector<std::vector<GItem>> items, int lanes = 32) {
   Gather G;
+  G.lanes = lanes;
   std::vector<std::vector<int>> segs(N);
   for (auto& its : items) {
     std::stable_sort(its.begin(), its.end(), [](const GItem& a, const GItem& b) { return a.k < b.k; });
     GLoop L;
     const int nnz = (int)its.size();
     G.entries += nnz;
-    L.steps = std::max(1, (nnz + 31) / 32);
-    L.ent.assign((size_t)L.steps * 64, 0u);
-    L.coef.assign((size_t)L.steps * 32, 0.0);
-    for (int l = 0; l < 32; ++l) {
+    L.steps = std::max(1, (nnz + lanes - 1) / lanes);
+    L.ent.assign((size_t)L.steps * lanes * 2, 0u);
+    L.coef.assign((size_t)L.steps * lanes, 0.0);
+    for (int l = 0; l < lanes; ++l) {
       const int a = l * L.steps, b = std::min(nnz, (l + 1) * L.steps);
       for (int q = a; q < b; ++q) {
         const GItem& it = its[q];
@@ -175,7 +181,7 @@ Gather build_gather(int N, std::vector<std::vector<GItem>> items) {
           y |= (1u << 20) | ((unsigned)G.nseg << 21);
           segs[it.k].push_back(G.nseg++);
         }
-        const size_t e = (size_t)(q - a) * 32 + l;
+        const size_t e = (size_t)(q - a) * lanes + l;
         L.ent[2 * e] = it.x;
         L.ent[2 * e + 1] = y;
         L.coef[e] = it.c;
@@ -187,6 +193,52 @@ Gather build_gather(int N, std::vector<std::vector<GItem>> items) {
   for (int k = 0; k < N; ++k) {
     for (int v : segs[k]) G.seg_idx.push_back(v);
     G.seg_ptr.push_back((int)G.seg_idx.size());
+  }
+  return G;
+}
+
+// Gather into the nonzero entries of a block of Jacobian rows: keys 0..nkeys-1
+// (every key has at least one item), items sorted by key and cut into `lanes`
+// runs of equal length.  The keys of one run are consecutive, so lane l needs
+// only its first key and advances one key per flush.  A key cut by a run
+// boundary is written by the lane it starts in; the lanes that continue it
+// write their partial sums to a carry slot (one per lane), and one fix-up
+// record per cut key adds those in lane order.  Fixed order: deterministic.
+struct NzItem {
+  int key;
+  unsigned slot;
+  int nu;
+};
+struct NzGather {
+  int steps = 1, nkeys = 0;
+  std::vector<unsigned> ent;     // [steps][lanes]: slot | (nu + 4) << 16 | flush << 19
+  std::vector<unsigned> lane0;   // [lanes]: first key | continues-a-key << 31
+  std::vector<unsigned> fix;     // per cut key: key | first carrying lane << 16 | last << 24
+};
+
+NzGather build_nz_gather(std::vector<NzItem> its, int nkeys, int lanes, unsigned zero_slot) {
+  NzGather G;
+  G.nkeys = nkeys;
+  std::stable_sort(its.begin(), its.end(), [](const NzItem& a, const NzItem& b) { return a.key < b.key; });
+  const int n = (int)its.size();
+  G.steps = std::max(1, (n + lanes - 1) / lanes);
+  G.ent.assign((size_t)G.steps * lanes, zero_slot);   // padding: the zero slot times nu index 0
+  G.lane0.assign(lanes, 0u);
+  for (int l = 0; l < lanes; ++l) {
+    const int a = l * G.steps, b = std::min(n, (l + 1) * G.steps);
+    if (a >= b) continue;
+    G.lane0[l] = (unsigned)its[a].key | ((a > 0 && its[a - 1].key == its[a].key) ? (1u << 31) : 0u);
+    for (int q = a; q < b; ++q) {
+      const bool flush = q + 1 == b || its[q + 1].key != its[q].key;
+      G.ent[(size_t)(q - a) * lanes + l] = its[q].slot | ((unsigned)(its[q].nu + 4) << 16) | (flush ? (1u << 19) : 0u);
+    }
+  }
+  for (int q = 0; q < n;) {
+    int e = q;
+    while (e < n && its[e].key == its[q].key) ++e;
+    const int la = q / G.steps, lb = (e - 1) / G.steps;
+    if (lb > la) G.fix.push_back((unsigned)its[q].key | ((unsigned)(la + 1) << 16) | ((unsigned)lb << 24));
+    q = e;
   }
   return G;
 }
@@ -208,7 +260,15 @@ void emit_array(std::ostringstream& o, const char* type, const std::string& name
 
 namespace {
 
-enum WMode { W_FWD = 0, W_JVP = 1, W_VJP = 2 };
+enum WMode { W_FWD = 0, W_JVP = 1, W_VJP = 2, W_JAC = 3, W_JAD = 4 };
+
+// Slots of a chunk's species partials in the Jacobian kernels: one per factor
+// occurrence (reactants, then products of reversible chunks), then one per
+// third-body efficiency term.
+int chunk_occ(const WChunk& c) { return c.nf + (c.rev ? c.nr : 0); }
+int chunk_gslots(const WChunk& c) {
+  return 32 * (chunk_occ(c) + ((c.kind != WK_PLAIN && c.kind != WK_PLOG) ? c.neff : 0));
+}
 
 std::string gname(const char* base, int g) { return std::string(base) + std::to_string(g); }
 
@@ -216,7 +276,7 @@ std::string gname(const char* base, int g) { return std::string(base) + std::to_
 void emit_gather_tables(std::ostringstream& o, const Gather& G, int g, bool coef) {
   for (size_t l = 0; l < G.loops.size(); ++l) {
     const auto& L = G.loops[l];
-    o << "__device__ const uint2 " << gname("w_ge", g) << "_" << l << "[" << L.steps * 32 << "] = {";
+    o << "__device__ const uint2 " << gname("w_ge", g) << "_" << l << "[" << L.steps * G.lanes << "] = {";
     for (size_t e = 0; e < L.ent.size() / 2; ++e)
       o << (e ? "," : "") << "{" << L.ent[2 * e] << "u," << L.ent[2 * e + 1] << "u}";
     o << "};\n";
@@ -227,14 +287,19 @@ void emit_gather_tables(std::ostringstream& o, const Gather& G, int g, bool coef
 }
 
 // One gather loop: lane l accumulates its run; `term` is the FP64 update of acc
-// for entry e (uint2) and coefficient c.
+// for entry e (uint2) and coefficient c.  `lane` names the thread's index among
+// the gather's lanes.
+// With sP2 given, a second accumulator acc2 flushes into sP2 alongside.
 void emit_gather_loop(std::ostringstream& k, const Gather& G, int g, size_t l, const std::string& term, bool coef,
-                      const std::string& sP) {
-  k << "    {\n      double acc = 0.0;\n#pragma unroll 4\n      for (int st = 0; st < " << G.loops[l].steps
-    << "; ++st) {\n        const uint2 e = __ldg(" << gname("w_ge", g) << "_" << l << " + st * 32 + lane);\n";
-  if (coef) k << "        const double c = __ldg(" << gname("w_gc", g) << "_" << l << " + st * 32 + lane);\n";
-  k << "        " << term << "\n"
-    << "        if (e.y & (1u << 20)) { " << sP << "[e.y >> 21] = acc; acc = 0.0; }\n      }\n    }\n";
+                      const std::string& sP, const std::string& lane = "lane", const std::string& sP2 = "") {
+  const std::string at = " + st * " + std::to_string(G.lanes) + " + " + lane + ");\n";
+  k << "    {\n      double acc = 0.0" << (sP2.empty() ? "" : ", acc2 = 0.0") << ";\n#pragma unroll 4\n"
+    << "      for (int st = 0; st < " << G.loops[l].steps
+    << "; ++st) {\n        const uint2 e = __ldg(" << gname("w_ge", g) << "_" << l << at;
+  if (coef) k << "        const double c = __ldg(" << gname("w_gc", g) << "_" << l << at;
+  k << "        " << term << "\n        if (e.y & (1u << 20)) { " << sP << "[e.y >> 21] = acc; acc = 0.0;";
+  if (!sP2.empty()) k << " " << sP2 << "[e.y >> 21] = acc2; acc2 = 0.0;";
+  k << " }\n      }\n    }\n";
 }
 
 // Per-species total of gather g (segments in sP): into the double variable `var`.
@@ -427,6 +492,48 @@ void emit_chunk(std::ostringstream& rc, const WChunk& c, int mode) {
     rc << "      const double dPf = " << dprod("i", c.nf, "sdA") << ";\n";
     if (c.rev) rc << "      const double dPr = " << dprod("o", c.nr, "sdA") << ";\n";
     rc << "      sR[s] = fma(dkk, D, kk * " << (c.rev ? "(dPf - dPr)" : "dPf") << ");\n";
+  } else if (mode == W_JAC || mode == W_JAD) {
+    // per-reaction partials of the dense Jacobian: dR/dT, the [M] term kM D rho,
+    // and dR/dY_i at fixed (rho, T) per factor occurrence (the other factors'
+    // product) and per efficiency term ((eps_i - 1)/W_i kM D rho)
+    auto others = [&](const char* v, int nfac, int q) {
+      std::string t;
+      for (int r = 0; r < nfac; ++r) if (r != q) t += " * sA[" + std::string(v) + std::to_string(r) + "]";
+      return t;
+    };
+    rc << "      const double R = kk * D;\n";
+    if (c.rev) {
+      rc << "      const double dS = sLp[i0]";
+      for (int q = 1; q < c.nf; ++q) rc << " + sLp[i" << q << "]";
+      for (int q = 0; q < c.nr; ++q) rc << " - sLp[o" << q << "]";
+      rc << ";\n      const double Rt = kk * fma(D, tau, Pr * dS);\n";
+    } else {
+      rc << "      const double Rt = kk * (D * tau);\n";
+    }
+    rc << "      sRt[s] = Rt;\n";
+    if (c.kind != WK_PLAIN) rc << "      const double RMr = kM * D * rho;\n      sRM[s] = RMr;\n";
+    else rc << "      sRM[s] = 0.0;\n";
+    for (int q = 0; q < c.nf; ++q)
+      rc << "      sG[" << c.goff + q * 32 << " + lane] = kk * sEr[i" << q << "]" << others("i", c.nf, q) << ";\n";
+    if (c.rev)
+      for (int q = 0; q < c.nr; ++q)
+        rc << "      sG[" << c.goff + (c.nf + q) * 32 << " + lane] = -kk * sEr[o" << q << "]" << others("o", c.nr, q)
+           << ";\n";
+    if (tb)
+      for (int q = 0; q < c.neff; ++q)
+        rc << "      sG[" << c.goff + (chunk_occ(c) + q) * 32 << " + lane] = __ldg(w_ec + " << c.eoff + q * 32
+           << " + lane) * RMr;\n";
+    if (mode == W_JAC) {
+      // the reaction's internal-energy and heat-capacity changes (Tdot row)
+      rc << "      double dE = 0.0, dC = 0.0;\n";
+      for (int q = 0; q < c.nrb; ++q)
+        rc << "      { const unsigned short b = __ldg(w_rb + " << c.roff + q * 32
+           << " + lane); const double nu = s_nu[b >> 10]; dE = fma(nu, seh[b & 1023], dE); dC = fma(nu, scm[b & 1023], dC); }\n";
+      rc << "      sDE[s] = dE;\n      pew = fma(dE, R, pew); pcw = fma(dC, R, pcw); pejt = fma(dE, Rt, pejt);\n";
+      if (c.kind != WK_PLAIN) rc << "      pU = fma(dE, RMr, pU);\n";
+    } else {
+      rc << "      (void)R;\n";
+    }
   } else {
     rc << "      double Rb = 0.0;\n";
     for (int q = 0; q < c.nrb; ++q)
@@ -444,6 +551,26 @@ void emit_chunk(std::ostringstream& rc, const WChunk& c, int mode) {
 }
 
 }  // namespace
+
+bool warp_supported(const Mechanism& m, std::string* why) {
+  if (m.n_species() > kWarpMaxSpecies || m.n_reactions() > kWarpMaxReactions) {
+    *why = "variant=warp supports up to " + std::to_string(kWarpMaxSpecies) + " species and " +
+           std::to_string(kWarpMaxReactions) + " reactions";
+    return false;
+  }
+  if (!common_tmid(m)) {
+    *why = "variant=warp needs all species to share one NASA-7 T_mid";
+    return false;
+  }
+  for (int j = 0; j < m.n_reactions(); ++j) {
+    const Reaction& r = m.reactions[j];
+    if (n_factors(r.reactants) > 3 || n_factors(r.products) > 3) {
+      *why = "variant=warp supports at most three factors a side (reaction " + std::to_string(j) + ")";
+      return false;
+    }
+  }
+  return true;
+}
 
 WarpEmit emit_warp_units(const Mechanism& m, const EmitOptions& opt) {
   WarpEmit out;
@@ -925,6 +1052,320 @@ __device__ double wtsolve(const double* sY, double e, double T0, int max_iter, f
     out.smem["wvjp"] = wp.second;
     out.wpb["wvjp"] = wp.first;
   }
+  // ===================== dense Jacobians, one block of 8 warps per state =====================
+  // Phase A (threads over species): thermo, activities, c_v.  Phase B (warps over
+  // chunks of 32 reactions, balanced by an operation estimate): per reaction
+  // dR/dT, the [M] term and one partial per factor occurrence and efficiency term
+  // (slots of sG).  Phase C: balanced gathers over the block's 256 threads -- the
+  // column of dT (sum nu dR/dT), the [M] rank-one factor u_k = sum nu kM D rho,
+  // the Tdot row's column sums -- then, per group of rows, the nonzero species
+  // entries (sum nu partial) into shared memory and every entry of the rows
+  // written once (u_k/W_i plus the nonzero part).
+  auto cta_jac = [&](bool ty) -> bool {
+    const int LN = 256, NW = 8, NB = (N + 31) / 32;
+    std::vector<WChunk> ch = P.chunks;
+    int gtot = 0;
+    for (auto& c : ch) { c.goff = gtot; gtot += chunk_gslots(c); }
+    const unsigned GZ = (unsigned)gtot;   // zero slot (gather padding)
+    if (gtot + 1 > 65536 || M >= (1 << 20)) return false;
+    // every reaction slot's partials: (species, slot of sG)
+    std::vector<std::vector<std::pair<int, unsigned>>> part(M);
+    for (auto& c : ch)
+      for (int l = 0; l < c.count; ++l) {
+        const int s = c.base + l;
+        const Reaction& r = m.reactions[P.order[s]];
+        std::vector<int> fr = side_factors(r.reactants);
+        for (size_t q = 0; q < fr.size(); ++q) part[s].push_back({fr[q], (unsigned)(c.goff + q * 32 + l)});
+        if (c.rev) {
+          std::vector<int> fp = side_factors(r.products);
+          for (size_t q = 0; q < fp.size(); ++q) part[s].push_back({fp[q], (unsigned)(c.goff + (c.nf + q) * 32 + l)});
+        }
+        if (c.kind != WK_PLAIN && c.kind != WK_PLOG) {
+          int q = 0;
+          for (auto& e : r.efficiencies) {
+            if (e.second == 1.0) continue;
+            part[s].push_back({e.first, (unsigned)(c.goff + (chunk_occ(c) + q) * 32 + l)});
+            ++q;
+          }
+        }
+      }
+    // gathers: dT column and [M] factor (the production-rate pairs), Tdot column sums
+    const Gather gJ = build_gather(N, {fw}, LN);
+    std::vector<GItem> td;
+    if (ty)
+      for (int s = 0; s < M; ++s)
+        for (auto& pi : part[s]) td.push_back({pi.first, pi.second, (unsigned)s, 0.0});
+    const Gather gT = build_gather(N, {td}, LN);
+    // nonzero pattern of the species block and its terms
+    std::vector<std::map<int, std::vector<std::pair<unsigned, int>>>> rowt(N);
+    for (int s = 0; s < M; ++s)
+      for (auto& kn : net_nu(m.reactions[P.order[s]]))
+        if (kn.second)
+          for (auto& pi : part[s]) rowt[kn.first][pi.first].push_back({pi.second, kn.second});
+    // row groups: the nonzero sums of a group (and 256 carries) reuse the
+    // reaction arrays dR/dT, [M] term and energy change (3 M doubles)
+    const int region = std::max(3 * M, 1280), cap = region - LN;
+    struct RGroup { int r0, r1, nnz; };
+    std::vector<RGroup> groups;
+    for (int k = 0; k < N;) {
+      RGroup g{k, k, 0};
+      while (g.r1 < N && g.nnz + (int)rowt[g.r1].size() <= cap) g.nnz += (int)rowt[g.r1++].size();
+      groups.push_back(g);
+      k = g.r1;
+    }
+    std::vector<unsigned> jm((size_t)2 * N * NB, 0u);   // per (row, 32-column block): mask, group-local base
+    std::vector<NzGather> nzg;
+    double nz_terms = 0, nnz_total = 0;
+    for (auto& g : groups) {
+      std::vector<NzItem> its;
+      int key = 0;
+      for (int k = g.r0; k < g.r1; ++k) {
+        for (int b = 0; b < NB; ++b) jm[2 * ((size_t)k * NB + b) + 1] = (unsigned)key;   // base before the block's first
+        int bprev = -1;
+        for (auto& it : rowt[k]) {
+          const int i = it.first, b = i / 32;
+          if (b != bprev) { jm[2 * ((size_t)k * NB + b) + 1] = (unsigned)key; bprev = b; }
+          jm[2 * ((size_t)k * NB + b)] |= 1u << (i % 32);
+          for (auto& t : it.second) its.push_back({key, t.first, t.second});
+          ++key;
+        }
+      }
+      nz_terms += its.size();
+      nnz_total += key;
+      nzg.push_back(build_nz_gather(its, key, LN, GZ));
+    }
+    // ---- source
+    std::ostringstream k;
+    k << o.str();
+    std::vector<double> cpt(2 * 5 * N1, 0.0), cdt(2 * 4 * N1, 0.0);
+    for (int q = 0; q < N; ++q)
+      for (int r = 0; r < 2; ++r) {
+        for (int t = 0; t < 5; ++t) cpt[(r * 5 + t) * N1 + q] = C[q].cp[r][t];
+        for (int t = 0; t < 4; ++t) cdt[(r * 4 + t) * N1 + q] = C[q].cpd[r][t];
+      }
+    emit_array(k, "double", "w_Cp", cpt, true);
+    if (ty) emit_array(k, "double", "w_Cd", cdt, true);
+    if (!ty) {
+      std::vector<double> Wt(N);
+      for (int q = 0; q < N; ++q) Wt[q] = m.species[q].W;
+      emit_array(k, "double", "w_W", Wt, true);
+    }
+    emit_gather_tables(k, gJ, 3, false);
+    if (ty) emit_gather_tables(k, gT, 4, false);
+    k << "__device__ const uint2 w_jm[" << N * NB << "] = {";
+    for (int q = 0; q < N * NB; ++q) k << (q ? "," : "") << "{" << jm[2 * q] << "u," << jm[2 * q + 1] << "u}";
+    k << "};\n";
+    for (size_t g = 0; g < nzg.size(); ++g) {
+      emit_array(k, "unsigned", "w_jz" + std::to_string(g), nzg[g].ent, false);
+      emit_array(k, "unsigned", "w_jl" + std::to_string(g), nzg[g].lane0, false);
+      emit_array(k, "unsigned", "w_jf" + std::to_string(g), nzg[g].fix, false);
+    }
+    k << R"(
+// warp sums of four values at once (every lane gets all four): 6 FP64 adds per lane
+__device__ __forceinline__ void warp_sum4(double (&v)[4], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const double mine = b4 ? v[q + 2] : v[q], give = b4 ? v[q] : v[q + 2];
+    v[q] = mine + __shfl_xor_sync(0xffffffffu, give, 16);
+  }
+  {
+    const double mine = b3 ? v[1] : v[0], give = b3 ? v[0] : v[1];
+    v[0] = mine + __shfl_xor_sync(0xffffffffu, give, 8);
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 4);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  const double t = v[0];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = __shfl_sync(0xffffffffu, t, ((q >> 1) & 1) * 16 + (q & 1) * 8);
+}
+// block sums of four values (every thread gets all four); sRed: 36 doubles
+__device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp, int lane) {
+  warp_sum4(v, lane);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sRed[warp * 4 + q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += sRed[w * 4 + threadIdx.x];
+    sRed[32 + threadIdx.x] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = sRed[32 + q];
+}
+)";
+    // shared memory (doubles)
+    std::vector<std::pair<std::string, int>> arr = {
+        {"s_exp", 512}, {"s_log", 256}, {"s_nu", 8}, {"sRed", 80},
+        {"sY", N1}, {"sL", N1}, {"sA", N1}, {"sEr", N1}, {"sLp", N1}, {"seh", N1}, {"scm", N1},
+        {"sjt", N1}, {"su", N1}, {"sX", N1},
+        {"sPj", std::max(1, gJ.nseg)}, {"sPu", std::max(1, gJ.nseg)}, {"sPt", ty ? std::max(1, gT.nseg) : 1},
+        {"sG", gtot + 1}, {"sR3", region}};
+    int words = 0;
+    for (auto& a : arr) words += a.second;
+    const long bytes = 8L * words;
+    if (bytes > 227L * 1024) return false;
+    const std::string kname = ty ? "pyro_jacobian_cta" : "pyro_jacobian_adiabatic_cta";
+    k << "\n// " << (ty ? "Dense Jacobian d(Tdot, omega)/d(T, Y) at fixed rho (arguments and layout as pyro_jacobian)"
+                        : "dS/dY at fixed (rho, e), S = W omega (arguments and layout as pyro_jacobian_adiabatic)")
+      << ",\n// one block of " << NW << " warps per state.\n"
+      << "extern \"C\" __global__ void __launch_bounds__(" << LN << ") " << kname
+      << "(i64 n, const double* __restrict__ g_rho,\n"
+         "    const double* __restrict__ g_T, const double* __restrict__ g_Y, double* __restrict__ g_J,\n"
+         "    double* __restrict__ g_scratch) {\n"
+         "  extern __shared__ double smem[];\n  (void)g_scratch;\n";
+    int off = 0;
+    for (auto& a : arr) {
+      k << "  double* " << a.first << " = smem + " << off << ";\n";
+      off += a.second;
+    }
+    k << "  double* sRt = sR3;\n  double* sRM = sR3 + " << M << ";\n  double* sDE = sR3 + " << 2 * M << ";\n"
+      << "  double* sP = sR3;            // nonzero sums of a row group (after the gathers)\n"
+      << "  double* sC = sR3 + " << cap << ";   // carries of the row-group gathers\n"
+      << "  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;\n"
+      << "  wload_tables(s_exp, s_log, s_nu);\n  if (tid == 0) sG[" << GZ << "] = 0.0;\n  __syncthreads();\n"
+      << "  for (i64 p = blockIdx.x; p < n; p += gridDim.x) {\n"
+      << "    const double rho = g_rho[p], T = g_T[p];\n"
+         "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
+         "    const double RT = " << lit((double)R_GAS) << " * T;\n"
+         "    const int hi = pdm::to_float_trunc(T) >= (float)TMID;\n"
+         "    double red[4] = {0.0, 0.0, 0.0, 0.0};   // sum Y/W, c_v, dc_v/dT\n"
+         "    for (int k = tid; k < NSP; k += " << LN << ") {\n"
+         "      const double y = g_Y[(i64)k * n + p];\n"
+      << species_L(true) <<
+         "      const double E = PEXP(q, s_exp);\n"
+         "      sY[k] = y; sL[k] = q; sA[k] = E * (rho * y); sEr[k] = E * rho; sLp[k] = Lp;\n"
+         "      seh[k] = fma(RT, hr, -RT);\n"
+         "      const double* Cp = w_Cp + hi * 5 * (NSP + 1);\n"
+         "      double cp = fma(T, __ldg(Cp + 4 * (NSP + 1) + k), __ldg(Cp + 3 * (NSP + 1) + k));\n"
+         "      cp = fma(T, cp, __ldg(Cp + 2 * (NSP + 1) + k));\n"
+         "      cp = fma(T, cp, __ldg(Cp + (NSP + 1) + k));\n"
+         "      cp = fma(T, cp, __ldg(Cp + k));\n"
+         "      const double yw = y * __ldg(w_invW + k), ywR = yw * " << lit((double)R_GAS) << ";\n"
+         "      red[0] += yw;\n      red[1] = fma(ywR, cp - 1.0, red[1]);\n";
+    if (ty)
+      k << "      scm[k] = " << lit((double)R_GAS) << " * (cp - 1.0);\n"
+           "      const double* Cd = w_Cd + hi * 4 * (NSP + 1);\n"
+           "      double cd = fma(T, __ldg(Cd + 3 * (NSP + 1) + k), __ldg(Cd + 2 * (NSP + 1) + k));\n"
+           "      cd = fma(T, cd, __ldg(Cd + (NSP + 1) + k));\n"
+           "      cd = fma(T, cd, __ldg(Cd + k));\n"
+           "      red[2] = fma(ywR, cd, red[2]);\n";
+    k << "    }\n"
+         "    if (tid == 0) { sY[NSP] = 0.0; sL[NSP] = 0.0; sA[NSP] = 1.0; sEr[NSP] = 0.0; sLp[NSP] = 0.0; seh[NSP] = 0.0; "
+         "scm[NSP] = 0.0; }\n"
+         "    cta_sum4(red, sRed, warp, lane);\n"
+         "    const double ysum = red[0], cv = red[1], cvT = red[2];\n    (void)cvT;\n";
+    if (plog) k << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lnR << ";\n";
+    // phase B: chunks to warps, largest estimated cost first, to the least loaded warp
+    std::vector<double> cost(ch.size());
+    for (size_t c = 0; c < ch.size(); ++c) {
+      const WChunk& q = ch[c];
+      double e = 30 + 3 * chunk_occ(q) + 4 * q.nrb;
+      if (q.kind == WK_TB) e += 4 + 3 * q.neff;
+      else if (q.kind == WK_LIND) e += 30 + 3 * q.neff;
+      else if (q.kind == WK_TROE3 || q.kind == WK_TROE4) e += 75 + 3 * q.neff;
+      else if (q.kind == WK_SRI) e += 60 + 3 * q.neff;
+      else if (q.kind == WK_PLOG) e += 20 + 4 * q.nodes;
+      cost[c] = e;
+    }
+    std::vector<int> ordc(ch.size());
+    for (size_t c = 0; c < ch.size(); ++c) ordc[c] = (int)c;
+    std::stable_sort(ordc.begin(), ordc.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<std::vector<int>> own(NW);
+    std::vector<double> load(NW, 0.0);
+    for (int c : ordc) {
+      const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      own[w].push_back(c);
+      load[w] += cost[c];
+    }
+    k << "    double pew = 0.0, pcw = 0.0, pejt = 0.0, pU = 0.0;   // sums over reactions (Tdot row)\n";
+    for (int w = 0; w < NW; ++w) {
+      std::sort(own[w].begin(), own[w].end());
+      k << "    if (warp == " << w << ") {\n";
+      for (int c : own[w]) emit_chunk(k, ch[c], ty ? W_JAC : W_JAD);
+      k << "    }\n";
+    }
+    k << "    __syncthreads();\n";
+    // phase C1: gathers
+    emit_gather_loop(k, gJ, 3, 0,
+        "const double nu = s_nu[(e.x >> 16) & 7u]; const unsigned s = e.x & 0xffffu; "
+        "acc = fma(nu, sRt[s], acc); acc2 = fma(nu, sRM[s], acc2);", false, "sPj", "tid", "sPu");
+    if (ty) {
+      emit_gather_loop(k, gT, 4, 0, "acc = fma(sDE[e.y & 0xfffffu], sG[e.x], acc);", false, "sPt", "tid");
+      k << "    double r4[4] = {pew, pcw, pejt, pU};\n    cta_sum4(r4, sRed + 40, warp, lane);\n"
+           "    const double rcv = pdm::rcp(rho * cv), Tdot = -r4[0] * rcv, tcv = Tdot * pdm::rcp(cv);\n"
+           "    if (tid == 0) g_J[p] = fma(-(r4[1] + r4[2]), rcv, -tcv * cvT);\n";
+    } else {
+      k << "    __syncthreads();\n    const double mrcv = -pdm::rcp(cv);\n";
+    }
+    // phase C2: per-species totals, the dT column (ty) and the Tdot row (ty)
+    k << "    for (int k = tid; k < NSP; k += " << LN << ") {\n" << gather_total(3, "sPj", "jt")
+      << gather_total(3, "sPu", "u");
+    if (ty) {
+      k << gather_total(4, "sPt", "td") <<
+           "      sjt[k] = jt; su[k] = u;\n"
+           "      const double iw = __ldg(w_invW + k);\n"
+           "      g_J[(i64)(1 + k) * " << N1 << " * n + p] = jt;\n"
+           "      g_J[(i64)(1 + k) * n + p] = fma(-fma(iw, r4[3], td), rcv, -tcv * (scm[k] * iw));\n";
+    } else {
+      k << "      const double Wk = __ldg(w_W + k);\n"
+           "      sjt[k] = Wk * jt; su[k] = Wk * u;\n"
+           "      sX[k] = (seh[k] * __ldg(w_invW + k)) * mrcv;   // dT/dY_k at fixed e\n";
+    }
+    k << "    }\n    __syncthreads();\n";
+    // phase C3: row groups
+    for (size_t g = 0; g < groups.size(); ++g) {
+      const RGroup& G = groups[g];
+      const NzGather& Z = nzg[g];
+      const std::string gs = std::to_string(g);
+      k << "    { // rows " << G.r0 << ".." << G.r1 - 1 << ": " << G.nnz << " nonzero species entries\n"
+           "      const unsigned l0 = __ldg(w_jl" << gs << " + tid);\n"
+           "      int key = (int)(l0 & 0x7fffffffu);\n      bool carry = (l0 >> 31) != 0u;\n"
+           "      double acc = 0.0;\n#pragma unroll 4\n"
+           "      for (int st = 0; st < " << Z.steps << "; ++st) {\n"
+           "        const unsigned e = __ldg(w_jz" << gs << " + st * " << LN << " + tid);\n"
+           "        acc = fma(s_nu[(e >> 16) & 7u], sG[e & 0xffffu], acc);\n"
+           "        if (e & (1u << 19)) { if (carry) { sC[tid] = acc; carry = false; } else { sP[key] = acc; } ++key; acc = 0.0; }\n"
+           "      }\n    }\n    __syncthreads();\n";
+      if (!Z.fix.empty())
+        k << "    if (tid < " << Z.fix.size() << ") {\n"
+             "      const unsigned f = __ldg(w_jf" << gs << " + tid);\n"
+             "      const int K = (int)(f & 0xffffu);\n      double v = sP[K];\n"
+             "      for (int l = (int)((f >> 16) & 255u); l <= (int)(f >> 24); ++l) v += sC[l];\n"
+             "      sP[K] = v;\n    }\n    __syncthreads();\n";
+      k << "    for (int q = warp; q < " << (G.r1 - G.r0) * NB << "; q += " << NW << ") {\n"
+           "      const int k = " << G.r0 << " + q / " << NB << ", b = q % " << NB << ";\n"
+           "      const int i = b * 32 + lane;\n"
+           "      if (i < NSP) {\n"
+           "        const uint2 mb = __ldg(w_jm + k * " << NB << " + b);\n";
+      if (ty)
+        k << "        double v = su[k] * __ldg(w_invW + i);\n"
+             "        if ((mb.x >> lane) & 1u) v += sP[mb.y + __popc(mb.x & ((1u << lane) - 1u))];\n"
+             "        g_J[((i64)(1 + k) * " << N1 << " + 1 + i) * n + p] = v;\n";
+      else
+        k << "        double v = fma(sjt[k], sX[i], su[k] * __ldg(w_invW + i));\n"
+             "        if ((mb.x >> lane) & 1u) v = fma(__ldg(w_W + k), sP[mb.y + __popc(mb.x & ((1u << lane) - 1u))], v);\n"
+             "        g_J[((i64)k * " << N << " + i) * n + p] = v;\n";
+      k << "      }\n    }\n    __syncthreads();\n";
+    }
+    k << "  }\n}\n";
+    const std::string key = ty ? "wjac" : "wjad";
+    out.sources[key] = k.str();
+    out.wpb[key] = NW;
+    out.smem[key] = (int)bytes;
+    out.stats[key + "_row_groups"] = (double)groups.size();
+    out.stats[key + "_nonzeros"] = nnz_total;
+    out.stats[key + "_terms"] = nz_terms;
+    out.stats[key + "_partial_slots"] = gtot;
+    return true;
+  };
+  out.stats["jacobian_cta"] = cta_jac(true) ? 1 : 0;
+  out.stats["jacobian_adiabatic_cta"] = cta_jac(false) ? 1 : 0;
   out.stats["warp_chunks"] = (double)P.chunks.size();
   out.stats["warp_gather_steps"] = gF.loops[0].steps;
   out.stats["warp_segments"] = gF.nseg;

@@ -25,6 +25,12 @@ struct WarpEmit {
 constexpr int kWarpMaxSpecies = 1022;
 constexpr int kWarpMaxReactions = 65535;
 
+// Whether the warp-per-state kernels cover the mechanism: the limits above, at
+// most three factors on each side of a reaction (packed factor lists; net
+// stoichiometric coefficients -3..3), and one NASA-7 T_mid shared by all species
+// (one range choice per state).  Otherwise *why says what is not met.
+bool warp_supported(const Mechanism& m, std::string* why);
+
 WarpEmit emit_warp_units(const Mechanism& m, const EmitOptions& opt);
 
 }  // namespace pyro

@@ -501,7 +501,8 @@ int ensure_store(pyro_mech* h, size_t bytes) {
 const char* group_kernel(const std::string& g) {
   return g == "jvp" ? "pyro_jvp" : g == "vjp" ? "pyro_vjp" : g == "jad" ? "pyro_jacobian_adiabatic"
        : g == "cn" ? "pyro_cn_assemble" : g == "tr" ? "pyro_transport" : g == "wfwd" ? "pyro_omega_warp"
-       : g == "wjvp" ? "pyro_jvp_warp" : g == "wvjp" ? "pyro_vjp_warp" : "pyro_jacobian";
+       : g == "wjvp" ? "pyro_jvp_warp" : g == "wvjp" ? "pyro_vjp_warp" : g == "wjac" ? "pyro_jacobian_cta"
+       : g == "wjad" ? "pyro_jacobian_adiabatic_cta" : "pyro_jacobian";
 }
 
 // Compile (in parallel threads, cached on disk) and load the named derivative
@@ -624,6 +625,26 @@ int launch_warp(const pyro_mech* h, const pyro_mech::Group& G, int64_t n, void* 
   return PYRO_OK;
 }
 
+// block-per-state kernels (dense Jacobians of variant=warp): one state per block
+// and iteration, a persistent grid of the resident blocks
+int launch_cta(const pyro_mech* h, const pyro_mech::Group& G, int64_t n, void* stream, void** params) {
+  int64_t cap = (int64_t)h->num_sms * G.blocks_per_sm;
+  unsigned grid = (unsigned)(n < cap ? n : cap);
+  if (grid == 0) return PYRO_OK;
+  CUresult r = driver().LaunchKernel(G.f, grid, 1, 1, G.block, 1, 1, G.smem, as_stream(stream), params, nullptr);
+  if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
+  return PYRO_OK;
+}
+
+// the dense Jacobian groups of a handle: block per state (variant=warp, where
+// emitted) or thread per state
+std::string jac_group(const pyro_mech* h, bool adiabatic) {
+  pyro_mech* m = const_cast<pyro_mech*>(h);
+  if (h->opt.warp && m->emitted.stats[adiabatic ? "jacobian_adiabatic_cta" : "jacobian_cta"] > 0)
+    return adiabatic ? "wjad" : "wjac";
+  return adiabatic ? "jad" : "jac";
+}
+
 int launch_deriv(const pyro_mech* h, const pyro_mech::Group& G, int64_t n, void* stream, void** params) {
   const int blk = G.block > 0 ? G.block : h->opt.deriv_block;
   const int smem = G.smem >= 0 ? G.smem : h->emitted.smem_dyn_bytes_deriv;
@@ -651,10 +672,9 @@ int pyro_mech_load(const char* mech_path, const char* options, pyro_mech** out) 
   if (!parse_options(options, h->opt, err)) { delete h; return fail(PYRO_EINVAL, err); }
   if (!parse_mechanism_file(mech_path, h->m, err)) { delete h; return fail(PYRO_EMECH, err); }
   if (!validate_mechanism(h->m, err)) { delete h; return fail(PYRO_EMECH, err); }
-  if (h->opt.warp && (h->m.n_species() > pyro::kWarpMaxSpecies || h->m.n_reactions() > pyro::kWarpMaxReactions)) {
+  if (h->opt.warp && !pyro::warp_supported(h->m, &err)) {
     delete h;
-    return fail(PYRO_EINVAL, "variant=warp supports up to " + std::to_string(pyro::kWarpMaxSpecies) + " species and " +
-                                 std::to_string(pyro::kWarpMaxReactions) + " reactions");
+    return fail(PYRO_EINVAL, err);
   }
   for (auto& s : h->m.species) h->W.push_back(s.W);
   EmitOptions eo;
@@ -911,15 +931,15 @@ int pyro_mech_prepare(const pyro_mech* hc, const char* kernels) {
   std::string k = kernels ? kernels : "all";
   std::vector<std::string> names;
   if (k == "all") {
-    names = {h->opt.warp ? "wjvp" : "jvp", h->opt.warp ? "wvjp" : "vjp", "jac"};
+    names = {h->opt.warp ? "wjvp" : "jvp", h->opt.warp ? "wvjp" : "vjp", jac_group(h, false)};
   }
   else {
     std::string item;
     std::stringstream ss(k);
     while (std::getline(ss, item, ',')) {
       if (item == "jvp" || item == "vjp") names.push_back(h->opt.warp ? "w" + item : item);
-      else if (item == "jacobian" || item == "jac") names.push_back("jac");
-      else if (item == "jacobian_adiabatic" || item == "jad") names.push_back("jad");
+      else if (item == "jacobian" || item == "jac") names.push_back(jac_group(h, false));
+      else if (item == "jacobian_adiabatic" || item == "jad") names.push_back(jac_group(h, true));
       else if (item == "cn" || item == "crank_nicolson") names.push_back("cn");
       else if (item == "warp" || item == "wfwd") names.push_back("wfwd");
       else if (item == "transport" || item == "tr") {
@@ -980,17 +1000,20 @@ int pyro_jacobian(const pyro_mech* hc, int64_t n, const double* rho, const doubl
     return fail(PYRO_EINVAL, "the dense Jacobian kernels need all species to share one NASA-7 T_mid");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
-  if (int rc = ensure_groups(h, {"jac"})) return rc;
-  const pyro_mech::Group& G = h->groups["jac"];
+  const std::string g = jac_group(h, false);
+  if (int rc = ensure_groups(h, {g})) return rc;
+  const pyro_mech::Group& G = h->groups[g];
+  const bool cta = g[0] == 'w';
   int NP = h->m.n_species() + 1;
   const int64_t NS = h->m.n_species();
-  if (int rc = ensure_jac_scratch(h, G, n)) return rc;
+  if (!cta)
+    if (int rc = ensure_jac_scratch(h, G, n)) return rc;
   return with_args(h, n, {{rho, 1, 8, true, false}, {T, 1, 8, true, false}, {Y, NS, 8, true, false}, {J, (int64_t)NP * NP, 8, false, true}},
                    stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
                      long long nn = nc;
                      void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &h->d_jac_scratch};
-                     return launch_deriv(h, G, nc, st, params);
-                   });
+                     return cta ? launch_cta(h, G, nc, st, params) : launch_deriv(h, G, nc, st, params);
+                   }, cta);
 }
 
 
@@ -1023,16 +1046,19 @@ int pyro_jacobian_adiabatic(const pyro_mech* hc, int64_t n, const double* rho, c
     return fail(PYRO_EINVAL, "the dense Jacobian kernels need all species to share one NASA-7 T_mid");
   if (n == 0) return PYRO_OK;
   if (int rc = check_device(h)) return rc;
-  if (int rc = ensure_groups(h, {"jad"})) return rc;
-  const pyro_mech::Group& G = h->groups["jad"];
+  const std::string g = jac_group(h, true);
+  if (int rc = ensure_groups(h, {g})) return rc;
+  const pyro_mech::Group& G = h->groups[g];
+  const bool cta = g[0] == 'w';
   const int64_t NS = h->m.n_species();
-  if (int rc = ensure_jac_scratch(h, G, n)) return rc;
+  if (!cta)
+    if (int rc = ensure_jac_scratch(h, G, n)) return rc;
   return with_args(h, n, {{rho, 1, 8, true, false}, {T, 1, 8, true, false}, {Y, NS, 8, true, false}, {J, NS * NS, 8, false, true}},
                    stream, [&](std::vector<void*>& d, int64_t nc, void* st) {
                      long long nn = nc;
                      void* params[] = {&nn, &d[0], &d[1], &d[2], &d[3], &h->d_jac_scratch};
-                     return launch_deriv(h, G, nc, st, params);
-                   });
+                     return cta ? launch_cta(h, G, nc, st, params) : launch_deriv(h, G, nc, st, params);
+                   }, cta);
 }
 
 namespace {

@@ -29,3 +29,18 @@ def mech_files(mech_dir):
         synth.write_mechanism(m, p)
         out[i], objs[i] = p, m
     return out, objs
+
+
+@pytest.fixture(scope="session")
+def mixed_reversibility_mech(mech_dir):
+    """The 53-species SRI/PLOG variant with every third reaction made irreversible,
+    so that reversible and irreversible reactions of each class sit side by side
+    in the kernels' reaction order."""
+    from paper_2503_24286_gb300 import synth
+    m = synth.config_mechanism(7)
+    for j, r in enumerate(m.reactions):
+        if j % 3 == 1:
+            r.reversible = False
+    p = os.path.join(mech_dir, "mech7_mixed.txt")
+    synth.write_mechanism(m, p)
+    return p

@@ -255,14 +255,17 @@ def test_full_size_workload_sampled(mechs, dev):
     assert np.all(np.abs(w[:, ii].cpu().numpy() - ow) <= TOL_W * G + 1e-300)
 
 
-@pytest.mark.parametrize("idx", [0, 1, 7])
-def test_warp_variant_parity(mechs, dev, mech_files, idx):
+@pytest.mark.parametrize("idx", [0, 1, 7, "7-mixed"])
+def test_warp_variant_parity(mechs, dev, mech_files, mixed_reversibility_mech, idx):
     """One warp per state (the emitted warp-per-state kernel, lanes splitting the
     species and the reactions) gives the oracle's results as well, including the
-    SRI and PLOG reactions of the pressure-dependent variant."""
+    SRI and PLOG reactions of the pressure-dependent variant and, with every third
+    reaction irreversible, reactions of both directions in one class."""
     from paper_2503_24286_gb300 import binding as B
-    orc = mechs[idx][1] if idx in mechs else O.Oracle(mech_files[0][idx])
-    m = B.Mechanism(mech_files[0][idx], "variant=warp")
+    path = mixed_reversibility_mech if idx == "7-mixed" else mech_files[0][idx]
+    orc = mechs[idx][1] if idx in mechs else O.Oracle(path)
+    m = B.Mechanism(path, "variant=warp")
+    idx = 7 if idx == "7-mixed" else idx
     assert m.stat("variant_warp") == 1
     st, rho, e = _inputs(idx, 777, orc, seed_offset=11)
     w = m.net_production_rates(_t(rho, dev), _t(st.Y, dev), T=_t(st.T, dev)).cpu().numpy()

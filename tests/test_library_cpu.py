@@ -126,6 +126,24 @@ def test_pressure_dependent_forms_parse_validate_and_compile(mech_files, tmp_pat
     mw = B.Mechanism(mech_files[0][7], "device=0;variant=warp;cache=0")
     mw.prepare("warp")
     assert mw.stat("wfwd_cubin_bytes") > 0 and mw.stat("warp_chunks") >= 325 / 32
+    # the warp tables pack three factors a side: a fourth-order reaction is refused
+    # by variant=warp (and accepted by the thread-per-state kernels)
+    mech = handmech.abcd_mechanism()
+    mech.reactions[0].reactants = [(0, 2), (1, 2)]
+    mech.reactions[0].products = [(2, 2), (3, 2)]
+    p4 = handmech.write(mech, str(tmp_path), "order4.txt")
+    assert B.Mechanism(p4, "device=0").stat("omega_fp64_flops_per_point") > 0
+    with pytest.raises(B.PyroError) as ei:
+        B.Mechanism(p4, "device=0;variant=warp")
+    assert ei.value.code == B.PYRO_EINVAL and "three factors" in str(ei.value)
+    # one NASA range choice per state: species with another T_mid are refused too
+    mech = handmech.abcd_mechanism()
+    mech.species[1].t_mid = 1500.0
+    pt = handmech.write(mech, str(tmp_path), "tmid.txt")
+    assert B.Mechanism(pt, "device=0").stat("jacobian_supported") == 0
+    with pytest.raises(B.PyroError) as ei:
+        B.Mechanism(pt, "device=0;variant=warp")
+    assert ei.value.code == B.PYRO_EINVAL and "T_mid" in str(ei.value)
     mech = handmech.abcd_mechanism(kind="falloff", low=(1e16, -1.0, 1000.0))
     mech.reactions[0].sri = (0.5, 100.0, -3.0)                # c must be positive
     with pytest.raises(B.PyroError) as ei:
