@@ -12,10 +12,13 @@ within 1e-11 of its gross scale (reading c15; for derivatives the oracle's GJ):
   53-species mechanism with its Troe data removed.
 
 The equilibrium states span mass fractions down to ~1e-230, so some rates and
-their derivatives fall near the bottom of the double range, where products pass
-through subnormal numbers and lose relative precision in either program;
-derivative entries are compared with an absolute floor of 1e-290 added to 1e-11
-of their gross scale (DER_FLOOR), far below any entry that matters.
+their derivatives fall near the bottom of the double range.  The kernels and
+the oracle form the same products in different orders (e.g. kk E_i rho a_j on
+the GPU against k_f C_i C_j in the oracle), and an intermediate that one of them
+takes through the subnormal range (below 2.2e-308) loses its relative
+precision there; derivative entries are compared with an absolute floor of
+1e-250 added to 1e-11 of their gross scale (DER_FLOOR), far below any entry that
+matters (a floor of 1e-290 fails at such entries).
 """
 import math
 
@@ -32,7 +35,7 @@ pytestmark = pytest.mark.gpu
 R = 8314.462618
 P0 = 101325.0
 TOL = 1e-11
-DER_FLOOR = 1e-290
+DER_FLOOR = 1e-250
 
 
 @pytest.fixture(scope="module")
