@@ -1205,7 +1205,7 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
         {"sY", N1}, {"sL", N1}, {"sA", N1}, {"sEr", N1}, {"sLp", N1}, {"seh", N1}, {"scm", N1},
         {"sjt", N1}, {"su", N1}, {"sX", N1},
         {"sPj", std::max(1, gJ.nseg)}, {"sPu", std::max(1, gJ.nseg)}, {"sPt", ty ? std::max(1, gT.nseg) : 1},
-        {"sG", gtot + 1}, {"sR3", region}};
+        {"sG", gtot + 1}, {"sR3", region}, {"sIW", N1}, {"sJMw", N * NB}};
     int words = 0;
     for (auto& a : arr) words += a.second;
     const long bytes = 8L * words;
@@ -1228,7 +1228,11 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
       << "  double* sP = sR3;            // nonzero sums of a row group (after the gathers)\n"
       << "  double* sC = sR3 + " << cap << ";   // carries of the row-group gathers\n"
       << "  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;\n"
-      << "  wload_tables(s_exp, s_log, s_nu);\n  if (tid == 0) sG[" << GZ << "] = 0.0;\n  __syncthreads();\n"
+      << "  uint2* sJM = reinterpret_cast<uint2*>(sJMw);   // (mask, base) of every (row, 32-column block)\n"
+      << "  wload_tables(s_exp, s_log, s_nu);\n  if (tid == 0) sG[" << GZ << "] = 0.0;\n"
+      << "  for (int q = tid; q < NSP; q += " << LN << ") sIW[q] = __ldg(w_invW + q);\n"
+      << "  for (int q = tid; q < " << N * NB << "; q += " << LN << ") sJM[q] = __ldg(w_jm + q);\n"
+      << "  __syncthreads();\n"
       << "  for (i64 p = blockIdx.x; p < n; p += gridDim.x) {\n"
       << "    const double rho = g_rho[p], T = g_T[p];\n"
          "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
@@ -1262,16 +1266,20 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
          "    const double ysum = red[0], cv = red[1], cvT = red[2];\n    (void)cvT;\n";
     if (plog) k << "    const double lnp = lnT + pdm::log(rho * ysum, s_log) + " << lnR << ";\n";
     // phase B: chunks to warps, largest estimated cost first, to the least loaded warp
+    // cost of a chunk: the FP64 operations of its emitted code (fma, binary + - *,
+    // and the device exponential / logarithm / reciprocal at their operation counts)
+    auto count = [](const std::string& t, const std::string& pat) {
+      double c = 0;
+      for (size_t at = t.find(pat); at != std::string::npos; at = t.find(pat, at + pat.size())) ++c;
+      return c;
+    };
     std::vector<double> cost(ch.size());
     for (size_t c = 0; c < ch.size(); ++c) {
-      const WChunk& q = ch[c];
-      double e = 30 + 3 * chunk_occ(q) + 4 * q.nrb;
-      if (q.kind == WK_TB) e += 4 + 3 * q.neff;
-      else if (q.kind == WK_LIND) e += 30 + 3 * q.neff;
-      else if (q.kind == WK_TROE3 || q.kind == WK_TROE4) e += 75 + 3 * q.neff;
-      else if (q.kind == WK_SRI) e += 60 + 3 * q.neff;
-      else if (q.kind == WK_PLOG) e += 20 + 4 * q.nodes;
-      cost[c] = e;
+      std::ostringstream t;
+      emit_chunk(t, ch[c], ty ? W_JAC : W_JAD);
+      const std::string x = t.str();
+      cost[c] = count(x, "fma(") + count(x, " * ") + count(x, " + ") + count(x, " - ") +
+                opt.warp_exp_ops * count(x, "PEXP(") + 7 * count(x, "pdm::log(") + 4 * count(x, "pdm::rcp(");
     }
     std::vector<int> ordc(ch.size());
     for (size_t c = 0; c < ch.size(); ++c) ordc[c] = (int)c;
@@ -1282,6 +1290,11 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
       const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
       own[w].push_back(c);
       load[w] += cost[c];
+    }
+    {
+      double mx = 0, sum = 0;
+      for (double l : load) { mx = std::max(mx, l); sum += l; }
+      out.stats[std::string(ty ? "wjac" : "wjad") + "_reaction_phase_imbalance"] = sum > 0 ? mx * NW / sum : 1.0;
     }
     k << "    double pew = 0.0, pcw = 0.0, pejt = 0.0, pU = 0.0;   // sums over reactions (Tdot row)\n";
     for (int w = 0; w < NW; ++w) {
@@ -1338,19 +1351,22 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
              "      const int K = (int)(f & 0xffffu);\n      double v = sP[K];\n"
              "      for (int l = (int)((f >> 16) & 255u); l <= (int)(f >> 24); ++l) v += sC[l];\n"
              "      sP[K] = v;\n    }\n    __syncthreads();\n";
-      k << "    for (int q = warp; q < " << (G.r1 - G.r0) * NB << "; q += " << NW << ") {\n"
-           "      const int k = " << G.r0 << " + q / " << NB << ", b = q % " << NB << ";\n"
-           "      const int i = b * 32 + lane;\n"
-           "      if (i < NSP) {\n"
-           "        const uint2 mb = __ldg(w_jm + k * " << NB << " + b);\n";
+      // one row per warp, its column blocks unrolled (independent loads and stores)
+      k << "    for (int k = " << G.r0 << " + warp; k < " << G.r1 << "; k += " << NW << ") {\n"
+           "      const double uk = su[k];\n";
+      if (ty) k << "      double* Jr = g_J + ((i64)(1 + k) * " << N1 << " + 1) * n + p;\n";
+      else k << "      const double jk = sjt[k], Wk = __ldg(w_W + k);\n      double* Jr = g_J + (i64)k * " << N << " * n + p;\n";
+      k << "#pragma unroll\n      for (int b = 0; b < " << NB << "; ++b) {\n"
+           "        const int i = b * 32 + lane;\n";
+      if (N % 32) k << "        if (b == " << NB - 1 << " && i >= NSP) break;\n";
+      k << "        const uint2 mb = sJM[k * " << NB << " + b];\n"
+           "        const bool nz = (mb.x >> lane) & 1u;\n"
+           "        const double t = nz ? sP[mb.y + __popc(mb.x & ((1u << lane) - 1u))] : 0.0;\n";
       if (ty)
-        k << "        double v = su[k] * __ldg(w_invW + i);\n"
-             "        if ((mb.x >> lane) & 1u) v += sP[mb.y + __popc(mb.x & ((1u << lane) - 1u))];\n"
-             "        g_J[((i64)(1 + k) * " << N1 << " + 1 + i) * n + p] = v;\n";
+        k << "        Jr[(i64)i * n] = fma(uk, sIW[i], t);\n";
       else
-        k << "        double v = fma(sjt[k], sX[i], su[k] * __ldg(w_invW + i));\n"
-             "        if ((mb.x >> lane) & 1u) v = fma(__ldg(w_W + k), sP[mb.y + __popc(mb.x & ((1u << lane) - 1u))], v);\n"
-             "        g_J[((i64)k * " << N << " + i) * n + p] = v;\n";
+        k << "        double v = fma(jk, sX[i], uk * sIW[i]);\n        if (nz) v = fma(Wk, t, v);\n"
+             "        Jr[(i64)i * n] = v;\n";
       k << "      }\n    }\n    __syncthreads();\n";
     }
     k << "  }\n}\n";
