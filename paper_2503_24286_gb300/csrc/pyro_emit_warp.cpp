@@ -1063,6 +1063,7 @@ __device__ double wtsolve(const double* sY, double e, double T0, int max_iter, f
   // written once (u_k/W_i plus the nonzero part).
   auto cta_jac = [&](bool ty) -> bool {
     const int LN = 256, NW = 8, NB = (N + 31) / 32;
+    const int CL = kJacCluster, CB = (N + 7) / 8;   // blocks per cluster (states), 8-column blocks
     std::vector<WChunk> ch = P.chunks;
     int gtot = 0;
     for (auto& c : ch) { c.goff = gtot; gtot += chunk_gslots(c); }
@@ -1161,6 +1162,26 @@ __device__ double wtsolve(const double* sY, double e, double T0, int max_iter, f
       emit_array(k, "unsigned", "w_jf" + std::to_string(g), nzg[g].fix, false);
     }
     k << R"(
+// Thread-block cluster of CL blocks (consecutive states): rank, barrier over the
+// cluster's threads (release/acquire: shared-memory writes before it are visible
+// to every block of the cluster after it), and a load from another block's
+// shared memory at the address of the same variable.
+__device__ __forceinline__ unsigned cl_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+}
+__device__ __forceinline__ double ld_dsmem(const double* q, unsigned rank) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(q);
+  unsigned ra;
+  double v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra));
+  return v;
+}
 // warp sums of four values at once (every lane gets all four): 6 FP64 adds per lane
 __device__ __forceinline__ void warp_sum4(double (&v)[4], int lane) {
   const bool b4 = lane & 16, b3 = lane & 8;
@@ -1214,7 +1235,7 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
     k << "\n// " << (ty ? "Dense Jacobian d(Tdot, omega)/d(T, Y) at fixed rho (arguments and layout as pyro_jacobian)"
                         : "dS/dY at fixed (rho, e), S = W omega (arguments and layout as pyro_jacobian_adiabatic)")
       << ",\n// one block of " << NW << " warps per state.\n"
-      << "extern \"C\" __global__ void __launch_bounds__(" << LN << ") " << kname
+      << "extern \"C\" __global__ void __cluster_dims__(" << CL << ", 1, 1) __launch_bounds__(" << LN << ", 2) " << kname
       << "(i64 n, const double* __restrict__ g_rho,\n"
          "    const double* __restrict__ g_T, const double* __restrict__ g_Y, double* __restrict__ g_J,\n"
          "    double* __restrict__ g_scratch) {\n"
@@ -1233,7 +1254,11 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
       << "  for (int q = tid; q < NSP; q += " << LN << ") sIW[q] = __ldg(w_invW + q);\n"
       << "  for (int q = tid; q < " << N * NB << "; q += " << LN << ") sJM[q] = __ldg(w_jm + q);\n"
       << "  __syncthreads();\n"
-      << "  for (i64 p = blockIdx.x; p < n; p += gridDim.x) {\n"
+      << "  // the cluster's blocks take the consecutive states pb .. pb + CL - 1 (a block past\n"
+         "  // the end evaluates the last state again and writes nothing of its own)\n"
+         "  const unsigned crank = cl_rank();\n"
+         "  for (i64 pb = (i64)(blockIdx.x - crank); pb < n; pb += gridDim.x) {\n"
+         "    const bool act = pb + crank < n;\n    const i64 p = act ? pb + crank : n - 1;\n"
       << "    const double rho = g_rho[p], T = g_T[p];\n"
          "    const double lnT = pdm::log(T, s_log), invT = pdm::rcp(T), invT2 = invT * invT;\n"
          "    const double RT = " << lit((double)R_GAS) << " * T;\n"
@@ -1312,7 +1337,7 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
       emit_gather_loop(k, gT, 4, 0, "acc = fma(sDE[e.y & 0xfffffu], sG[e.x], acc);", false, "sPt", "tid");
       k << "    double r4[4] = {pew, pcw, pejt, pU};\n    cta_sum4(r4, sRed + 40, warp, lane);\n"
            "    const double rcv = pdm::rcp(rho * cv), Tdot = -r4[0] * rcv, tcv = Tdot * pdm::rcp(cv);\n"
-           "    if (tid == 0) g_J[p] = fma(-(r4[1] + r4[2]), rcv, -tcv * cvT);\n";
+           "    if (tid == 0 && act) g_J[p] = fma(-(r4[1] + r4[2]), rcv, -tcv * cvT);\n";
     } else {
       k << "    __syncthreads();\n    const double mrcv = -pdm::rcp(cv);\n";
     }
@@ -1323,8 +1348,10 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
       k << gather_total(4, "sPt", "td") <<
            "      sjt[k] = jt; su[k] = u;\n"
            "      const double iw = __ldg(w_invW + k);\n"
-           "      g_J[(i64)(1 + k) * " << N1 << " * n + p] = jt;\n"
-           "      g_J[(i64)(1 + k) * n + p] = fma(-fma(iw, r4[3], td), rcv, -tcv * (scm[k] * iw));\n";
+           "      if (act) {\n"
+           "        g_J[(i64)(1 + k) * " << N1 << " * n + p] = jt;\n"
+           "        g_J[(i64)(1 + k) * n + p] = fma(-fma(iw, r4[3], td), rcv, -tcv * (scm[k] * iw));\n"
+           "      }\n";
     } else {
       k << "      const double Wk = __ldg(w_W + k);\n"
            "      sjt[k] = Wk * jt; su[k] = Wk * u;\n"
@@ -1350,24 +1377,31 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
              "      const unsigned f = __ldg(w_jf" << gs << " + tid);\n"
              "      const int K = (int)(f & 0xffffu);\n      double v = sP[K];\n"
              "      for (int l = (int)((f >> 16) & 255u); l <= (int)(f >> 24); ++l) v += sC[l];\n"
-             "      sP[K] = v;\n    }\n    __syncthreads();\n";
-      // one row per warp, its column blocks unrolled (independent loads and stores)
-      k << "    for (int k = " << G.r0 << " + warp; k < " << G.r1 << "; k += " << NW << ") {\n"
-           "      const double uk = su[k];\n";
-      if (ty) k << "      double* Jr = g_J + ((i64)(1 + k) * " << N1 << " + 1) * n + p;\n";
-      else k << "      const double jk = sjt[k], Wk = __ldg(w_W + k);\n      double* Jr = g_J + (i64)k * " << N << " * n + p;\n";
-      k << "#pragma unroll\n      for (int b = 0; b < " << NB << "; ++b) {\n"
-           "        const int i = b * 32 + lane;\n";
-      if (N % 32) k << "        if (b == " << NB - 1 << " && i >= NSP) break;\n";
-      k << "        const uint2 mb = sJM[k * " << NB << " + b];\n"
-           "        const bool nz = (mb.x >> lane) & 1u;\n"
-           "        const double t = nz ? sP[mb.y + __popc(mb.x & ((1u << lane) - 1u))] : 0.0;\n";
+             "      sP[K] = v;\n    }\n";
+      // every block's sums of this row group complete and visible to the cluster
+      k << "    cl_sync();\n";
+      // the rows of the group for the cluster's CL states: each (row, 8-column block)
+      // item is one warp instruction, lanes 4c .. 4c + 3 holding column 8 cb + c of
+      // the CL consecutive states, so that four lanes fill one 32-byte sector of J;
+      // the other blocks' values are read from their shared memory
+      k << "    for (int q = (int)crank * " << NW << " + warp; q < " << (G.r1 - G.r0) * CB << "; q += " << NW * CL << ") {\n"
+           "      const int k = " << G.r0 << " + q / " << CB << ", i = (q % " << CB << ") * 8 + (lane >> 2);\n"
+           "      const unsigned rr = lane & 3u;\n";
+      if (N % 8) k << "      if (i < NSP) {\n";
+      else k << "      {\n";
+      k << "        const uint2 mb = sJM[k * " << NB << " + (i >> 5)];\n"
+           "        const int bit = i & 31;\n"
+           "        const bool nz = (mb.x >> bit) & 1u;\n"
+           "        const double t = nz ? ld_dsmem(sP + mb.y + __popc(mb.x & ((1u << bit) - 1u)), rr) : 0.0;\n"
+           "        const double uk = ld_dsmem(su + k, rr);\n";
       if (ty)
-        k << "        Jr[(i64)i * n] = fma(uk, sIW[i], t);\n";
+        k << "        const double v = fma(uk, sIW[i], t);\n"
+             "        if (pb + rr < n) g_J[((i64)(1 + k) * " << N1 << " + 1 + i) * n + pb + rr] = v;\n";
       else
-        k << "        double v = fma(jk, sX[i], uk * sIW[i]);\n        if (nz) v = fma(Wk, t, v);\n"
-             "        Jr[(i64)i * n] = v;\n";
-      k << "      }\n    }\n    __syncthreads();\n";
+        k << "        double v = fma(ld_dsmem(sjt + k, rr), ld_dsmem(sX + i, rr), uk * sIW[i]);\n"
+             "        if (nz) v = fma(__ldg(w_W + k), t, v);\n"
+             "        if (pb + rr < n) g_J[((i64)k * " << N << " + i) * n + pb + rr] = v;\n";
+      k << "      }\n    }\n    cl_sync();   // before the next group's gather overwrites the sums\n";
     }
     k << "  }\n}\n";
     const std::string key = ty ? "wjac" : "wjad";

@@ -25,6 +25,11 @@ struct WarpEmit {
 constexpr int kWarpMaxSpecies = 1022;
 constexpr int kWarpMaxReactions = 65535;
 
+// Blocks (consecutive states) per thread-block cluster of the block-per-state
+// Jacobian kernels: the dense write pass of a cluster covers its states together,
+// four lanes filling one 32-byte sector of the output.  Grids are multiples of it.
+constexpr int kJacCluster = 4;
+
 // Whether the warp-per-state kernels cover the mechanism: the limits above, at
 // most three factors on each side of a reaction (packed factor lists; net
 // stoichiometric coefficients -3..3), and one NASA-7 T_mid shared by all species

@@ -46,6 +46,7 @@ struct Driver {
   decltype(&cuLaunchKernel) LaunchKernel = nullptr;
   decltype(&cuFuncSetAttribute) FuncSetAttribute = nullptr;
   decltype(&cuOccupancyMaxActiveBlocksPerMultiprocessor) Occupancy = nullptr;
+  decltype(&cuOccupancyMaxActiveClusters) MaxActiveClusters = nullptr;
   decltype(&cuGetErrorString) GetErrorString = nullptr;
   bool ok = false;
   std::string err;
@@ -70,6 +71,7 @@ Driver& driver() {
            get("cuLaunchKernel", (void**)&d.LaunchKernel) &&
            get("cuFuncSetAttribute", (void**)&d.FuncSetAttribute) &&
            get("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void**)&d.Occupancy) &&
+           get("cuOccupancyMaxActiveClusters", (void**)&d.MaxActiveClusters) &&
            get("cuGetErrorString", (void**)&d.GetErrorString);
   });
   return d;
@@ -256,6 +258,7 @@ struct pyro_mech {
     int residual_blocks_per_sm = 0;         // Crank-Nicolson right-hand side (chord iterations)
     int block = 0;                          // threads per block (0: the derivative block size)
     int smem = -1;                          // dynamic shared memory (-1: the derivative kernels')
+    int clusters = 0;                       // clusters resident at once (clustered kernels)
   };
   std::map<std::string, Group> groups;
   std::mutex group_mu;
@@ -559,6 +562,21 @@ int ensure_groups(pyro_mech* h, const std::vector<std::string>& names) {
     if (r != CUDA_SUCCESS || nb < 1) return fail(PYRO_ECUDA, std::string(group_kernel(todo[i])) + " does not fit on an SM");
     G.blocks_per_sm = nb;
     h->emitted.stats[todo[i] + "_blocks_per_sm"] = nb;
+    if (todo[i] == "wjac" || todo[i] == "wjad") {
+      // persistent grid of the clusters that fit at once (a cluster's blocks share a GPC)
+      CUlaunchConfig cfg;
+      std::memset(&cfg, 0, sizeof(cfg));
+      cfg.gridDimX = (unsigned)(pyro::kJacCluster * h->num_sms);
+      cfg.gridDimY = cfg.gridDimZ = 1;
+      cfg.blockDimX = (unsigned)blk;
+      cfg.blockDimY = cfg.blockDimZ = 1;
+      cfg.sharedMemBytes = (unsigned)smem;
+      int ncl = 0;
+      r = d.MaxActiveClusters(&ncl, G.f, &cfg);
+      if (r != CUDA_SUCCESS || ncl < 1) return fail(PYRO_ECUDA, std::string(group_kernel(todo[i])) + ": no cluster fits");
+      G.clusters = ncl;
+      h->emitted.stats[todo[i] + "_active_clusters"] = ncl;
+    }
     if (h->emitted.stats["deriv_store_global"] > 0 && todo[i] != "jac" && todo[i] != "jad" && todo[i] != "cn" &&
         todo[i][0] != 'w') {
       size_t bytes = (size_t)h->num_sms * nb * 4 * h->m.n_species() * h->opt.deriv_block * sizeof(double);
@@ -628,8 +646,11 @@ int launch_warp(const pyro_mech* h, const pyro_mech::Group& G, int64_t n, void* 
 // block-per-state kernels (dense Jacobians of variant=warp): one state per block
 // and iteration, a persistent grid of the resident blocks
 int launch_cta(const pyro_mech* h, const pyro_mech::Group& G, int64_t n, void* stream, void** params) {
-  int64_t cap = (int64_t)h->num_sms * G.blocks_per_sm;
-  unsigned grid = (unsigned)(n < cap ? n : cap);
+  // clusters of kJacCluster blocks: the grid is a multiple of the cluster size
+  const int64_t CLs = pyro::kJacCluster;
+  const int64_t cap = CLs * G.clusters;
+  const int64_t need = (n + CLs - 1) / CLs * CLs;
+  unsigned grid = (unsigned)(need < cap ? need : cap);
   if (grid == 0) return PYRO_OK;
   CUresult r = driver().LaunchKernel(G.f, grid, 1, 1, G.block, 1, 1, G.smem, as_stream(stream), params, nullptr);
   if (r != CUDA_SUCCESS) return fail(PYRO_ECUDA, "kernel launch: " + cu_err(r));
