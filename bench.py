@@ -64,6 +64,8 @@ PROFILED_TRAFFIC = {
     # 2^19-state ncu captures scaled by 8 to a 2^22-state launch
     "953a6879ca9d63b7": 3.334e9,
     "a24d27e8509fd73d": 3.330e9,
+    # 2^20-state capture (dram__bytes_read.sum + dram__bytes_write.sum) scaled by 4
+    "d480c6fd1d99f5f7": 3.497e9,
 }
 
 
