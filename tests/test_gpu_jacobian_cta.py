@@ -93,3 +93,22 @@ def test_block_per_state_single_and_empty(mech_files, mixed_reversibility_mech, 
     assert np.all(np.abs(J - Jo) <= TOL * G + 1e-300)
     e = torch.empty(0, dtype=torch.float64, device=dev)
     assert m.jacobian(e, e, torch.empty((orc.N, 0), dtype=torch.float64, device=dev)).numel() == 0
+
+
+def test_block_per_state_output_alignment(mech_files, mixed_reversibility_mech, dev):
+    """The dense pass writes two adjacent states with one 16-byte store when the
+    state count is even and J is 16-byte aligned, else one state per store: an
+    output that starts 8 bytes into an allocation (even n) and an odd n give the
+    same bits as the aligned call."""
+    m, orc, _ = _handle(mech_files, mixed_reversibility_mech, 1)
+    NP = orc.N + 1
+    for n in (64, 63):
+        st = synth.config_states(1, n=n, offset_seed=65)
+        rho = orc.density(st.p, st.T, st.Y)
+        r, T, Y = _t(rho, dev), _t(st.T, dev), _t(st.Y, dev)
+        J = m.jacobian(r, T, Y)
+        buf = torch.empty(NP * NP * n + 1, dtype=torch.float64, device=dev)
+        Jo = buf[1:].view(NP * NP, n)
+        assert Jo.data_ptr() % 16 == 8
+        m.jacobian(r, T, Y, out=Jo)
+        assert torch.equal(J, Jo)
