@@ -1063,7 +1063,7 @@ __device__ double wtsolve(const double* sY, double e, double T0, int max_iter, f
   // written once (u_k/W_i plus the nonzero part).
   auto cta_jac = [&](bool ty) -> bool {
     const int LN = 256, NW = 8, NB = (N + 31) / 32;
-    const int CL = kJacCluster, CB = (N + 7) / 8, CB16 = (N + 15) / 16;   // blocks per cluster (states), column blocks
+    const int CL = kJacCluster, CB16 = (N + 15) / 16;   // blocks per cluster (states), 16-column blocks
     std::vector<WChunk> ch = P.chunks;
     int gtot = 0;
     for (auto& c : ch) { c.goff = gtot; gtot += chunk_gslots(c); }
@@ -1389,46 +1389,36 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
       if (g == 0)
         k << "    for (int q = tid; q < " << CL * N << "; q += " << LN << ") sU4[q] = ld_dsmem(su + q % NSP, (unsigned)(q / NSP));\n"
              "    __syncthreads();\n";
-      if (ty) {
-        // the rows of the group for the cluster's CL states: each (row, 16-column block)
-        // item is one warp instruction, lane 2c + h holding column 16 cb + c of states
-        // 2h and 2h + 1 (one 16-byte store; two lanes fill one 32-byte sector of J); the
-        // other blocks' nonzero sums are read from their shared memory
-        k << "    for (int q = (int)crank * " << NW << " + warp; q < " << (G.r1 - G.r0) * CB16 << "; q += " << NW * CL << ") {\n"
-             "      const int k = " << G.r0 << " + q / " << CB16 << ", i = (q % " << CB16 << ") * 16 + (lane >> 1);\n"
-             "      const unsigned s0 = (lane & 1u) * 2u;\n";
-        if (N % 16) k << "      if (i < NSP) {\n";
-        else k << "      {\n";
-        k << "        const uint2 mb = sJM[k * " << NB << " + (i >> 5)];\n"
-             "        const int bit = i & 31;\n"
-             "        const bool nz = (mb.x >> bit) & 1u;\n"
-             "        const double* sPi = sP + mb.y + __popc(mb.x & ((1u << bit) - 1u));\n"
-             "        const double t0 = nz ? ld_dsmem(sPi, s0) : 0.0, t1 = nz ? ld_dsmem(sPi, s0 + 1u) : 0.0;\n"
-             "        const double iw = sIW[i];\n"
-             "        const double v0 = fma(sU4[s0 * NSP + k], iw, t0), v1 = fma(sU4[(s0 + 1u) * NSP + k], iw, t1);\n"
-             "        double* dst = g_J + ((i64)(1 + k) * " << N1 << " + 1 + i) * n + pb + s0;\n"
-             "        if (vec2 && pb + s0 + 1 < n) {\n"
-             "          *reinterpret_cast<double2*>(dst) = make_double2(v0, v1);\n"
-             "        } else {\n"
-             "          if (pb + s0 < n) dst[0] = v0;\n"
-             "          if (pb + s0 + 1 < n) dst[1] = v1;\n"
-             "        }\n";
-      } else {
-        // as above with (row, 8-column block) items, lanes 4c .. 4c + 3 holding column
-        // 8 cb + c of the CL states (four lanes fill one sector)
-        k << "    for (int q = (int)crank * " << NW << " + warp; q < " << (G.r1 - G.r0) * CB << "; q += " << NW * CL << ") {\n"
-             "      const int k = " << G.r0 << " + q / " << CB << ", i = (q % " << CB << ") * 8 + (lane >> 2);\n"
-             "      const unsigned rr = lane & 3u;\n";
-        if (N % 8) k << "      if (i < NSP) {\n";
-        else k << "      {\n";
-        k << "        const uint2 mb = sJM[k * " << NB << " + (i >> 5)];\n"
-             "        const int bit = i & 31;\n"
-             "        const bool nz = (mb.x >> bit) & 1u;\n"
-             "        const double t = nz ? ld_dsmem(sP + mb.y + __popc(mb.x & ((1u << bit) - 1u)), rr) : 0.0;\n"
-             "        double v = fma(ld_dsmem(sjt + k, rr), ld_dsmem(sX + i, rr), sU4[rr * NSP + k] * sIW[i]);\n"
-             "        if (nz) v = fma(__ldg(w_W + k), t, v);\n"
-             "        if (pb + rr < n) g_J[((i64)k * " << N << " + i) * n + pb + rr] = v;\n";
-      }
+      // the rows of the group for the cluster's CL states: each (row, 16-column block)
+      // item is one warp instruction, lane 2c + h holding column 16 cb + c of states
+      // 2h and 2h + 1 (one 16-byte store; two lanes fill one 32-byte sector of J); the
+      // other blocks' per-state values are read from their shared memory
+      k << "    for (int q = (int)crank * " << NW << " + warp; q < " << (G.r1 - G.r0) * CB16 << "; q += " << NW * CL << ") {\n"
+           "      const int k = " << G.r0 << " + q / " << CB16 << ", i = (q % " << CB16 << ") * 16 + (lane >> 1);\n"
+           "      const unsigned s0 = (lane & 1u) * 2u;\n";
+      if (N % 16) k << "      if (i < NSP) {\n";
+      else k << "      {\n";
+      k << "        const uint2 mb = sJM[k * " << NB << " + (i >> 5)];\n"
+           "        const int bit = i & 31;\n"
+           "        const bool nz = (mb.x >> bit) & 1u;\n"
+           "        const double* sPi = sP + mb.y + __popc(mb.x & ((1u << bit) - 1u));\n"
+           "        const double t0 = nz ? ld_dsmem(sPi, s0) : 0.0, t1 = nz ? ld_dsmem(sPi, s0 + 1u) : 0.0;\n"
+           "        const double iw = sIW[i];\n";
+      if (ty)
+        k << "        const double v0 = fma(sU4[s0 * NSP + k], iw, t0), v1 = fma(sU4[(s0 + 1u) * NSP + k], iw, t1);\n"
+             "        double* dst = g_J + ((i64)(1 + k) * " << N1 << " + 1 + i) * n + pb + s0;\n";
+      else
+        k << "        const double Wk = __ldg(w_W + k);\n"
+             "        double v0 = fma(ld_dsmem(sjt + k, s0), ld_dsmem(sX + i, s0), sU4[s0 * NSP + k] * iw);\n"
+             "        double v1 = fma(ld_dsmem(sjt + k, s0 + 1u), ld_dsmem(sX + i, s0 + 1u), sU4[(s0 + 1u) * NSP + k] * iw);\n"
+             "        if (nz) { v0 = fma(Wk, t0, v0); v1 = fma(Wk, t1, v1); }\n"
+             "        double* dst = g_J + ((i64)k * " << N << " + i) * n + pb + s0;\n";
+      k << "        if (vec2 && pb + s0 + 1 < n) {\n"
+           "          *reinterpret_cast<double2*>(dst) = make_double2(v0, v1);\n"
+           "        } else {\n"
+           "          if (pb + s0 < n) dst[0] = v0;\n"
+           "          if (pb + s0 + 1 < n) dst[1] = v1;\n"
+           "        }\n";
       k << "      }\n    }\n    cl_sync();   // before the next group's gather overwrites the sums\n";
     }
     k << "  }\n}\n";

@@ -96,10 +96,10 @@ def test_block_per_state_single_and_empty(mech_files, mixed_reversibility_mech, 
 
 
 def test_block_per_state_output_alignment(mech_files, mixed_reversibility_mech, dev):
-    """The dense pass writes two adjacent states with one 16-byte store when the
-    state count is even and J is 16-byte aligned, else one state per store: an
-    output that starts 8 bytes into an allocation (even n) and an odd n give the
-    same bits as the aligned call."""
+    """The dense passes write two adjacent states with one 16-byte store when the
+    state count is even and J is 16-byte aligned, else one state per store: for
+    both Jacobians, an output that starts 8 bytes into an allocation gives the
+    bits of the aligned call, at an even and an odd state count."""
     m, orc, _ = _handle(mech_files, mixed_reversibility_mech, 1)
     NP = orc.N + 1
     for n in (64, 63):
@@ -112,3 +112,7 @@ def test_block_per_state_output_alignment(mech_files, mixed_reversibility_mech, 
         assert Jo.data_ptr() % 16 == 8
         m.jacobian(r, T, Y, out=Jo)
         assert torch.equal(J, Jo)
+        A = m.jacobian_adiabatic(r, T, Y)
+        Ao = buf[1:orc.N * orc.N * n + 1].view(orc.N * orc.N, n)
+        m.jacobian_adiabatic(r, T, Y, out=Ao)
+        assert torch.equal(A, Ao)
