@@ -78,7 +78,13 @@ typedef struct pyro_mech pyro_mech;
  *                        pyro_jvp, pyro_vjp): the lanes split the species and
  *                        the reactions, in chunks of 32 reactions emitted for
  *                        the mechanism's reaction classes -- the faster form for
- *                        large mechanisms such as 160 species / 1100 reactions)
+ *                        large mechanisms such as 160 species / 1100 reactions;
+ *                        pyro_jacobian and pyro_jacobian_adiabatic then run one
+ *                        block of 8 warps per state, in clusters of 4 blocks on
+ *                        4 consecutive states, with no per-handle scratch).
+ *                        variant=warp needs at most three factors on each side
+ *                        of a reaction and one NASA-7 T_mid for all species
+ *                        (PYRO_EINVAL otherwise)
  *   store=auto|shared|global  (where each thread keeps its state's species
  *                        arrays: shared memory, or -- automatic when they do
  *                        not fit, e.g. 160 species -- a library-owned global
@@ -199,8 +205,10 @@ int pyro_vjp(const pyro_mech* mech, int64_t n, const double* rho, const double* 
  * use, grown as needed; 8 B x pyro_mech_stat("jacobian_scratch_doubles_per_point")
  * x deriv_block (default 64) x the resident blocks: with the defaults ~0.6 GB for
  * 53 species, ~3 GB for 160 species and 1100 reactions): calls on one handle that use it (pyro_jacobian,
- * pyro_jacobian_adiabatic, pyro_cn_step) must not overlap on the GPU.  Needs
- * all species to share one NASA-7 T_mid. */
+ * pyro_jacobian_adiabatic, pyro_cn_step) must not overlap on the GPU.  Handles
+ * loaded with variant=warp use the block-per-state kernels instead, which keep
+ * the partials in shared memory and need no scratch (their calls may overlap).
+ * Needs all species to share one NASA-7 T_mid. */
 int pyro_jacobian(const pyro_mech* mech, int64_t n, const double* rho, const double* T, const double* Y,
                   double* J, void* stream);
 
