@@ -24,6 +24,13 @@
 //    each species boundary, and one pass over the species adds the (at most a
 //    few) partial sums of each species.  Fixed order: results are
 //    deterministic.
+//
+// The dense Jacobians (d(Tdot, omega)/d(T, Y) at fixed rho and dS/dY at fixed
+// (rho, e)) run one block of 8 warps per state with the same reaction chunks
+// spread over the warps, every per-reaction partial kept in shared memory, the
+// rows assembled by block-wide balanced gathers and written once; blocks form
+// clusters of 4 on consecutive states so that the write pass fills whole
+// 32-byte output sectors from the 4 blocks' shared memory.
 #include "pyro_emit_warp.h"
 
 #include <algorithm>

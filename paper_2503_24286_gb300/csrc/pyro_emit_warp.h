@@ -11,7 +11,8 @@
 namespace pyro {
 
 struct WarpEmit {
-  // "wfwd": pyro_omega_warp, "wjvp": pyro_jvp_warp, "wvjp": pyro_vjp_warp
+  // "wfwd": pyro_omega_warp, "wjvp": pyro_jvp_warp, "wvjp": pyro_vjp_warp,
+  // "wjac": pyro_jacobian_cta, "wjad": pyro_jacobian_adiabatic_cta
   std::map<std::string, std::string> sources;
   std::map<std::string, double> stats;
   std::map<std::string, int> wpb;               // warps (states) per block of each kernel
