@@ -1232,7 +1232,10 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
         {"s_exp", 512}, {"s_log", 256}, {"s_nu", 8}, {"sRed", 80},
         {"sY", N1}, {"sL", N1}, {"sA", N1}, {"sEr", N1}, {"sLp", N1}, {"seh", N1}, {"scm", N1},
         {"sjt", N1}, {"su", N1}, {"sX", N1},
-        {"sPj", std::max(1, gJ.nseg)}, {"sPu", std::max(1, gJ.nseg)}, {"sPt", ty ? std::max(1, gT.nseg) : 1},
+        // (dS/dY: after phase C2, sPj..sPu hold the cluster's jt_k and sPt its dT/dY_i)
+        {"sPj", ty ? std::max(1, gJ.nseg) : std::max(gJ.nseg, 2 * N)},
+        {"sPu", ty ? std::max(1, gJ.nseg) : std::max(gJ.nseg, 2 * N)},
+        {"sPt", ty ? std::max(1, gT.nseg) : CL * N},
         {"sG", gtot + 1}, {"sR3", region}, {"sIW", N1}, {"sJMw", N * NB}};
     int words = 0;
     for (auto& a : arr) words += a.second;
@@ -1254,6 +1257,8 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
     }
     k << "  double* sRt = sR3;\n  double* sRM = sR3 + " << M << ";\n  double* sDE = sR3 + " << 2 * M << ";\n"
       << "  double* sU4 = sY;           // the cluster's u_k, [state][species] (during the row groups)\n"
+      << (ty ? "" : "  double* sJT4 = sPj;         // the cluster's W_k jt_k and dT/dY_i (dS/dY, during the row groups)\n"
+                    "  double* sX4 = sPt;\n")
       << "  // 16-byte stores of two adjacent states need an even state count and a 16-byte aligned J\n"
       << "  const bool vec2 = (n & 1) == 0 && (reinterpret_cast<unsigned long long>(g_J) & 15ull) == 0;\n"
       << "  (void)vec2;\n"
@@ -1391,15 +1396,20 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
              "      sP[K] = v;\n    }\n";
       // every block's sums of this row group complete and visible to the cluster
       k << "    cl_sync();\n";
-      // the cluster's u_k (written in phase C2 of every block, so complete now) copied
-      // once per state into this block's species arrays, free after phase B
-      if (g == 0)
-        k << "    for (int q = tid; q < " << CL * N << "; q += " << LN << ") sU4[q] = ld_dsmem(su + q % NSP, (unsigned)(q / NSP));\n"
-             "    __syncthreads();\n";
+      // the cluster's u_k (and for dS/dY jt_k and dT/dY_i), written in phase C2 of
+      // every block and so complete now, copied once per state into arrays of this
+      // block that are free by then (species arrays, gather segments)
+      if (g == 0) {
+        k << "    for (int q = tid; q < " << CL * N << "; q += " << LN << ") {\n"
+             "      const unsigned r = (unsigned)(q / NSP);\n      const int c = q % NSP;\n"
+             "      sU4[q] = ld_dsmem(su + c, r);\n";
+        if (!ty) k << "      sJT4[q] = ld_dsmem(sjt + c, r);\n      sX4[q] = ld_dsmem(sX + c, r);\n";
+        k << "    }\n    __syncthreads();\n";
+      }
       // the rows of the group for the cluster's CL states: each (row, 16-column block)
       // item is one warp instruction, lane 2c + h holding column 16 cb + c of states
       // 2h and 2h + 1 (one 16-byte store; two lanes fill one 32-byte sector of J); the
-      // other blocks' per-state values are read from their shared memory
+      // other blocks' nonzero sums are read from their shared memory
       k << "    for (int q = (int)crank * " << NW << " + warp; q < " << (G.r1 - G.r0) * CB16 << "; q += " << NW * CL << ") {\n"
            "      const int k = " << G.r0 << " + q / " << CB16 << ", i = (q % " << CB16 << ") * 16 + (lane >> 1);\n"
            "      const unsigned s0 = (lane & 1u) * 2u;\n";
@@ -1416,8 +1426,8 @@ __device__ __forceinline__ void cta_sum4(double (&v)[4], double* sRed, int warp,
              "        double* dst = g_J + ((i64)(1 + k) * " << N1 << " + 1 + i) * n + pb + s0;\n";
       else
         k << "        const double Wk = __ldg(w_W + k);\n"
-             "        double v0 = fma(ld_dsmem(sjt + k, s0), ld_dsmem(sX + i, s0), sU4[s0 * NSP + k] * iw);\n"
-             "        double v1 = fma(ld_dsmem(sjt + k, s0 + 1u), ld_dsmem(sX + i, s0 + 1u), sU4[(s0 + 1u) * NSP + k] * iw);\n"
+             "        double v0 = fma(sJT4[s0 * NSP + k], sX4[s0 * NSP + i], sU4[s0 * NSP + k] * iw);\n"
+             "        double v1 = fma(sJT4[(s0 + 1u) * NSP + k], sX4[(s0 + 1u) * NSP + i], sU4[(s0 + 1u) * NSP + k] * iw);\n"
              "        if (nz) { v0 = fma(Wk, t0, v0); v1 = fma(Wk, t1, v1); }\n"
              "        double* dst = g_J + ((i64)k * " << N << " + i) * n + pb + s0;\n";
       k << "        if (vec2 && pb + s0 + 1 < n) {\n"
