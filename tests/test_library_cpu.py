@@ -126,6 +126,13 @@ def test_pressure_dependent_forms_parse_validate_and_compile(mech_files, tmp_pat
     mw = B.Mechanism(mech_files[0][7], "device=0;variant=warp;cache=0")
     mw.prepare("warp")
     assert mw.stat("wfwd_cubin_bytes") > 0 and mw.stat("warp_chunks") >= 325 / 32
+    # and the block-per-state Jacobians (clusters of 4 states), with the reaction
+    # chunks spread evenly enough over the 8 warps
+    mw.prepare("jacobian,jacobian_adiabatic")
+    assert mw.stat("jacobian_cta") == 1 and mw.stat("jacobian_adiabatic_cta") == 1
+    assert mw.stat("wjac_cubin_bytes") > 0 and mw.stat("wjad_cubin_bytes") > 0
+    assert mw.stat("wjac_nonzeros") <= 53 * 53 and mw.stat("wjac_terms") >= mw.stat("wjac_nonzeros")
+    assert mw.stat("wjac_reaction_phase_imbalance") < 2.5
     # the warp tables pack three factors a side: a fourth-order reaction is refused
     # by variant=warp (and accepted by the thread-per-state kernels)
     mech = handmech.abcd_mechanism()
